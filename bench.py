@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the decomposed-ADMM hot path on GB300: ADMM iterations/s and time-to-1e-4.
+
+One step = one cold-start solve (admm_reset + admm_solve) of the dual block-arrow workload
+l=100, d=10, h=20, m=200 (n=1020, 100 cliques of 30) with FP32 clique eigensolves and an FP64
+affine step, to max(eps_p, eps_d) < 1e-4. value = ADMM iterations per second over the timed solves
+(device time, CUDA events; L2 flushed before every solve). The same solves with FP64 eigensolves
+are reported beside it, and so is the CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config C]
+
+For N > 1 the launcher starts one process per GPU; every rank solves its own replica (the
+single-instance path does not shard) and value = all ranks' iterations / slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iter/s & time-to-1e-4 residual: batched FP32 vs plain FP64, one GB300"
+UNIT = "iter/s"
+FLUSH_BYTES = 256 << 20          # > 129 MB L2
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# Device constants used for the ALU roofline (GB300: 152 SMs, 128 FP32 lanes per SM, FP64 at
+# 1.25 TFLOP/s nominal for the whole GPU).
+NUM_SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-iters", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload(config: int):
+    from sdp_inputs import CONFIGS, config_instance
+    cfg = dict(CONFIGS[config])
+    inst = config_instance(config)
+    arrs = dict(n=inst.n, cliques=inst.cliques, A_ptr=inst.A_ptr, A_row=inst.A_row, A_col=inst.A_col,
+                A_val=inst.A_val, b=inst.b, C_row=inst.C_row, C_col=inst.C_col, C_val=inst.C_val)
+    return cfg, inst, arrs
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_worker(args):
+    """Runs in a child process with one BLAS thread: times oracle iterations on the workload."""
+    from oracle import chordal_admm as orc
+    cfg, inst, arrs = workload(args.config)
+    t0 = time.perf_counter()
+    sdp = orc.ChordalSDP(inst.n, inst.cliques, inst.A_ptr, inst.A_row, inst.A_col, inst.A_val,
+                         inst.b, inst.C_row, inst.C_col, inst.C_val)
+    setup_s = time.perf_counter() - t0
+    step = orc.primal_iteration if cfg["form"] == "primal" else orc.dual_iteration
+    st = orc.admm_init(sdp, cfg["form"])
+    iters, t0 = 0, time.perf_counter()
+    limit = args.oracle_iters if args.oracle_iters > 0 else 10 ** 9
+    while iters < limit and (args.oracle_iters > 0 or time.perf_counter() - t0 < args.cpu_seconds):
+        st = step(sdp, st, cfg["rho"])
+        iters += 1
+    dt = time.perf_counter() - t0
+    print(json.dumps(dict(iters=iters, seconds=dt, setup_seconds=setup_s)))
+
+
+def run_oracle(args, iters=0, seconds=None):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", str(args.config),
+           "--cpu-seconds", str(seconds if seconds is not None else args.cpu_seconds),
+           "--oracle-iters", str(iters)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if res.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(args, cfg):
+    r = run_oracle(args)
+    return dict(value=r["iters"] / r["seconds"], unit=UNIT, cores=1, kind="oracle",
+                sample=f"{r['iters']} oracle {cfg['form']}-form iterations from a cold start on "
+                       f"{cfg['name']} (setup {r['setup_seconds']:.2f} s excluded), one BLAS thread")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "utilization.gpu",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(CLOCK_FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(CLOCK_FIELDS):
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 reasons=[CLOCK_FIELDS[5 + i].split(".")[1] for i in range(4)
+                                          if parts[5 + i].lower().startswith("active")]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["util"] >= 50] or rows
+        reasons = sorted({x for r in loaded for x in r["reasons"]})
+        return dict(sm_mhz=statistics.median(r["sm"] for r in loaded), sm_max_mhz=max(r["smax"] for r in rows),
+                    reasons=reasons, samples=len(rows), samples_under_load=len(loaded))
+
+
+# ----------------------------------------------------------------------------- roofline model
+
+def kernel_model(name, inst_sizes, cfg, prec):
+    """Algorithmic work of one launch of a kernel: (bound, amount, unit). Bytes count every
+    array the kernel must read or write once; flops count the eigensolve as 9 s^3 (symmetric QR
+    with vectors, Golub & Van Loan) plus 2 s^3 for the rebuild V diag(lambda+) V^T."""
+    s, p = inst_sizes["s_list"], inst_sizes["p"]
+    nEL, SL, m, nnz = inst_sizes["nEL"], inst_sizes["SL"], inst_sizes["m"], inst_sizes["nnz"]
+    if name.startswith("project"):
+        flops = sum(11.0 * si ** 3 for si in s)
+        return "alu", flops, "flop"
+    if name in ("spmv_rows",):
+        return "hbm", nnz * 12.0 + nEL * 8.0, "byte"
+    if name in ("spmv_cols",):
+        return "hbm", nnz * 10.0 + (nEL + 1) * 4.0 + nEL * (8 * 3 + 1) + m * 8.0, "byte"
+    if name in ("tri_lower", "tri_upper"):
+        return "hbm", m * (m + 1) / 2 * 8.0 + 2 * m * 8.0, "byte"
+    if name == "scatter_dual":
+        return "hbm", SL * (8 * 2 + 4) + nEL * (4 + 8 + 8 * 2 + 8 + 1), "byte"
+    if name == "scatter_primal":
+        return "hbm", SL * (8 * 3 + 4) + nEL * (4 + 8 + 8 * 2 + 8 + 1), "byte"
+    if name == "update_dual":
+        return "hbm", SL * (8 * 4 + 4 + 1 + 8 * 2), "byte"
+    return "hbm", 0.0, "byte"
+
+
+def roofline(phases, inst_sizes, cfg, prec, peaks, clocks):
+    name = max(phases, key=phases.get)
+    bound, amount, unit = kernel_model(name, inst_sizes, cfg, prec)
+    ms = phases[name]
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        entry = tr.get(f"{name}:{prec}")
+        if entry and entry.get("source_sha") == source_sha():
+            traffic = entry["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    if bound == "alu":
+        mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        if prec == "fp32":
+            peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+            peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        else:
+            peak = FP64_NOMINAL_TFLOPS
+            peak_src = "nominal FP64 1.25 TFLOP/s"
+        achieved = amount / (ms * 1e-3) / 1e12
+        return dict(kernel=name, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=achieved / peak, traffic=traffic, peak_source=peak_src, ms=ms)
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = amount / (ms * 1e-3) / 1e9
+    return dict(kernel=name, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                traffic=traffic, peak_source="of measured (MEASURED_PEAKS.json hbm_gbs)", ms=ms)
+
+
+def source_sha():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1609_06068_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:12]
+
+
+# ----------------------------------------------------------------------------- arms
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce(world, value, op):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_reference(args):
+    world, rank, local = dist_init(args)
+    if rank != 0:
+        return
+    cfg, inst, arrs = workload(args.config)
+    per_step = max(1, int(os.environ.get("BENCH_REF_ITERS", "10")))
+    if args.warmup > 0:
+        run_oracle(args, iters=min(per_step, 3))
+    r = run_oracle(args, iters=per_step * max(1, args.steps))
+    value = r["iters"] / r["seconds"]
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * r["seconds"] / max(1, args.steps),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", config=dict(workload=cfg["name"], form=cfg["form"], rho=cfg["rho"],
+                                              step=f"{per_step} oracle iterations"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                                  sample=f"{r['iters']} {cfg['form']}-form oracle iterations, one BLAS thread"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    world, rank, local = dist_init(args)
+    import numpy as np
+    import torch
+
+    import paper_1609_06068_gb300 as cadmm
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    cadmm.load_library()
+    cfg, inst, arrs = workload(args.config)
+    opts = cadmm.make_opts(rho=cfg["rho"], tol=cfg["tol"] if cfg["tol"] > 0 else 1e-4,
+                           max_iter=cfg["max_iter"], check_every=16, form=cfg["form"], prec="fp32")
+    solver = cadmm.ChordalADMM(arrs, opts)
+    sz = solver.sizes
+    inst_sizes = dict(s_list=[len(c) for c in inst.cliques], p=sz["p"], nEL=sz["nE_lower"],
+                      SL=sz["S_lower"], m=sz["m"], nnz=sz["nnz_A"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed_solves(k):
+        iters, ms, launches, res = 0, [], 0, None
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.reset(stream)
+            res = solver.solve(stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters += res["iters"]
+            launches += res["kernel_launches"] + 2      # + ctrl reset and the r rebuild
+        return iters, ms, launches, res
+
+    for _ in range(args.warmup):
+        solver.reset(stream)
+        solver.solve(stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    iters, ms, launches, last = timed_solves(args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+
+    total_ms = sum(ms)
+    total_ms_max = reduce(world, total_ms, "max")
+    iters_all = reduce(world, iters, "sum")
+    value = iters_all / (total_ms_max * 1e-3)
+    ms_per_step = total_ms_max / args.steps
+    fp32_iters_per_solve = iters / args.steps
+
+    # FP64 eigensolves on the same instance (the plain baseline of the metric)
+    solver.set_opts(prec="fp64")
+    it64, ms64, _, last64 = timed_solves(args.fp64_steps)
+    fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=UNIT, time_to_tol_ms=sum(ms64) / args.fp64_steps,
+                iters_per_solve=it64 / args.fp64_steps, obj_dual=last64["obj_dual"],
+                obj_primal=last64["obj_primal"], status=last64["status"])
+    phases64 = cadmm.sdp_time_phases(solver.h, reps=5, stream=stream)
+    solver.set_opts(prec="fp32")
+    phases = cadmm.sdp_time_phases(solver.h, reps=50, stream=stream)
+
+    peaks = {}
+    try:
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    roof = roofline(phases, inst_sizes, cfg, "fp32", peaks, clocks)
+
+    # end to end through the C ABI from pinned host arrays: setup, solve, read the solution
+    pinned = {}
+    h2d = 0
+    for k in ("A_ptr", "A_row", "A_col", "A_val", "b", "C_row", "C_col", "C_val"):
+        a = np.ascontiguousarray(arrs[k])
+        t = torch.from_numpy(a).pin_memory()
+        pinned[k] = t.numpy()
+        h2d += a.nbytes
+    cl = [np.asarray(c, np.int32) for c in arrs["cliques"]]
+    h2d += sum(c.nbytes for c in cl) + 4 * (len(cl) + 1)
+    e2e_arrs = dict(pinned, n=arrs["n"], cliques=cl)
+    e2e_iters, e2e_s, d2h = 0, 0.0, 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = cadmm.ChordalADMM(e2e_arrs, opts)
+        r2 = s2.solve(stream)
+        X, y, Z = s2.solution()
+        s2.close()
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        e2e_iters += r2["iters"]
+        d2h = X.nbytes + y.nbytes + Z.nbytes + 64
+    e2e_iters_all = reduce(world, e2e_iters, "sum")
+    e2e_s_max = reduce(world, e2e_s, "max")
+    e2e = dict(value=e2e_iters_all / e2e_s_max, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+               ms_per_step=1e3 * e2e_s_max / args.e2e_steps,
+               includes="sdp_setup (host maps, A D^-1 A^T, Cholesky, upload) + admm_solve + sdp_get_solution")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(args, cfg)
+
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32 eigensolves + f64 affine/reductions", data="synthetic",
+            config=dict(workload=cfg["name"], n=sz["n"], m=sz["m"], p=sz["p"], clique=sz["max_clique"],
+                        form=cfg["form"], rho=cfg["rho"], tol=opts.tol, max_iter=opts.max_iter,
+                        step="one cold-start solve to max(eps_p, eps_d) < tol",
+                        l2="256 MiB buffer written before every timed solve", parallelism=f"replicas x{world}"),
+            time_to_tol_ms=ms_per_step, iters_per_solve=fp32_iters_per_solve,
+            obj_dual=last["obj_dual"], obj_primal=last["obj_primal"], status=last["status"],
+            fp64_plain=fp64, speedup_fp32_vs_fp64_time_to_tol=fp64["time_to_tol_ms"] / ms_per_step,
+            phases_ms_fp32=phases, phases_ms_fp64=phases64,
+            roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks,
+            gpu=torch.cuda.get_device_name(local))
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.oracle_worker:
+        oracle_worker(args)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

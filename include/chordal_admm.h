@@ -1,0 +1,192 @@
+/*
+ * chordal_admm.h — C ABI of the GB300 (sm_103a) hot path of chordally decomposed ADMM for sparse
+ * semidefinite programs (Zheng, Fantuzzi, Papachristodoulou, Goulart, Wynn, "Fast ADMM for
+ * Semidefinite Programs with Chordal Sparsity").
+ *
+ * Problem (Section I, Eqs. PrimalSDP / DualSDP):
+ *     min <C, X>  s.t.  <A_i, X> = b_i (i = 1..m),  X PSD          (primal standard form)
+ *     max <b, y>  s.t.  sum_i y_i A_i + Z = C,       Z PSD          (dual standard form)
+ * with an aggregate sparsity pattern whose chordal graph has maximal cliques C_1..C_p (Section III.A).
+ *
+ * Conventions shared by every entry point:
+ *   - Symmetric matrices are passed in lower-triangle coordinate form: entry k is (row[k], col[k],
+ *     val[k]) with row >= col, 0-based; an off-diagonal entry stands for both (i,j) and (j,i).
+ *     Repeated coordinates are summed.
+ *   - E_L is the lower pattern: all pairs (i >= j) with i, j in a common clique, in column-major
+ *     order (by column, then row). Vectors "on E_L" have one entry per such pair.
+ *   - Clique blocks are stored "packed": clique k's s_k x s_k block keeps its lower triangle column
+ *     by column (LAPACK 'L' packed order), blocks one after another in clique order. S_L is the
+ *     total length, sum_k s_k (s_k + 1) / 2. Clique vertices must be strictly ascending (the
+ *     paper's E_k sorts them in natural order, Section II.B).
+ *   - Pointers are HOST pointers unless the argument says "device". The library copies host
+ *     inputs; the caller keeps ownership of everything it passes.
+ *   - Every function returns an int status: 0 success, > 0 a non-fatal outcome, < 0 an error
+ *     (see SDP_* below). No C++ exception crosses this boundary. sdp_last_error() gives a
+ *     message for the most recent error on the calling thread.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ */
+#ifndef CHORDAL_ADMM_H
+#define CHORDAL_ADMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------- */
+#define SDP_OK               0   /* converged (max(eps_p, eps_d) < tol) or call succeeded   */
+#define SDP_MAX_ITER         1   /* iteration budget of the call used without convergence   */
+#define SDP_ERR_ARG         -1   /* bad argument (size, pointer, option, row < col)          */
+#define SDP_ERR_CLIQUE      -2   /* cliques unsorted / out of range, or a data nonzero is not
+                                    covered by any clique block                              */
+#define SDP_ERR_NOT_PD      -3   /* A D^-1 A^T not positive definite (A rank-deficient)      */
+#define SDP_ERR_CUDA        -4   /* a CUDA runtime call failed                               */
+#define SDP_ERR_NAN         -5   /* a residual or objective became NaN/Inf                   */
+#define SDP_ERR_TIMEOUT     -6   /* a host wait on the device exceeded its time limit        */
+#define SDP_ERR_UNSUPPORTED -7   /* size beyond what the kernels support (see limits below)  */
+
+/* Limits of this build: clique size <= SDP_MAX_CLIQUE, m <= SDP_MAX_CONSTRAINTS, nnz(A) and S_L
+ * below 2^31. */
+#define SDP_MAX_CLIQUE       96
+#define SDP_MAX_CONSTRAINTS  16384
+
+/* ---- options ------------------------------------------------------------------------------ */
+#define SDP_PRIMAL    0   /* Algorithm 1: ADMM on the decomposed primal (Eq. PrimalVectorForm) */
+#define SDP_DUAL      1   /* Algorithm 2: ADMM on the decomposed dual (Eq. DualDecomposedSDPVector) */
+#define SDP_PROJ_FP64 0   /* clique eigendecompositions and reconstructions in FP64            */
+#define SDP_PROJ_FP32 1   /* ... in FP32; everything else stays FP64                            */
+
+typedef struct sdp_ctx* sdp_handle;   /* opaque; owns all of its device memory */
+
+typedef struct {
+    double rho;        /* ADMM penalty rho > 0 (Eqs. AugLagrPrimal / AugLagrDual)                */
+    double tol;        /* stop once max(eps_p, eps_d) < tol; tol <= 0 never stops early          */
+    int max_iter;      /* iteration cap of one admm_solve call (the paper uses 2000)             */
+    int check_every;   /* admm_solve reads the device stop flag every check_every iterations;
+                          iterations after convergence inside that window are skipped on the
+                          device, so results do not depend on it (0 = default 16)                */
+    int form;          /* SDP_PRIMAL or SDP_DUAL                                                 */
+    int prec;          /* SDP_PROJ_FP64 or SDP_PROJ_FP32                                         */
+    int flags;         /* reserved, must be 0                                                    */
+} admm_opts;
+
+typedef struct {
+    int iters;         /* iterations performed on this handle since the last admm_reset          */
+    int status;        /* SDP_OK, SDP_MAX_ITER or SDP_ERR_NAN (same as the return value)         */
+    double eps_p;      /* relative primal residual of the last iteration                         */
+    double eps_d;      /* relative dual residual of the last iteration                           */
+    double obj_primal; /* primal objective estimate <C, X>                                       */
+    double obj_dual;   /* dual objective estimate <b, y>                                         */
+    double seconds;    /* host wall-clock time of the call                                       */
+    long long kernel_launches; /* kernels this call launched (graph nodes included; kernels of
+                                  iterations after convergence start and return at once)          */
+} admm_result;
+
+typedef struct {
+    int n, m, p, max_clique;
+    long long nE_lower;    /* |E_L| */
+    long long S_lower;     /* S_L   */
+    long long nnz_A;       /* stored nonzeros of A on E_L (after merging duplicates) */
+} sdp_sizes;
+
+/* Residual definitions (the paper cites Boyd et al. 2011 for them without restating; this build
+ * reads them as follows, with Euclidean norms over the full symmetric vectors):
+ *   primal form: eps_p = ||[x_k - H_k x]|| / max(||[x_k]||, ||[H_k x]||, 1e-12),
+ *                eps_d = rho ||sum_k H_k^T (x_k+ - x_k)|| / max(||sum_k H_k^T lambda_k||, 1e-12);
+ *   dual form:   eps_p = ||[z_k - v_k]|| / max(||[z_k]||, ||[v_k]||, 1e-12),
+ *                eps_d = rho ||[v_k+ - v_k]|| / max(||[lambda_k]||, 1e-12).                   */
+
+/* ---- setup (Algorithms 1-2, "Setup: chordal decomposition, KKT factorization") -------------
+ * Builds the clique index maps (H_k as gather indices and their inverse as a CSR scatter map),
+ * D = sum_k H_k^T H_k (Section III.B.1), A on E_L in CSR and CSC form, M = A D^-1 A^T and its
+ * Cholesky factor L (computed once and cached; the per-iteration triangular solves use L^-1 and
+ * L^-T formed here), uploads everything to the device and zeroes the iterates.
+ *   n, m        matrix order and number of constraints (1 <= m <= SDP_MAX_CONSTRAINTS)
+ *   A_ptr[m+1]  constraint i owns coordinates A_ptr[i] .. A_ptr[i+1]-1 of A_row/A_col/A_val
+ *   b[m]        right-hand side
+ *   C_*         cost matrix C, C_nnz coordinates
+ *   pat_*       optional extra pattern coordinates that must be covered (may be NULL/0)
+ *   clique_ptr[p+1], clique_vtx  the maximal cliques, vertices strictly ascending
+ *   opts        initial options (copied)
+ *   out         receives the handle on success
+ * Errors: SDP_ERR_ARG, SDP_ERR_CLIQUE, SDP_ERR_NOT_PD, SDP_ERR_UNSUPPORTED, SDP_ERR_CUDA. */
+int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
+              const double* A_val, const double* b,
+              long long C_nnz, const int* C_row, const int* C_col, const double* C_val,
+              long long pat_nnz, const int* pat_row, const int* pat_col,
+              int p, const int* clique_ptr, const int* clique_vtx,
+              const admm_opts* opts, sdp_handle* out);
+
+/* Replace the options (rho, tol, form, precision may all change; the KKT factor does not depend
+ * on them). Takes effect at the next admm_iterate / admm_solve. Does not reset the iterates. */
+int sdp_set_opts(sdp_handle h, const admm_opts* opts);
+
+/* Zero the iterates (x, y, clique blocks, multipliers) and the iteration counter. Stream-ordered. */
+int admm_reset(sdp_handle h, void* cuda_stream);
+
+/* Run up to n_iters ADMM iterations (Algorithm 1 or 2 by opts.form) from the handle's current
+ * state, stopping early once max(eps_p, eps_d) < tol. Each iteration runs as captured CUDA graphs
+ * on cuda_stream; the call returns after the stream has finished them.
+ * Returns SDP_OK (converged), SDP_MAX_ITER (budget used), SDP_ERR_NAN, or an error. */
+int admm_iterate(sdp_handle h, int n_iters, void* cuda_stream, admm_result* out);
+
+/* admm_iterate with n_iters = opts.max_iter, from the current state (call admm_reset first for a
+ * cold start). */
+int admm_solve(sdp_handle h, void* cuda_stream, admm_result* out);
+
+int sdp_get_sizes(sdp_handle h, sdp_sizes* out);
+
+/* SDP-level solution estimates on E_L (host outputs, any may be NULL), by stationarity of the KKT
+ * systems at a fixed point: primal form X = x, y = -rho*y_admm, Z = sum_k H_k^T lambda_k; dual form
+ * X = -rho*x, y = y_admm, Z = sum_k H_k^T z_k. X_lower and Z_lower have nE_lower entries. */
+int sdp_get_solution(sdp_handle h, double* X_lower, double* y, double* Z_lower);
+
+/* Raw ADMM iterates (host outputs, any may be NULL): x on E_L (the affine iterate), y (m), and
+ * three packed block vectors of length S_L. Primal form: blk_a = x_k, blk_b = lambda_k, blk_c
+ * unused. Dual form: blk_a = z_k, blk_b = lambda_k, blk_c = v_k. */
+int sdp_get_state(sdp_handle h, double* x, double* y, double* blk_a, double* blk_b, double* blk_c);
+
+/* Set the iterates (same layout as sdp_get_state; NULL leaves a part unchanged). Used for warm
+ * starts and to resume from a checkpoint. Synchronous. */
+int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* blk_a,
+                  const double* blk_b, const double* blk_c);
+
+/* The index maps built by sdp_setup (host outputs, any may be NULL): the lower pattern E_L as
+ * (pat_row, pat_col) [nE_lower], the packed block offsets blk_off [p+1], and gather_idx [S_L]:
+ * for every packed block position, the E_L index it reads (H_k as an index map). */
+int sdp_get_maps(sdp_handle h, int* pat_row, int* pat_col, long long* blk_off, int* gather_idx);
+
+/* H_k x for every clique k (Section III.A): blocks_out[device, S_L] = gather of x[device, nE_lower].
+ * Exact copies. */
+int sdp_gather(sdp_handle h, const double* x, double* blocks_out, void* cuda_stream);
+
+/* sum_k H_k^T v_k (Section III.B.1): out[device, nE_lower] from blocks[device, S_L]. Each entry
+ * adds its clique contributions in ascending k starting from the first; no atomics, so the result
+ * is deterministic. */
+int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stream);
+
+/* Batched projection onto the PSD cone, P(W) = V max(Lambda, 0) V^T (Eqs. XkUpdate / zkUpdate):
+ * in and out are DEVICE pointers to packed lower blocks (FP64); sizes[count] and offsets[count]
+ * are HOST arrays giving each block's order (1 <= s <= SDP_MAX_CLIQUE) and its element offset in
+ * in/out. prec selects FP64 or FP32 eigensolves (results are FP64 either way). Blocks run in one
+ * launch, largest first. The call allocates a small stream-ordered device schedule. in == out is
+ * allowed; blocks must not overlap otherwise. */
+int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
+                        int count, int prec, void* cuda_stream);
+
+/* Profiling: run `reps` iterations kernel by kernel (no graph) on cuda_stream with CUDA events
+ * between the kernels, and write the average device milliseconds of each kernel of one iteration
+ * to ms_out[0 .. count-1] in launch order (count = 7 primal, 8 dual; returns count, or < 0 on
+ * error; max_out is the capacity of ms_out). The iterations really run and advance the state, with
+ * the stop test disabled. sdp_phase_name(form, i) names kernel i. */
+int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
+const char* sdp_phase_name(int form, int i);
+
+void sdp_free(sdp_handle h);
+const char* sdp_status_string(int status);
+const char* sdp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHORDAL_ADMM_H */

@@ -27,6 +27,7 @@ Readings where the paper is silent (each one also listed in the design notes):
 * Eq. (DualMultUpdate) is printed as ``λ_k = ρ H_k x``; substituting Eq. (vkEqn) into
   Eq. (MultUpdateDualSDP) gives ``λ_k = −ρ H_k x``, which is what Algorithm 2 uses here.
 * ``Σ_k H_kᵀ(·)`` adds clique contributions in ascending ``k`` starting from zero.
+* ``ρ⁻¹`` is formed once as ``1/ρ`` and multiplies, as the paper writes ``ρ⁻¹λ_k`` and ``ρ⁻¹c``.
 """
 
 from __future__ import annotations
@@ -250,15 +251,16 @@ def admm_init(sdp: ChordalSDP, form: str) -> dict:
 
 def primal_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     """One pass of Algorithm 1: x-update, clique projections, multipliers, residuals."""
-    # Eq. (OptCondMinYPrimal): right-hand side Σ H_kᵀ(x_k + λ_k/ρ) − c/ρ and b.
-    r = sdp.HT_sum([st["xk"][k] + st["lam"][k] / rho for k in range(sdp.p)]) - sdp.c / rho
+    rinv = 1.0 / rho
+    # Eq. (OptCondMinYPrimal): right-hand side Σ H_kᵀ(x_k + ρ⁻¹λ_k) − ρ⁻¹c and b.
+    r = sdp.HT_sum([st["xk"][k] + rinv * st["lam"][k] for k in range(sdp.p)]) - rinv * sdp.c
     x, y = sdp.kkt_solve(r, sdp.b)
-    # Eq. (XkUpdate): x_k = vec P_k[vec⁻¹(H_k x − λ_k/ρ)].
+    # Eq. (XkUpdate): x_k = vec P_k[vec⁻¹(H_k x − ρ⁻¹λ_k)].
     u = [sdp.H(k, x) for k in range(sdp.p)]
     xk_new = []
     for k in range(sdp.p):
         s = len(sdp.cliques[k])
-        xk_new.append(_vec(proj_psd(_mat(u[k] - st["lam"][k] / rho, s))))
+        xk_new.append(_vec(proj_psd(_mat(u[k] - rinv * st["lam"][k], s))))
     # Eq. (LambdakUpdate): λ_k += ρ (x_k − H_k x).
     lam_new = [st["lam"][k] + rho * (xk_new[k] - u[k]) for k in range(sdp.p)]
     # Residuals (reading of Section III.B's stopping test, see module docstring).
@@ -275,17 +277,18 @@ def primal_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
 
 def dual_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     """One pass of Algorithm 2: projections, (y, x), v_k, multipliers, residuals."""
-    # Eq. (zkUpdate): z_k = vec P_k[vec⁻¹(v_k − λ_k/ρ)].
+    rinv = 1.0 / rho
+    # Eq. (zkUpdate): z_k = vec P_k[vec⁻¹(v_k − ρ⁻¹λ_k)].
     zk = []
     for k in range(sdp.p):
         s = len(sdp.cliques[k])
-        zk.append(_vec(proj_psd(_mat(st["vk"][k] - st["lam"][k] / rho, s))))
-    # Eq. (OptCondMinYDual): right-hand side c − Σ H_kᵀ(z_k + λ_k/ρ) and −b/ρ.
-    r = sdp.c - sdp.HT_sum([zk[k] + st["lam"][k] / rho for k in range(sdp.p)])
-    x, y = sdp.kkt_solve(r, -sdp.b / rho)
-    # Eq. (vkEqn): v_k = z_k + λ_k/ρ + H_k x.
+        zk.append(_vec(proj_psd(_mat(st["vk"][k] - rinv * st["lam"][k], s))))
+    # Eq. (OptCondMinYDual): right-hand side c − Σ H_kᵀ(z_k + ρ⁻¹λ_k) and −ρ⁻¹b.
+    r = sdp.c - sdp.HT_sum([zk[k] + rinv * st["lam"][k] for k in range(sdp.p)])
+    x, y = sdp.kkt_solve(r, -(rinv * sdp.b))
+    # Eq. (vkEqn): v_k = z_k + ρ⁻¹λ_k + H_k x.
     u = [sdp.H(k, x) for k in range(sdp.p)]
-    vk_new = [zk[k] + st["lam"][k] / rho + u[k] for k in range(sdp.p)]
+    vk_new = [zk[k] + rinv * st["lam"][k] + u[k] for k in range(sdp.p)]
     # Eq. (DualMultUpdate) with the sign that Eq. (MultUpdateDualSDP) implies: λ_k = −ρ H_k x.
     lam_new = [-rho * u[k] for k in range(sdp.p)]
     # The general update of Eq. (MultUpdateDualSDP), kept for the identity check in the tests.
@@ -319,10 +322,10 @@ def admm_solve(sdp: ChordalSDP, form: str = "primal", rho: float = 1.0, tol: flo
         st = step(sdp, st, rho)
         if history:
             hist.append((st["eps_p"], st["eps_d"], st["obj_primal"], st["obj_dual"]))
-        e = max(st["eps_p"], st["eps_d"])
-        if not np.isfinite(e):
+        if not (np.isfinite(st["eps_p"]) and np.isfinite(st["eps_d"])):
             status = -5
             break
+        e = max(st["eps_p"], st["eps_d"])
         if e < tol:
             status = 0
             break

@@ -1,0 +1,368 @@
+"""GB300 (sm_103a) hot path of chordally decomposed ADMM for sparse SDPs.
+
+Python binding of the C ABI declared in ``include/chordal_admm.h``. Every function here has the
+name of a C entry point and only marshals arguments (NumPy arrays for host data, ``torch`` CUDA
+tensors for device buffers, ``torch``'s current stream by default). All computation runs in the
+CUDA library ``lib/libchordal_admm.so``; when it is missing, the first call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libchordal_admm.so")
+
+SDP_OK = 0
+SDP_MAX_ITER = 1
+SDP_ERR_ARG = -1
+SDP_ERR_CLIQUE = -2
+SDP_ERR_NOT_PD = -3
+SDP_ERR_CUDA = -4
+SDP_ERR_NAN = -5
+SDP_ERR_TIMEOUT = -6
+SDP_ERR_UNSUPPORTED = -7
+SDP_MAX_CLIQUE = 96
+SDP_MAX_CONSTRAINTS = 16384
+
+SDP_PRIMAL = 0
+SDP_DUAL = 1
+SDP_PROJ_FP64 = 0
+SDP_PROJ_FP32 = 1
+
+FORMS = {"primal": SDP_PRIMAL, "dual": SDP_DUAL}
+PRECS = {"fp64": SDP_PROJ_FP64, "fp32": SDP_PROJ_FP32}
+
+# Symbols the header declares (checked by the CPU test suite against the built library).
+EXPORTS = [
+    "sdp_setup", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
+    "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
+    "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name", "sdp_free",
+    "sdp_status_string", "sdp_last_error",
+]
+
+
+class SDPError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+class admm_opts(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("form", ctypes.c_int), ("prec", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class admm_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("eps_p", ctypes.c_double),
+                ("eps_d", ctypes.c_double), ("obj_primal", ctypes.c_double),
+                ("obj_dual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+class sdp_sizes(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
+                ("max_clique", ctypes.c_int), ("nE_lower", ctypes.c_longlong),
+                ("S_lower", ctypes.c_longlong), ("nnz_A", ctypes.c_longlong)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "sdp_setup": (_I, [_I, _I, _P, _P, _P, _P, _P, _LL, _P, _P, _P, _LL, _P, _P, _I, _P, _P,
+                           ctypes.POINTER(admm_opts), ctypes.POINTER(_P)]),
+        "sdp_set_opts": (_I, [_P, ctypes.POINTER(admm_opts)]),
+        "admm_reset": (_I, [_P, _P]),
+        "admm_iterate": (_I, [_P, _I, _P, ctypes.POINTER(admm_result)]),
+        "admm_solve": (_I, [_P, _P, ctypes.POINTER(admm_result)]),
+        "sdp_get_sizes": (_I, [_P, ctypes.POINTER(sdp_sizes)]),
+        "sdp_get_solution": (_I, [_P, _P, _P, _P]),
+        "sdp_get_state": (_I, [_P, _P, _P, _P, _P, _P]),
+        "sdp_set_state": (_I, [_P, _P, _P, _P, _P, _P]),
+        "sdp_get_maps": (_I, [_P, _P, _P, _P, _P]),
+        "sdp_gather": (_I, [_P, _P, _P, _P]),
+        "sdp_scatter": (_I, [_P, _P, _P, _P]),
+        "project_psd_batched": (_I, [_P, _P, _P, _P, _I, _I, _P]),
+        "sdp_time_phases": (_I, [_P, _I, _P, _P, _I]),
+        "sdp_phase_name": (ctypes.c_char_p, [_I, _I]),
+        "sdp_free": (None, [_P]),
+        "sdp_status_string": (ctypes.c_char_p, [_I]),
+        "sdp_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str, ok=(SDP_OK,)) -> int:
+    if rc in ok:
+        return rc
+    lib = load_library()
+    msg = lib.sdp_last_error().decode() or lib.sdp_status_string(rc).decode()
+    raise SDPError(rc, where, msg)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _stream(stream):
+    """cudaStream_t of ``stream`` (a torch.cuda.Stream, an int handle, or None = torch current)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, n: int | None = None, name: str = "tensor"):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} needs at least {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_opts(rho=1.0, tol=1e-4, max_iter=2000, check_every=16, form="primal", prec="fp64") -> admm_opts:
+    return admm_opts(float(rho), float(tol), int(max_iter), int(check_every),
+                     FORMS.get(form, form), PRECS.get(prec, prec), 0)
+
+
+def _result(r: admm_result) -> dict:
+    return dict(iters=r.iters, status=r.status, eps_p=r.eps_p, eps_d=r.eps_d,
+                obj_primal=r.obj_primal, obj_dual=r.obj_dual, seconds=r.seconds,
+                kernel_launches=r.kernel_launches)
+
+
+# ------------------------------------------------------------------------------- entry points
+
+def sdp_setup(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliques=None,
+              clique_ptr=None, clique_vtx=None, pat_row=None, pat_col=None, opts=None):
+    """Set up the decomposed problem on the current CUDA device; returns the opaque handle."""
+    lib = load_library()
+    if cliques is not None:
+        sizes = np.array([len(c) for c in cliques], dtype=np.int64)
+        clique_ptr = np.concatenate([[0], np.cumsum(sizes)])
+        clique_vtx = np.concatenate([np.asarray(c) for c in cliques]) if len(cliques) else np.zeros(0)
+    A_ptr = _arr(A_ptr, np.int64)
+    A_row, A_col, A_val = _arr(A_row, np.int32), _arr(A_col, np.int32), _arr(A_val, np.float64)
+    b = _arr(b, np.float64)
+    C_row, C_col, C_val = _arr(C_row, np.int32), _arr(C_col, np.int32), _arr(C_val, np.float64)
+    clique_ptr, clique_vtx = _arr(clique_ptr, np.int32), _arr(clique_vtx, np.int32)
+    pr = _arr(pat_row, np.int32) if pat_row is not None else None
+    pc = _arr(pat_col, np.int32) if pat_col is not None else None
+    opts = opts if opts is not None else make_opts()
+    h = ctypes.c_void_p()
+    rc = lib.sdp_setup(int(n), len(b), _ptr(A_ptr), _ptr(A_row), _ptr(A_col), _ptr(A_val), _ptr(b),
+                       len(C_val), _ptr(C_row), _ptr(C_col), _ptr(C_val),
+                       0 if pr is None else len(pr), _ptr(pr), _ptr(pc),
+                       len(clique_ptr) - 1, _ptr(clique_ptr), _ptr(clique_vtx),
+                       ctypes.byref(opts), ctypes.byref(h))
+    _check(rc, "sdp_setup")
+    _FORM_OF[h.value] = opts.form
+    return h
+
+
+def sdp_set_opts(h, opts: admm_opts):
+    _check(load_library().sdp_set_opts(h, ctypes.byref(opts)), "sdp_set_opts")
+    _FORM_OF[getattr(h, "value", h)] = opts.form
+
+
+def admm_reset(h, stream=None):
+    _check(load_library().admm_reset(h, _stream(stream)), "admm_reset")
+
+
+def admm_iterate(h, n_iters: int, stream=None) -> dict:
+    r = admm_result()
+    rc = load_library().admm_iterate(h, int(n_iters), _stream(stream), ctypes.byref(r))
+    _check(rc, "admm_iterate", ok=(SDP_OK, SDP_MAX_ITER))
+    return _result(r)
+
+
+def admm_solve(h, stream=None) -> dict:
+    r = admm_result()
+    rc = load_library().admm_solve(h, _stream(stream), ctypes.byref(r))
+    _check(rc, "admm_solve", ok=(SDP_OK, SDP_MAX_ITER))
+    return _result(r)
+
+
+def sdp_get_sizes(h) -> dict:
+    s = sdp_sizes()
+    _check(load_library().sdp_get_sizes(h, ctypes.byref(s)), "sdp_get_sizes")
+    return {f: getattr(s, f) for f, _ in sdp_sizes._fields_}
+
+
+def sdp_get_solution(h):
+    """(X on E_L, y, Z on E_L) as NumPy arrays."""
+    sz = sdp_get_sizes(h)
+    X = np.empty(sz["nE_lower"]); y = np.empty(sz["m"]); Z = np.empty(sz["nE_lower"])
+    _check(load_library().sdp_get_solution(h, _ptr(X), _ptr(y), _ptr(Z)), "sdp_get_solution")
+    return X, y, Z
+
+
+def sdp_get_state(h) -> dict:
+    sz = sdp_get_sizes(h)
+    out = dict(x=np.empty(sz["nE_lower"]), y=np.empty(sz["m"]), blk_a=np.empty(sz["S_lower"]),
+               blk_b=np.empty(sz["S_lower"]), blk_c=np.empty(sz["S_lower"]))
+    _check(load_library().sdp_get_state(h, *(_ptr(out[k]) for k in ("x", "y", "blk_a", "blk_b", "blk_c"))),
+           "sdp_get_state")
+    return out
+
+
+def sdp_set_state(h, x=None, y=None, blk_a=None, blk_b=None, blk_c=None):
+    arrs = [None if v is None else _arr(v, np.float64) for v in (x, y, blk_a, blk_b, blk_c)]
+    _check(load_library().sdp_set_state(h, *(_ptr(a) for a in arrs)), "sdp_set_state")
+
+
+def sdp_get_maps(h) -> dict:
+    sz = sdp_get_sizes(h)
+    out = dict(pat_row=np.empty(sz["nE_lower"], np.int32), pat_col=np.empty(sz["nE_lower"], np.int32),
+               blk_off=np.empty(sz["p"] + 1, np.int64), gather_idx=np.empty(sz["S_lower"], np.int32))
+    _check(load_library().sdp_get_maps(h, *(_ptr(out[k]) for k in ("pat_row", "pat_col", "blk_off", "gather_idx"))),
+           "sdp_get_maps")
+    return out
+
+
+def sdp_gather(h, x, blocks_out, stream=None):
+    sz = sdp_get_sizes(h)
+    _check(load_library().sdp_gather(h, _dev_ptr(x, sz["nE_lower"], "x"),
+                                      _dev_ptr(blocks_out, sz["S_lower"], "blocks_out"), _stream(stream)),
+           "sdp_gather")
+
+
+def sdp_scatter(h, blocks, out, stream=None):
+    sz = sdp_get_sizes(h)
+    _check(load_library().sdp_scatter(h, _dev_ptr(blocks, sz["S_lower"], "blocks"),
+                                       _dev_ptr(out, sz["nE_lower"], "out"), _stream(stream)),
+           "sdp_scatter")
+
+
+def project_psd_batched(inp, out, sizes, offsets, prec="fp64", stream=None):
+    """P(W) of packed lower blocks: ``inp``/``out`` float64 CUDA tensors; sizes/offsets host arrays."""
+    sizes = _arr(sizes, np.int32)
+    offsets = _arr(offsets, np.int64)
+    if len(sizes) != len(offsets):
+        raise ValueError("sizes and offsets differ in length")
+    need = int((offsets + sizes.astype(np.int64) * (sizes + 1) // 2).max()) if len(sizes) else 0
+    _check(load_library().project_psd_batched(_dev_ptr(inp, need, "inp"), _dev_ptr(out, need, "out"),
+                                              _ptr(sizes), _ptr(offsets), len(sizes),
+                                              PRECS.get(prec, prec), _stream(stream)),
+           "project_psd_batched")
+
+
+def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:
+    """Average device milliseconds of each kernel of one iteration, by kernel name."""
+    lib = load_library()
+    ms = np.zeros(16)
+    n = lib.sdp_time_phases(h, int(reps), _stream(stream), _ptr(ms), len(ms))
+    if n < 0:
+        _check(n, "sdp_time_phases")
+    form = _form_of(h)
+    return {lib.sdp_phase_name(form, i).decode(): float(ms[i]) for i in range(n)}
+
+
+def sdp_phase_name(form: int, i: int) -> str | None:
+    r = load_library().sdp_phase_name(int(form), int(i))
+    return None if r is None else r.decode()
+
+
+_FORM_OF = {}
+
+
+def _form_of(h) -> int:
+    return _FORM_OF.get(getattr(h, "value", h), SDP_PRIMAL)
+
+
+def sdp_free(h):
+    if h:
+        load_library().sdp_free(h)
+
+
+def sdp_status_string(code: int) -> str:
+    return load_library().sdp_status_string(int(code)).decode()
+
+
+def sdp_last_error() -> str:
+    return load_library().sdp_last_error().decode()
+
+
+class ChordalADMM:
+    """Owns one handle: ``with ChordalADMM(inst_arrays, opts) as s: s.solve()``."""
+
+    def __init__(self, arrays: dict, opts: admm_opts | None = None):
+        self.opts = opts if opts is not None else make_opts()
+        self.h = sdp_setup(arrays["n"], arrays["A_ptr"], arrays["A_row"], arrays["A_col"],
+                           arrays["A_val"], arrays["b"], arrays["C_row"], arrays["C_col"],
+                           arrays["C_val"], cliques=arrays["cliques"], opts=self.opts)
+        self.sizes = sdp_get_sizes(self.h)
+
+    def set_opts(self, **kw):
+        d = {f: getattr(self.opts, f) for f, _ in admm_opts._fields_}
+        for k, v in kw.items():
+            d[k] = FORMS.get(v, PRECS.get(v, v)) if k in ("form", "prec") else v
+        self.opts = admm_opts(**d)
+        sdp_set_opts(self.h, self.opts)
+
+    def reset(self, stream=None):
+        admm_reset(self.h, stream)
+
+    def iterate(self, n, stream=None):
+        return admm_iterate(self.h, n, stream)
+
+    def solve(self, stream=None):
+        return admm_solve(self.h, stream)
+
+    def state(self):
+        return sdp_get_state(self.h)
+
+    def solution(self):
+        return sdp_get_solution(self.h)
+
+    def close(self):
+        if self.h:
+            sdp_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,580 @@
+// C ABI of the decomposed-ADMM hot path: handle lifetime, device uploads, CUDA-graph capture of
+// whole iterations, and the host loop that launches graphs and polls the device stop flag.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sdp_internal.h"
+
+using cadmm::Ctrl;
+using cadmm::HostProblem;
+using cadmm::IterPtrs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return set_err(SDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kWaitTimeoutSeconds = 600.0;
+constexpr int kColCtasPerSm = 4;
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Wait for an event with a host-side time limit. The kernels contain no device-side waits, so
+// this limit only guards against a device that stopped answering.
+int wait_event(cudaEvent_t ev, double timeout_s) {
+    const double t0 = now_s();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return SDP_OK;
+        if (e != cudaErrorNotReady) return set_err(SDP_ERR_CUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+        if (now_s() - t0 > timeout_s) return set_err(SDP_ERR_TIMEOUT, "timed out waiting for the device");
+        std::this_thread::yield();
+    }
+}
+
+int check_opts(const admm_opts* o) {
+    if (!o) return set_err(SDP_ERR_ARG, "opts is NULL");
+    if (!(o->rho > 0.0) || o->rho != o->rho) return set_err(SDP_ERR_ARG, "rho must be positive");
+    if (o->max_iter < 0 || o->check_every < 0) return set_err(SDP_ERR_ARG, "max_iter and check_every must be >= 0");
+    if (o->form != SDP_PRIMAL && o->form != SDP_DUAL) return set_err(SDP_ERR_ARG, "form must be SDP_PRIMAL or SDP_DUAL");
+    if (o->prec != SDP_PROJ_FP64 && o->prec != SDP_PROJ_FP32) return set_err(SDP_ERR_ARG, "prec must be SDP_PROJ_FP64 or SDP_PROJ_FP32");
+    if (o->flags != 0) return set_err(SDP_ERR_ARG, "flags must be 0");
+    return SDP_OK;
+}
+
+}  // namespace
+
+struct sdp_ctx {
+    int device = 0;
+    admm_opts opts{};
+    int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0;
+    long long nnz = 0;
+    // host copies needed after setup
+    std::vector<int> pat_row, pat_col, blk_off, gather_idx;
+    std::vector<void*> allocs;
+    IterPtrs P{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g_one = nullptr, g_chunk = nullptr;
+    int chunk = 0, g_form = -1, g_prec = -1;
+    double g_rho = 0.0;
+    Ctrl* h_ctrl = nullptr;    // pinned, two slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    template <typename T>
+    int dalloc(T** ptr, size_t count) {
+        void* p_ = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        const cudaError_t e = cudaMalloc(&p_, bytes);
+        if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        allocs.push_back(p_);
+        *ptr = static_cast<T*>(p_);
+        return SDP_OK;
+    }
+    template <typename T>
+    int upload(T** ptr, const std::vector<T>& v) {
+        int rc = dalloc(ptr, v.size());
+        if (rc) return rc;
+        if (!v.empty()) {
+            const cudaError_t e = cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+        }
+        return SDP_OK;
+    }
+    void destroy_graphs() {
+        if (g_one) cudaGraphExecDestroy(g_one);
+        if (g_chunk) cudaGraphExecDestroy(g_chunk);
+        g_one = g_chunk = nullptr;
+        g_form = g_prec = -1;
+    }
+    ~sdp_ctx() {
+        cudaSetDevice(device);
+        destroy_graphs();
+        for (void* a : allocs) cudaFree(a);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (h_ctrl) cudaFreeHost(h_ctrl);
+    }
+};
+
+namespace {
+
+int capture_graph(sdp_ctx* h, int iters, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < iters && le == cudaSuccess; ++i)
+        le = cadmm::launch_iteration(h->P, h->opts.form, h->opts.prec, h->opts.rho, h->cap_stream);
+    const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return set_err(SDP_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(le));
+    }
+    if (ee != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
+    const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    return SDP_OK;
+}
+
+int ensure_graphs(sdp_ctx* h) {
+    const int chunk = h->opts.check_every > 0 ? h->opts.check_every : 16;
+    if (h->g_one && h->g_form == h->opts.form && h->g_prec == h->opts.prec && h->g_rho == h->opts.rho &&
+        h->chunk == chunk)
+        return SDP_OK;
+    h->destroy_graphs();
+    int rc = capture_graph(h, 1, &h->g_one);
+    if (rc) return rc;
+    rc = capture_graph(h, chunk, &h->g_chunk);
+    if (rc) return rc;
+    h->chunk = chunk;
+    h->g_form = h->opts.form;
+    h->g_prec = h->opts.prec;
+    h->g_rho = h->opts.rho;
+    return SDP_OK;
+}
+
+int sync_ctrl(sdp_ctx* h, cudaStream_t st, Ctrl* dst) {
+    CK(cudaMemcpyAsync(dst, h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->ev[0], st));
+    return wait_event(h->ev[0], kWaitTimeoutSeconds);
+}
+
+// Recompute the primal right-hand side r from the current blocks (needed after a reset, a state
+// upload or a change of rho). Clears a stop flag left by a finished solve first, since every
+// kernel skips its work while the flag is set.
+int rebuild_r_if_primal(sdp_ctx* h, cudaStream_t st) {
+    if (h->opts.form != SDP_PRIMAL) return SDP_OK;
+    CK(cadmm::launch_ctrl_clear(h->P.ctrl, st));
+    CK(cadmm::launch_primal_rebuild_r(h->P, h->opts.rho, st));
+    return SDP_OK;
+}
+
+int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
+    const double t0 = now_s();
+    int rc = ensure_graphs(h);
+    if (rc) return rc;
+    CK(cadmm::launch_ctrl_arm(h->P.ctrl, n_iters, h->opts.tol, st));
+    int remaining = n_iters;
+    int slot = 0, launched_chunks = 0;
+    bool stop = false;
+    long long launched_iters = 0;
+    // Chunks of `chunk` iterations; after each chunk the stop flag is copied back, and the host
+    // reads the previous chunk's flag while the current chunk runs.
+    while (remaining >= h->chunk && !stop) {
+        CK(cudaGraphLaunch(h->g_chunk, st));
+        remaining -= h->chunk;
+        launched_iters += h->chunk;
+        CK(cudaMemcpyAsync(&h->h_ctrl[slot], h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(h->ev[slot], st));
+        if (launched_chunks > 0) {
+            rc = wait_event(h->ev[slot ^ 1], kWaitTimeoutSeconds);
+            if (rc) return rc;
+            if (h->h_ctrl[slot ^ 1].done) stop = true;
+        }
+        ++launched_chunks;
+        slot ^= 1;
+    }
+    while (remaining > 0 && !stop) {
+        CK(cudaGraphLaunch(h->g_one, st));
+        --remaining;
+        ++launched_iters;
+    }
+    Ctrl c{};
+    rc = sync_ctrl(h, st, &c);
+    if (rc) return rc;
+    if (out) {
+        out->iters = c.iter;
+        out->status = c.status;
+        out->eps_p = c.eps_p;
+        out->eps_d = c.eps_d;
+        out->obj_primal = c.obj_p;
+        out->obj_dual = c.obj_d;
+        out->seconds = now_s() - t0;
+        out->kernel_launches = 1 + launched_iters * cadmm::iteration_kernel_count(h->opts.form);
+    }
+    if (c.status == SDP_ERR_NAN) set_err(SDP_ERR_NAN, "a residual or objective became NaN/Inf");
+    return c.status;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
+              const double* A_val, const double* b, long long C_nnz, const int* C_row,
+              const int* C_col, const double* C_val, long long pat_nnz, const int* pat_row,
+              const int* pat_col, int p, const int* clique_ptr, const int* clique_vtx,
+              const admm_opts* opts, sdp_handle* out) {
+    try {
+        if (!out) return set_err(SDP_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        int rc = check_opts(opts);
+        if (rc) return rc;
+        HostProblem hp;
+        std::string err;
+        rc = cadmm::build_host_problem(n, m, A_ptr, A_row, A_col, A_val, b, C_nnz, C_row, C_col, C_val,
+                                       pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, hp, err);
+        if (rc) return set_err(rc, err);
+
+        sdp_ctx* h = new sdp_ctx();
+        std::unique_ptr<sdp_ctx> guard(h);
+        CK(cudaGetDevice(&h->device));
+        h->opts = *opts;
+        h->n = hp.n; h->m = hp.m; h->p = hp.p; h->smax = hp.smax;
+        h->nEL = hp.nEL; h->SL = hp.SL; h->nnz = hp.nnz;
+        h->pat_row = hp.pat_row; h->pat_col = hp.pat_col;
+        h->blk_off = hp.blk_off; h->gather_idx = hp.gather_idx;
+        CK(cadmm::project_prepare());
+        CK(cadmm::iteration_prepare());
+
+        int num_sms = 0;
+        CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
+        IterPtrs& P = h->P;
+        P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
+        // CTAs per CSR row: enough row chunks for ~2 waves, each chunk >= 2048 nonzeros.
+        {
+            const long long avg = std::max<long long>(1, hp.nnz / hp.m);
+            long long R = (2LL * num_sms + hp.m - 1) / hp.m;
+            R = std::min<long long>(R, std::max<long long>(1, avg / 2048));
+            P.R = (int)std::max<long long>(1, std::min<long long>(R, 64));
+        }
+        P.ent_ctas = (hp.nEL + 255) / 256;
+        P.pos_ctas = (hp.SL + 255) / 256;
+        P.col_ctas = std::max(1, std::min(num_sms * kColCtasPerSm, (hp.nEL + 31) / 32));
+
+        std::vector<long long> off64(hp.blk_off.begin(), hp.blk_off.end());
+        int* d_int = nullptr;
+#define UP(field, vec)                                             \
+    do {                                                           \
+        auto* tmp_ = const_cast<std::remove_const_t<std::remove_pointer_t<decltype(P.field)>>*>(P.field); \
+        rc = h->upload(&tmp_, vec);                                \
+        if (rc) return rc;                                         \
+        P.field = tmp_;                                            \
+    } while (0)
+        UP(blk_off, hp.blk_off);
+        UP(blk_off64, off64);
+        UP(blk_size, hp.blk_size);
+        UP(order, hp.order);
+        UP(gather_idx, hp.gather_idx);
+        UP(pos_w, hp.pos_w);
+        UP(sc_ptr, hp.sc_ptr);
+        UP(sc_pos, hp.sc_pos);
+        UP(D, hp.D);
+        UP(wdinv, hp.wdinv);
+        UP(c, hp.c);
+        UP(b, hp.b);
+        UP(ew, hp.ew);
+        UP(a_rowptr, hp.a_rowptr);
+        UP(a_col, hp.a_col);
+        UP(a_val, hp.a_val);
+        UP(c_colptr, hp.c_colptr);
+        UP(c_row, hp.c_row);
+        UP(c_val, hp.c_val);
+        UP(Linv, hp.Linv);
+        UP(LinvT, hp.LinvT);
+#undef UP
+        (void)d_int;
+        if ((rc = h->dalloc(&P.x, hp.nEL))) return rc;
+        if ((rc = h->dalloc(&P.y, hp.m))) return rc;
+        if ((rc = h->dalloc(&P.r, hp.nEL))) return rc;
+        if ((rc = h->dalloc(&P.rsw, hp.nEL))) return rc;
+        if ((rc = h->dalloc(&P.z1, hp.m))) return rc;
+        if ((rc = h->dalloc(&P.xk[0], hp.SL))) return rc;
+        if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
+        if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
+        if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
+        if ((rc = h->dalloc(&P.tpart, (size_t)hp.m * P.R))) return rc;
+        if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
+        if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas, P.pos_ctas) * 8))) return rc;
+        if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_ctas))) return rc;
+        if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
+        CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
+        CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+        guard.release();
+        *out = h;
+        rc = admm_reset(h, nullptr);
+        if (rc) {
+            delete h;
+            *out = nullptr;
+            return rc;
+        }
+        CK(cudaDeviceSynchronize());
+        return SDP_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(SDP_ERR_ARG, "host out of memory");
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_setup");
+    }
+}
+
+int sdp_set_opts(sdp_handle h, const admm_opts* opts) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->device));
+    const bool rebuild = opts->rho != h->opts.rho || opts->form != h->opts.form;
+    h->opts = *opts;
+    if (rebuild) {
+        rc = rebuild_r_if_primal(h, nullptr);
+        if (rc) return rc;
+        CK(cudaDeviceSynchronize());
+    }
+    return SDP_OK;
+}
+
+int admm_reset(sdp_handle h, void* cuda_stream) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = as_stream(cuda_stream);
+    IterPtrs& P = h->P;
+    CK(cudaMemsetAsync(P.x, 0, sizeof(double) * std::max(1, P.nEL), st));
+    CK(cudaMemsetAsync(P.y, 0, sizeof(double) * P.m, st));
+    CK(cudaMemsetAsync(P.z1, 0, sizeof(double) * P.m, st));
+    CK(cudaMemsetAsync(P.r, 0, sizeof(double) * std::max(1, P.nEL), st));
+    CK(cudaMemsetAsync(P.rsw, 0, sizeof(double) * std::max(1, P.nEL), st));
+    for (int i = 0; i < 2; ++i) CK(cudaMemsetAsync(P.xk[i], 0, sizeof(double) * std::max(1, P.SL), st));
+    CK(cudaMemsetAsync(P.lam, 0, sizeof(double) * std::max(1, P.SL), st));
+    CK(cudaMemsetAsync(P.vk, 0, sizeof(double) * std::max(1, P.SL), st));
+    CK(cadmm::launch_ctrl_reset(P.ctrl, st));
+    return rebuild_r_if_primal(h, st);
+}
+
+int admm_iterate(sdp_handle h, int n_iters, void* cuda_stream, admm_result* out) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    if (n_iters < 0) return set_err(SDP_ERR_ARG, "n_iters must be >= 0");
+    CK(cudaSetDevice(h->device));
+    try {
+        return run_iterations(h, n_iters, as_stream(cuda_stream), out);
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in admm_iterate");
+    }
+}
+
+int admm_solve(sdp_handle h, void* cuda_stream, admm_result* out) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    return admm_iterate(h, h->opts.max_iter, cuda_stream, out);
+}
+
+int sdp_get_sizes(sdp_handle h, sdp_sizes* out) {
+    if (!h || !out) return set_err(SDP_ERR_ARG, "NULL argument");
+    out->n = h->n; out->m = h->m; out->p = h->p; out->max_clique = h->smax;
+    out->nE_lower = h->nEL; out->S_lower = h->SL; out->nnz_A = h->nnz;
+    return SDP_OK;
+}
+
+int sdp_get_state(sdp_handle h, double* x, double* y, double* blk_a, double* blk_b, double* blk_c) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    Ctrl c{};
+    CK(cudaMemcpy(&c, h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    const IterPtrs& P = h->P;
+    const size_t sl = sizeof(double) * P.SL;
+    if (x) CK(cudaMemcpy(x, P.x, sizeof(double) * P.nEL, cudaMemcpyDeviceToHost));
+    if (y) CK(cudaMemcpy(y, P.y, sizeof(double) * P.m, cudaMemcpyDeviceToHost));
+    const double* a_src = h->opts.form == SDP_PRIMAL ? P.xk[c.iter & 1] : P.xk[0];
+    if (blk_a) CK(cudaMemcpy(blk_a, a_src, sl, cudaMemcpyDeviceToHost));
+    if (blk_b) CK(cudaMemcpy(blk_b, P.lam, sl, cudaMemcpyDeviceToHost));
+    if (blk_c) CK(cudaMemcpy(blk_c, P.vk, sl, cudaMemcpyDeviceToHost));
+    return SDP_OK;
+}
+
+int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* blk_a,
+                  const double* blk_b, const double* blk_c) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    Ctrl c{};
+    CK(cudaMemcpy(&c, h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    const IterPtrs& P = h->P;
+    const size_t sl = sizeof(double) * P.SL;
+    if (x) CK(cudaMemcpy(P.x, x, sizeof(double) * P.nEL, cudaMemcpyHostToDevice));
+    if (y) CK(cudaMemcpy(P.y, y, sizeof(double) * P.m, cudaMemcpyHostToDevice));
+    double* a_dst = h->opts.form == SDP_PRIMAL ? P.xk[c.iter & 1] : P.xk[0];
+    if (blk_a) CK(cudaMemcpy(a_dst, blk_a, sl, cudaMemcpyHostToDevice));
+    if (blk_b) CK(cudaMemcpy(P.lam, blk_b, sl, cudaMemcpyHostToDevice));
+    if (blk_c) CK(cudaMemcpy(P.vk, blk_c, sl, cudaMemcpyHostToDevice));
+    int rc = rebuild_r_if_primal(h, nullptr);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    return SDP_OK;
+}
+
+int sdp_get_solution(sdp_handle h, double* X_lower, double* y, double* Z_lower) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    const int nEL = h->nEL, m = h->m, SL = h->SL;
+    std::vector<double> x(nEL), ya(m), blk(SL);
+    int rc = sdp_get_state(h, x.data(), ya.data(), nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    const double rho = h->opts.rho;
+    if (X_lower) {
+        if (h->opts.form == SDP_PRIMAL) std::copy(x.begin(), x.end(), X_lower);
+        else for (int e = 0; e < nEL; ++e) X_lower[e] = -rho * x[e];
+    }
+    if (y) {
+        if (h->opts.form == SDP_PRIMAL) for (int i = 0; i < m; ++i) y[i] = -rho * ya[i];
+        else std::copy(ya.begin(), ya.end(), y);
+    }
+    if (Z_lower) {
+        // primal form: Z = sum_k H_k^T lambda_k; dual form: Z = sum_k H_k^T z_k
+        double* d_out = nullptr;
+        CK(cudaMalloc(&d_out, sizeof(double) * std::max(1, nEL)));
+        const IterPtrs& P = h->P;
+        Ctrl c{};
+        cudaError_t e = cudaMemcpy(&c, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+        const double* src = h->opts.form == SDP_PRIMAL ? P.lam : P.xk[0];
+        if (e == cudaSuccess) e = cadmm::launch_scatter(P, src, d_out, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpy(Z_lower, d_out, sizeof(double) * nEL, cudaMemcpyDeviceToHost);
+        cudaFree(d_out);
+        if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("sdp_get_solution: ") + cudaGetErrorString(e));
+    }
+    return SDP_OK;
+}
+
+int sdp_get_maps(sdp_handle h, int* pat_row, int* pat_col, long long* blk_off, int* gather_idx) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    if (pat_row) std::copy(h->pat_row.begin(), h->pat_row.end(), pat_row);
+    if (pat_col) std::copy(h->pat_col.begin(), h->pat_col.end(), pat_col);
+    if (blk_off) for (size_t k = 0; k < h->blk_off.size(); ++k) blk_off[k] = h->blk_off[k];
+    if (gather_idx) std::copy(h->gather_idx.begin(), h->gather_idx.end(), gather_idx);
+    return SDP_OK;
+}
+
+int sdp_gather(sdp_handle h, const double* x, double* blocks_out, void* cuda_stream) {
+    if (!h || !x || !blocks_out) return set_err(SDP_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cadmm::launch_gather(h->P, x, blocks_out, as_stream(cuda_stream)));
+    return SDP_OK;
+}
+
+int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stream) {
+    if (!h || !blocks || !out) return set_err(SDP_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cadmm::launch_scatter(h->P, blocks, out, as_stream(cuda_stream)));
+    return SDP_OK;
+}
+
+int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
+                        int count, int prec, void* cuda_stream) {
+    if (count < 0) return set_err(SDP_ERR_ARG, "count must be >= 0");
+    if (count == 0) return SDP_OK;
+    if (!in || !out || !sizes || !offsets) return set_err(SDP_ERR_ARG, "NULL argument");
+    if (prec != SDP_PROJ_FP64 && prec != SDP_PROJ_FP32) return set_err(SDP_ERR_ARG, "bad prec");
+    int smax = 0;
+    for (int k = 0; k < count; ++k) {
+        if (sizes[k] < 1) return set_err(SDP_ERR_ARG, "block sizes must be >= 1");
+        if (sizes[k] > SDP_MAX_CLIQUE) return set_err(SDP_ERR_UNSUPPORTED, "block larger than SDP_MAX_CLIQUE");
+        if (offsets[k] < 0) return set_err(SDP_ERR_ARG, "offsets must be >= 0");
+        smax = std::max(smax, sizes[k]);
+    }
+    // schedule: largest blocks first
+    std::vector<int> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
+    cudaStream_t st = as_stream(cuda_stream);
+    CK(cadmm::project_prepare());
+    // One stream-ordered device buffer holds order, sizes and offsets.
+    const size_t bytes = (size_t)count * (2 * sizeof(int) + sizeof(long long));
+    std::vector<unsigned char> host(bytes);
+    std::memcpy(host.data(), offsets, (size_t)count * sizeof(long long));
+    std::memcpy(host.data() + (size_t)count * sizeof(long long), sizes, (size_t)count * sizeof(int));
+    std::memcpy(host.data() + (size_t)count * (sizeof(long long) + sizeof(int)), order.data(),
+                (size_t)count * sizeof(int));
+    void* d = nullptr;
+    CK(cudaMallocAsync(&d, bytes, st));
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        cadmm::ProjArgs a{};
+        a.off = static_cast<const long long*>(d);
+        a.size = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) + (size_t)count * sizeof(long long));
+        a.order = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) +
+                                               (size_t)count * (sizeof(long long) + sizeof(int)));
+        a.count = count;
+        a.rho = 1.0;
+        a.in = in;
+        a.out = out;
+        a.ctrl = nullptr;
+        e = cadmm::launch_project(a, cadmm::PROJ_PLAIN, prec, smax, st);
+    }
+    // The pageable host copy above returns once the data is staged, so `host` may go away.
+    const cudaError_t fe = cudaFreeAsync(d, st);
+    if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("project_psd_batched: ") + cudaGetErrorString(e));
+    if (fe != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(fe));
+    return SDP_OK;
+}
+
+int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out) {
+    if (!h || reps < 1 || !ms_out) return set_err(SDP_ERR_ARG, "bad argument");
+    const int count = cadmm::iteration_kernel_count(h->opts.form);
+    if (max_out < count) return set_err(SDP_ERR_ARG, "ms_out too small");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = as_stream(cuda_stream);
+    std::vector<cudaEvent_t> ev(count + 1);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    std::vector<double> acc(count, 0.0);
+    int rc = SDP_OK;
+    cudaError_t ce = cadmm::launch_ctrl_arm(h->P.ctrl, reps, 0.0, st);
+    for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
+        ce = cadmm::launch_iteration(h->P, h->opts.form, h->opts.prec, h->opts.rho, st, ev.data());
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(ev[count]);
+        for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+            float ms = 0.f;
+            ce = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (ce != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("sdp_time_phases: ") + cudaGetErrorString(ce));
+    for (int i = 0; i < count; ++i) ms_out[i] = acc[i] / reps;
+    (void)rc;
+    return count;
+}
+
+const char* sdp_phase_name(int form, int i) { return cadmm::phase_name(form, i); }
+
+void sdp_free(sdp_handle h) { delete h; }
+
+const char* sdp_status_string(int status) {
+    switch (status) {
+        case SDP_OK: return "converged / success";
+        case SDP_MAX_ITER: return "iteration budget reached without convergence";
+        case SDP_ERR_ARG: return "bad argument";
+        case SDP_ERR_CLIQUE: return "cliques unsorted or not covering a data nonzero";
+        case SDP_ERR_NOT_PD: return "A D^-1 A^T not positive definite (A rank-deficient)";
+        case SDP_ERR_CUDA: return "CUDA error";
+        case SDP_ERR_NAN: return "NaN/Inf in residuals or objective";
+        case SDP_ERR_TIMEOUT: return "timed out waiting for the device";
+        case SDP_ERR_UNSUPPORTED: return "size beyond the supported limits";
+        default: return "unknown status";
+    }
+}
+
+const char* sdp_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

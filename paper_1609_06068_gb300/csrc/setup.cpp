@@ -1,0 +1,279 @@
+// Host setup of the decomposed problem (Algorithms 1-2, "Setup: chordal decomposition, KKT
+// factorization"): clique index maps, D, A on the lower pattern, and the cached factor of A D^-1 A^T.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "sdp_internal.h"
+
+namespace cadmm {
+
+namespace {
+
+inline long long key_of(long long row, long long col, long long n) { return col * n + row; }
+
+int fail(std::string& err, int code, const std::string& msg) {
+    err = msg;
+    return code;
+}
+
+// Lower E_L index of (row, col), row >= col; -1 when the pair is not in the pattern.
+inline long long find_entry(const std::vector<long long>& keys, long long k) {
+    auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    if (it == keys.end() || *it != k) return -1;
+    return (long long)(it - keys.begin());
+}
+
+}  // namespace
+
+int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
+                       const double* A_val, const double* b, long long C_nnz, const int* C_row,
+                       const int* C_col, const double* C_val, long long pat_nnz,
+                       const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
+                       const int* clique_vtx, HostProblem& hp, std::string& err) {
+    if (n <= 0 || m < 1 || p < 1 || !A_ptr || !b || !clique_ptr || !clique_vtx)
+        return fail(err, SDP_ERR_ARG, "n, m, p must be positive and A_ptr, b, cliques non-NULL");
+    if (m > SDP_MAX_CONSTRAINTS)
+        return fail(err, SDP_ERR_UNSUPPORTED, "m exceeds SDP_MAX_CONSTRAINTS");
+    if (C_nnz < 0 || pat_nnz < 0 || (C_nnz > 0 && (!C_row || !C_col || !C_val)) ||
+        (pat_nnz > 0 && (!pat_row || !pat_col)))
+        return fail(err, SDP_ERR_ARG, "bad C or pattern arrays");
+    if (A_ptr[0] != 0) return fail(err, SDP_ERR_ARG, "A_ptr[0] must be 0");
+    for (int i = 0; i < m; ++i)
+        if (A_ptr[i + 1] < A_ptr[i]) return fail(err, SDP_ERR_ARG, "A_ptr must be non-decreasing");
+    if (A_ptr[m] > 0 && (!A_row || !A_col || !A_val))
+        return fail(err, SDP_ERR_ARG, "A coordinate arrays are NULL");
+
+    hp = HostProblem();
+    hp.n = n;
+    hp.m = m;
+    hp.p = p;
+
+    // ---- cliques: E_k sorts vertices in natural order (Section II.B)
+    if (clique_ptr[0] != 0) return fail(err, SDP_ERR_CLIQUE, "clique_ptr[0] must be 0");
+    long long SL = 0;
+    hp.blk_size.resize(p);
+    hp.blk_off.resize(p + 1);
+    for (int k = 0; k < p; ++k) {
+        const int lo = clique_ptr[k], hi = clique_ptr[k + 1];
+        const int s = hi - lo;
+        if (s < 1) return fail(err, SDP_ERR_CLIQUE, "empty clique");
+        if (s > SDP_MAX_CLIQUE) return fail(err, SDP_ERR_UNSUPPORTED, "clique larger than SDP_MAX_CLIQUE");
+        for (int a = lo; a < hi; ++a) {
+            if (clique_vtx[a] < 0 || clique_vtx[a] >= n)
+                return fail(err, SDP_ERR_CLIQUE, "clique vertex out of range");
+            if (a > lo && clique_vtx[a] <= clique_vtx[a - 1])
+                return fail(err, SDP_ERR_CLIQUE, "clique vertices must be strictly ascending");
+        }
+        hp.blk_size[k] = s;
+        hp.blk_off[k] = (int)SL;
+        SL += (long long)s * (s + 1) / 2;
+        if (SL >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "packed block length >= 2^31");
+        hp.smax = std::max(hp.smax, s);
+    }
+    hp.blk_off[p] = (int)SL;
+    hp.SL = (int)SL;
+
+    // Processing order: largest cliques first (stable), so the longest eigensolves start first.
+    hp.order.resize(p);
+    std::iota(hp.order.begin(), hp.order.end(), 0);
+    std::stable_sort(hp.order.begin(), hp.order.end(),
+                     [&](int x, int y) { return hp.blk_size[x] > hp.blk_size[y]; });
+
+    // ---- lower pattern E_L = union of lower clique pairs, column-major (key = col*n + row).
+    // Packed positions are enumerated in storage order: clique, column b, rows a >= b.
+    std::vector<long long> pos_key(SL);
+    hp.pos_w.resize(SL);
+    {
+        long long q = 0;
+        for (int k = 0; k < p; ++k) {
+            const int* v = clique_vtx + clique_ptr[k];
+            const int s = hp.blk_size[k];
+            for (int bb = 0; bb < s; ++bb)
+                for (int a = bb; a < s; ++a, ++q) {
+                    pos_key[q] = key_of(v[a], v[bb], n);
+                    hp.pos_w[q] = (a == bb) ? 1 : 2;
+                }
+        }
+    }
+    std::vector<long long> keys(pos_key);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    if ((long long)keys.size() >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
+    const int nEL = (int)keys.size();
+    hp.nEL = nEL;
+    hp.pat_row.resize(nEL);
+    hp.pat_col.resize(nEL);
+    hp.ew.resize(nEL);
+    for (int e = 0; e < nEL; ++e) {
+        hp.pat_row[e] = (int)(keys[e] % n);
+        hp.pat_col[e] = (int)(keys[e] / n);
+        hp.ew[e] = hp.pat_row[e] == hp.pat_col[e] ? 1 : 2;
+    }
+
+    // ---- H_k as a gather map, and its transpose as a CSR scatter map with ascending k.
+    hp.gather_idx.resize(SL);
+    std::vector<int> cnt(nEL + 1, 0);
+    for (long long q = 0; q < SL; ++q) {
+        const long long e = find_entry(keys, pos_key[q]);
+        hp.gather_idx[q] = (int)e;
+        cnt[e + 1]++;
+    }
+    hp.sc_ptr.resize(nEL + 1);
+    hp.sc_ptr[0] = 0;
+    for (int e = 0; e < nEL; ++e) hp.sc_ptr[e + 1] = hp.sc_ptr[e] + cnt[e + 1];
+    hp.sc_pos.resize(SL);
+    {
+        std::vector<int> fillp(hp.sc_ptr.begin(), hp.sc_ptr.end() - 1);
+        for (long long q = 0; q < SL; ++q) hp.sc_pos[fillp[hp.gather_idx[q]]++] = (int)q;
+    }
+    // D = sum_k H_k^T H_k (Section III.B.1): number of cliques covering each entry.
+    hp.D.resize(nEL);
+    hp.wdinv.resize(nEL);
+    for (int e = 0; e < nEL; ++e) {
+        hp.D[e] = (double)(hp.sc_ptr[e + 1] - hp.sc_ptr[e]);
+        hp.wdinv[e] = (double)hp.ew[e] / hp.D[e];
+    }
+
+    // ---- cost c on E_L; every data nonzero must lie in a clique block.
+    hp.c.assign(nEL, 0.0);
+    for (long long t = 0; t < C_nnz; ++t) {
+        const long long r = C_row[t], cc = C_col[t];
+        if (r < 0 || r >= n || cc < 0 || cc >= n) return fail(err, SDP_ERR_ARG, "C index out of range");
+        if (r < cc) return fail(err, SDP_ERR_ARG, "C must be given as lower coordinates (row >= col)");
+        const long long e = find_entry(keys, key_of(r, cc, n));
+        if (e < 0) {
+            if (C_val[t] == 0.0) continue;
+            return fail(err, SDP_ERR_CLIQUE, "a nonzero of C is not covered by the cliques");
+        }
+        hp.c[e] += C_val[t];
+    }
+    for (long long t = 0; t < pat_nnz; ++t) {
+        const long long r = pat_row[t], cc = pat_col[t];
+        if (r < 0 || r >= n || cc < 0 || cc >= n || r < cc)
+            return fail(err, SDP_ERR_ARG, "pattern coordinates out of range or not lower");
+        if (find_entry(keys, key_of(r, cc, n)) < 0)
+            return fail(err, SDP_ERR_CLIQUE, "a pattern entry is not covered by the cliques");
+    }
+    hp.b.assign(b, b + m);
+
+    // ---- A on E_L: CSR by constraint (duplicates merged), then CSC by entry.
+    hp.a_rowptr.assign(m + 1, 0);
+    std::vector<std::pair<int, double>> row;
+    for (int i = 0; i < m; ++i) {
+        row.clear();
+        for (long long t = A_ptr[i]; t < A_ptr[i + 1]; ++t) {
+            const long long r = A_row[t], cc = A_col[t];
+            if (r < 0 || r >= n || cc < 0 || cc >= n) return fail(err, SDP_ERR_ARG, "A index out of range");
+            if (r < cc) return fail(err, SDP_ERR_ARG, "A must be given as lower coordinates (row >= col)");
+            const long long e = find_entry(keys, key_of(r, cc, n));
+            if (e < 0) {
+                if (A_val[t] == 0.0) continue;
+                return fail(err, SDP_ERR_CLIQUE, "a nonzero of A is not covered by the cliques");
+            }
+            row.emplace_back((int)e, A_val[t]);
+        }
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
+        size_t w = 0;
+        for (size_t t = 0; t < row.size(); ++t) {
+            if (w > 0 && row[w - 1].first == row[t].first) row[w - 1].second += row[t].second;
+            else row[w++] = row[t];
+        }
+        for (size_t t = 0; t < w; ++t) {
+            if (row[t].second == 0.0) continue;
+            hp.a_col.push_back(row[t].first);
+            hp.a_val.push_back(row[t].second);
+        }
+        if ((long long)hp.a_col.size() >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "nnz(A) >= 2^31");
+        hp.a_rowptr[i + 1] = (int)hp.a_col.size();
+    }
+    hp.nnz = (long long)hp.a_col.size();
+    hp.c_colptr.assign(nEL + 1, 0);
+    for (long long t = 0; t < hp.nnz; ++t) hp.c_colptr[hp.a_col[t] + 1]++;
+    for (int e = 0; e < nEL; ++e) hp.c_colptr[e + 1] += hp.c_colptr[e];
+    hp.c_row.resize(hp.nnz);
+    hp.c_val.resize(hp.nnz);
+    {
+        std::vector<int> fillp(hp.c_colptr.begin(), hp.c_colptr.end() - 1);
+        for (int i = 0; i < m; ++i)
+            for (int t = hp.a_rowptr[i]; t < hp.a_rowptr[i + 1]; ++t) {
+                const int q = fillp[hp.a_col[t]]++;
+                hp.c_row[q] = (unsigned short)i;
+                hp.c_val[q] = hp.a_val[t];
+            }
+    }
+
+    // ---- M = A D^-1 A^T on the full symmetric vectors: M_ij = sum_e w_e A_ie A_je / D_e, with
+    // w_e = 2 off the diagonal (both (i,j) and (j,i) of the pattern) and 1 on it. Columns are
+    // split into a fixed number of chunks so the sum order does not depend on the machine.
+    const size_t mm = (size_t)m * m;
+    std::vector<double> M(mm, 0.0);
+    {
+        const int chunks = (m <= 2048) ? 16 : 1;
+        std::vector<std::vector<double>> part(chunks);
+        auto work = [&](int ch) {
+            std::vector<double>& Mp = part[ch];
+            Mp.assign(mm, 0.0);
+            const long long e0 = (long long)nEL * ch / chunks, e1 = (long long)nEL * (ch + 1) / chunks;
+            for (long long e = e0; e < e1; ++e) {
+                const double wd = hp.wdinv[e];
+                const int lo = hp.c_colptr[e], hi = hp.c_colptr[e + 1];
+                for (int s1 = lo; s1 < hi; ++s1) {
+                    const double vi = wd * hp.c_val[s1];
+                    double* Mi = Mp.data() + (size_t)hp.c_row[s1] * m;
+                    for (int s2 = lo; s2 <= s1; ++s2) Mi[hp.c_row[s2]] += vi * hp.c_val[s2];
+                }
+            }
+        };
+        const unsigned hw = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)chunks));
+        for (int base = 0; base < chunks; base += (int)hw) {
+            std::vector<std::thread> th;
+            for (int ch = base; ch < std::min(chunks, base + (int)hw); ++ch) th.emplace_back(work, ch);
+            for (auto& t : th) t.join();
+        }
+        for (int ch = 0; ch < chunks; ++ch)
+            for (size_t q = 0; q < mm; ++q) M[q] += part[ch][q];
+    }
+
+    // ---- Cholesky M = L L^T (row-major lower, in place). A pivot at or below 1e-12 of the
+    // original diagonal means A has (numerically) dependent rows.
+    std::vector<double> L(mm, 0.0);
+    for (int j = 0; j < m; ++j) {
+        const double* Lj = L.data() + (size_t)j * m;
+        double d = M[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
+        if (!(d > 1e-12 * M[(size_t)j * m + j]) || !std::isfinite(d))
+            return fail(err, SDP_ERR_NOT_PD, "A D^-1 A^T is not positive definite (A rank-deficient)");
+        const double ljj = std::sqrt(d);
+        L[(size_t)j * m + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double* Li = L.data() + (size_t)i * m;
+            double s = M[(size_t)i * m + j];
+            for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+            Li[j] = s / ljj;
+        }
+    }
+    // ---- L^-1 (lower) by forward substitution on the unit vectors, and its transpose.
+    hp.Linv.assign(mm, 0.0);
+    std::vector<double> xcol(m);
+    for (int j = 0; j < m; ++j) {
+        std::fill(xcol.begin(), xcol.end(), 0.0);
+        xcol[j] = 1.0 / L[(size_t)j * m + j];
+        for (int i = j + 1; i < m; ++i) {
+            const double* Li = L.data() + (size_t)i * m;
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s += Li[k] * xcol[k];
+            xcol[i] = -s / Li[i];
+        }
+        for (int i = j; i < m; ++i) hp.Linv[(size_t)i * m + j] = xcol[i];
+    }
+    hp.LinvT.assign(mm, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) hp.LinvT[(size_t)j * m + i] = hp.Linv[(size_t)i * m + j];
+    return SDP_OK;
+}
+
+}  // namespace cadmm

@@ -1,0 +1,124 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every function the header
+declares, and its host-side validation rejects bad input before touching a GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1609_06068_gb300 as cadmm
+from paper_1609_06068_gb300 import build as cbuild
+from tests import sdp_cases
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "chordal_admm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(cadmm.LIB_PATH):
+        cbuild.build()
+    return cadmm.load_library()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+def test_header_declares_the_binding_names():
+    assert header_functions() == sorted(cadmm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert cadmm.sdp_status_string(code) != "unknown status"
+    assert cadmm.sdp_status_string(42) == "unknown status"
+
+
+def _arrays():
+    return sdp_cases.random_block_arrow(l=3, d=2, h=2, m=4)
+
+
+def _setup_rc(arrs, opts=None, cliques=None):
+    """Call sdp_setup directly and return (rc, handle); only host validation may run."""
+    lib = cadmm.load_library()
+    cl = cliques if cliques is not None else arrs["cliques"]
+    sizes = np.array([len(c) for c in cl])
+    ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    vtx = np.concatenate(cl).astype(np.int32)
+    A_ptr = np.asarray(arrs["A_ptr"], np.int64)
+    A_row = np.asarray(arrs["A_row"], np.int32); A_col = np.asarray(arrs["A_col"], np.int32)
+    A_val = np.asarray(arrs["A_val"], np.float64); b = np.asarray(arrs["b"], np.float64)
+    C_row = np.asarray(arrs["C_row"], np.int32); C_col = np.asarray(arrs["C_col"], np.int32)
+    C_val = np.asarray(arrs["C_val"], np.float64)
+    o = opts if opts is not None else cadmm.make_opts()
+    h = ctypes.c_void_p()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    rc = lib.sdp_setup(arrs["n"], len(b), P(A_ptr), P(A_row), P(A_col), P(A_val), P(b),
+                       len(C_val), P(C_row), P(C_col), P(C_val), 0, None, None,
+                       len(cl), P(ptr), P(vtx), ctypes.byref(o), ctypes.byref(h))
+    return rc, h
+
+
+def test_setup_rejects_bad_options(lib):
+    arrs = _arrays()
+    assert _setup_rc(arrs, opts=cadmm.make_opts(rho=0.0))[0] == cadmm.SDP_ERR_ARG
+    assert _setup_rc(arrs, opts=cadmm.make_opts(rho=-1.0))[0] == cadmm.SDP_ERR_ARG
+    assert _setup_rc(arrs, opts=cadmm.make_opts(form=7))[0] == cadmm.SDP_ERR_ARG
+    assert _setup_rc(arrs, opts=cadmm.make_opts(prec=3))[0] == cadmm.SDP_ERR_ARG
+    assert _setup_rc(arrs, opts=cadmm.make_opts(max_iter=-1))[0] == cadmm.SDP_ERR_ARG
+
+
+def test_setup_rejects_bad_cliques(lib):
+    arrs = _arrays()
+    rc, _ = _setup_rc(arrs, cliques=[c[::-1] for c in arrs["cliques"]])
+    assert rc == cadmm.SDP_ERR_CLIQUE and "ascending" in cadmm.sdp_last_error()
+    rc, _ = _setup_rc(arrs, cliques=arrs["cliques"][:-1])
+    assert rc == cadmm.SDP_ERR_CLIQUE and "not covered" in cadmm.sdp_last_error()
+    big = [np.arange(cadmm.SDP_MAX_CLIQUE + 1, dtype=np.int32)]
+    arrs_big = dict(arrs, n=cadmm.SDP_MAX_CLIQUE + 1)
+    assert _setup_rc(arrs_big, cliques=big)[0] == cadmm.SDP_ERR_UNSUPPORTED
+
+
+def test_setup_rejects_rank_deficient_A(lib):
+    arrs = _arrays()
+    k0 = int(arrs["A_ptr"][1])
+    bad = dict(arrs)
+    bad["A_ptr"] = np.concatenate([arrs["A_ptr"], [arrs["A_ptr"][-1] + k0]])
+    bad["A_row"] = np.concatenate([arrs["A_row"], arrs["A_row"][:k0]])
+    bad["A_col"] = np.concatenate([arrs["A_col"], arrs["A_col"][:k0]])
+    bad["A_val"] = np.concatenate([arrs["A_val"], arrs["A_val"][:k0]])
+    bad["b"] = np.concatenate([arrs["b"], arrs["b"][:1]])
+    assert _setup_rc(bad)[0] == cadmm.SDP_ERR_NOT_PD
+
+
+def test_setup_rejects_upper_coordinates(lib):
+    arrs = _arrays()
+    bad = dict(arrs)
+    bad["C_row"], bad["C_col"] = arrs["C_col"], arrs["C_row"]
+    off = np.asarray(arrs["C_row"]) != np.asarray(arrs["C_col"])
+    assert off.any()
+    assert _setup_rc(bad)[0] == cadmm.SDP_ERR_ARG
+
+
+def test_project_batched_validates_on_host(lib):
+    f = lib.project_psd_batched
+    sizes = np.array([3, 0], np.int32)
+    offs = np.array([0, 6], np.int64)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    dummy = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    assert f(dummy, dummy, P(sizes), P(offs), 2, 0, None) == cadmm.SDP_ERR_ARG
+    sizes = np.array([cadmm.SDP_MAX_CLIQUE + 1], np.int32)
+    assert f(dummy, dummy, P(sizes), P(offs[:1]), 1, 0, None) == cadmm.SDP_ERR_UNSUPPORTED
+    assert f(dummy, dummy, P(sizes), P(offs[:1]), 1, 5, None) == cadmm.SDP_ERR_ARG
+    assert f(None, None, None, None, 0, 0, None) == cadmm.SDP_OK

@@ -1,0 +1,92 @@
+"""GPU parity of the batched PSD projection (Eqs. XkUpdate, zkUpdate) against the oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import chordal_admm as orc
+from tests.gpu_support import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 3, 5, 12, 15, 16, 17, 30, 31, 32, 33, 40, 60, 64, 95, 96]
+
+
+def packed(W):
+    s = W.shape[0]
+    return np.concatenate([W[j:, j] for j in range(s)])
+
+
+def unpacked(v, s):
+    W = np.zeros((s, s))
+    pos = 0
+    for j in range(s):
+        W[j:, j] = v[pos:pos + s - j]
+        W[j, j:] = v[pos:pos + s - j]
+        pos += s - j
+    return W
+
+
+def special_blocks(rng):
+    out = []
+    out.append(np.zeros((7, 7)))                                  # zero
+    out.append(np.diag(rng.standard_normal(9)))                   # diagonal
+    out.append(3.0 * np.eye(8))                                   # repeated eigenvalue, PSD
+    out.append(-2.0 * np.eye(6))                                  # NSD
+    g = rng.standard_normal(11); out.append(np.outer(g, g))       # rank one
+    G = rng.standard_normal((13, 13)); out.append(-(G @ G.T))     # NSD dense
+    W = rng.standard_normal((10, 10)); out.append((W + W.T) * 1e-20)   # tiny scale
+    W = rng.standard_normal((10, 10)); out.append((W + W.T) * 1e20)    # huge scale
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 20)))
+    ev = np.repeat([2.0, -1.0, 0.0, 5.0], 5)                      # clustered spectrum
+    out.append((Q * ev) @ Q.T)
+    return out
+
+
+def batch(rng):
+    blocks = []
+    for s in SIZES:
+        W = rng.standard_normal((s, s)) * 10.0
+        blocks.append((W + W.T) / 2)
+    blocks += special_blocks(rng)
+    return blocks
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_project_matches_oracle(prec, tol):
+    torch, cadmm = require_gpu()
+    rng = np.random.default_rng(42)
+    blocks = batch(rng)
+    sizes = np.array([b.shape[0] for b in blocks], np.int32)
+    lens = sizes.astype(np.int64) * (sizes + 1) // 2
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = np.concatenate([packed(b) for b in blocks])
+    inp = torch.tensor(flat, device="cuda")
+    out = torch.full_like(inp, np.nan)
+    cadmm.project_psd_batched(inp, out, sizes, offs, prec=prec)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k, W in enumerate(blocks):
+        s = W.shape[0]
+        P = unpacked(got[offs[k]:offs[k] + lens[k]], s)
+        ref = orc.proj_psd(W)
+        nW = max(np.linalg.norm(W), 1e-300)
+        err = np.linalg.norm(P - ref) / nW
+        assert err <= tol, (k, s, prec, err)
+        if np.linalg.norm(W) > 0:
+            assert np.linalg.eigvalsh(P)[0] >= -tol * nW
+
+
+def test_project_in_place_and_empty():
+    torch, cadmm = require_gpu()
+    rng = np.random.default_rng(7)
+    W = rng.standard_normal((30, 30)); W = W + W.T
+    v = torch.tensor(np.concatenate([packed(W), packed(-W)]), device="cuda")
+    sizes = np.array([30, 30], np.int32)
+    offs = np.array([0, 465], np.int64)
+    cadmm.project_psd_batched(v, v, sizes, offs, prec="fp64")
+    torch.cuda.synchronize()
+    got = v.cpu().numpy()
+    # Moreau: W = P(W) - P(-W)
+    np.testing.assert_allclose(unpacked(got[:465], 30) - unpacked(got[465:], 30), W,
+                               atol=1e-12 * np.linalg.norm(W))
+    cadmm.project_psd_batched(v, v, np.zeros(0, np.int32), np.zeros(0, np.int64))
