@@ -171,11 +171,11 @@ def kernel_model(name, inst_sizes, cfg, prec):
         return "hbm", nnz * 10.0 + (nEL + 1) * 4.0 + nEL * (8 * 3 + 1) + m * 8.0, "byte"
     if name in ("tri_lower", "tri_upper"):
         return "hbm", m * (m + 1) / 2 * 8.0 + 2 * m * 8.0, "byte"
-    if name == "scatter_dual":
+    if name.startswith("scatter_dual"):
         return "hbm", SL * (8 * 2 + 4) + nEL * (4 + 8 + 8 * 2 + 8 + 1), "byte"
-    if name == "scatter_primal":
+    if name.startswith("scatter_primal"):
         return "hbm", SL * (8 * 3 + 4) + nEL * (4 + 8 + 8 * 2 + 8 + 1), "byte"
-    if name == "update_dual":
+    if name.startswith("update_dual"):
         return "hbm", SL * (8 * 4 + 4 + 1 + 8 * 2), "byte"
     return "hbm", 0.0, "byte"
 
@@ -335,13 +335,15 @@ def run_ours(args):
     fp32_iters_per_solve = iters / args.steps
 
     # FP64 eigensolves on the same instance (the plain baseline of the metric)
-    solver.set_opts(prec="fp64")
-    it64, ms64, _, last64 = timed_solves(args.fp64_steps)
-    fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=UNIT, time_to_tol_ms=sum(ms64) / args.fp64_steps,
-                iters_per_solve=it64 / args.fp64_steps, obj_dual=last64["obj_dual"],
-                obj_primal=last64["obj_primal"], status=last64["status"])
-    phases64 = cadmm.sdp_time_phases(solver.h, reps=5, stream=stream)
-    solver.set_opts(prec="fp32")
+    fp64, phases64 = None, None
+    if args.fp64_steps > 0:
+        solver.set_opts(prec="fp64")
+        it64, ms64, _, last64 = timed_solves(args.fp64_steps)
+        fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=UNIT, time_to_tol_ms=sum(ms64) / args.fp64_steps,
+                    iters_per_solve=it64 / args.fp64_steps, obj_dual=last64["obj_dual"],
+                    obj_primal=last64["obj_primal"], status=last64["status"])
+        phases64 = cadmm.sdp_time_phases(solver.h, reps=5, stream=stream)
+        solver.set_opts(prec="fp32")
     phases = cadmm.sdp_time_phases(solver.h, reps=50, stream=stream)
 
     peaks = {}
@@ -375,11 +377,14 @@ def run_ours(args):
         e2e_s += time.perf_counter() - t0
         e2e_iters += r2["iters"]
         d2h = X.nbytes + y.nbytes + Z.nbytes + 64
-    e2e_iters_all = reduce(world, e2e_iters, "sum")
-    e2e_s_max = reduce(world, e2e_s, "max")
-    e2e = dict(value=e2e_iters_all / e2e_s_max, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-               ms_per_step=1e3 * e2e_s_max / args.e2e_steps,
-               includes="sdp_setup (host maps, A D^-1 A^T, Cholesky, upload) + admm_solve + sdp_get_solution")
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_iters_all = reduce(world, e2e_iters, "sum")
+        e2e_s_max = reduce(world, e2e_s, "max")
+        e2e = dict(value=e2e_iters_all / e2e_s_max, unit=UNIT, h2d_bytes_per_step=h2d,
+                   d2h_bytes_per_step=d2h, ms_per_step=1e3 * e2e_s_max / args.e2e_steps,
+                   includes="sdp_setup (host maps, A D^-1 A^T, Cholesky, upload) + admm_solve + "
+                            "sdp_get_solution")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -396,7 +401,8 @@ def run_ours(args):
                         l2="256 MiB buffer written before every timed solve", parallelism=f"replicas x{world}"),
             time_to_tol_ms=ms_per_step, iters_per_solve=fp32_iters_per_solve,
             obj_dual=last["obj_dual"], obj_primal=last["obj_primal"], status=last["status"],
-            fp64_plain=fp64, speedup_fp32_vs_fp64_time_to_tol=fp64["time_to_tol_ms"] / ms_per_step,
+            fp64_plain=fp64,
+            speedup_fp32_vs_fp64_time_to_tol=(fp64["time_to_tol_ms"] / ms_per_step) if fp64 else None,
             phases_ms_fp32=phases, phases_ms_fp64=phases64,
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks,
             gpu=torch.cuda.get_device_name(local))

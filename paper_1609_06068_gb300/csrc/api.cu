@@ -263,11 +263,12 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
             P.R = (int)std::max<long long>(1, std::min<long long>(R, 64));
         }
         P.ent_ctas = (hp.nEL + 255) / 256;
+        P.n_heavy = (int)hp.heavy.size();
+        P.heavy_ctas = (P.n_heavy + 7) / 8;
         P.pos_ctas = (hp.SL + 255) / 256;
         P.col_ctas = std::max(1, std::min(num_sms * kColCtasPerSm, (hp.nEL + 31) / 32));
 
         std::vector<long long> off64(hp.blk_off.begin(), hp.blk_off.end());
-        int* d_int = nullptr;
 #define UP(field, vec)                                             \
     do {                                                           \
         auto* tmp_ = const_cast<std::remove_const_t<std::remove_pointer_t<decltype(P.field)>>*>(P.field); \
@@ -278,12 +279,15 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         UP(blk_off, hp.blk_off);
         UP(blk_off64, off64);
         UP(blk_size, hp.blk_size);
+        UP(voff, hp.voff);
         UP(order, hp.order);
         UP(gather_idx, hp.gather_idx);
         UP(pos_w, hp.pos_w);
         UP(sc_ptr, hp.sc_ptr);
         UP(sc_pos, hp.sc_pos);
+        UP(heavy, hp.heavy);
         UP(D, hp.D);
+        UP(dinv, hp.dinv);
         UP(wdinv, hp.wdinv);
         UP(c, hp.c);
         UP(b, hp.b);
@@ -297,7 +301,6 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         UP(Linv, hp.Linv);
         UP(LinvT, hp.LinvT);
 #undef UP
-        (void)d_int;
         if ((rc = h->dalloc(&P.x, hp.nEL))) return rc;
         if ((rc = h->dalloc(&P.y, hp.m))) return rc;
         if ((rc = h->dalloc(&P.r, hp.nEL))) return rc;
@@ -309,9 +312,14 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
         if ((rc = h->dalloc(&P.tpart, (size_t)hp.m * P.R))) return rc;
         if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
-        if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas, P.pos_ctas) * 8))) return rc;
+        if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas + P.heavy_ctas, P.pos_ctas) * 8))) return rc;
         if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_ctas))) return rc;
         if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
+        {
+            double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
+            if ((rc = h->dalloc(&vs, (size_t)hp.voff[hp.p]))) return rc;
+            P.vstore = vs;
+        }
         CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
         CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
@@ -339,12 +347,14 @@ int sdp_set_opts(sdp_handle h, const admm_opts* opts) {
     if (rc) return rc;
     CK(cudaSetDevice(h->device));
     const bool rebuild = opts->rho != h->opts.rho || opts->form != h->opts.form;
+    const bool new_prec = opts->prec != h->opts.prec;
     h->opts = *opts;
+    if (new_prec) CK(cadmm::launch_vstore_identity(h->P, h->opts.prec, nullptr));
     if (rebuild) {
         rc = rebuild_r_if_primal(h, nullptr);
         if (rc) return rc;
-        CK(cudaDeviceSynchronize());
     }
+    if (rebuild || new_prec) CK(cudaDeviceSynchronize());
     return SDP_OK;
 }
 
@@ -362,6 +372,7 @@ int admm_reset(sdp_handle h, void* cuda_stream) {
     CK(cudaMemsetAsync(P.lam, 0, sizeof(double) * std::max(1, P.SL), st));
     CK(cudaMemsetAsync(P.vk, 0, sizeof(double) * std::max(1, P.SL), st));
     CK(cadmm::launch_ctrl_reset(P.ctrl, st));
+    CK(cadmm::launch_vstore_identity(P, h->opts.prec, st));
     return rebuild_r_if_primal(h, st);
 }
 
@@ -420,6 +431,7 @@ int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* 
     if (blk_a) CK(cudaMemcpy(a_dst, blk_a, sl, cudaMemcpyHostToDevice));
     if (blk_b) CK(cudaMemcpy(P.lam, blk_b, sl, cudaMemcpyHostToDevice));
     if (blk_c) CK(cudaMemcpy(P.vk, blk_c, sl, cudaMemcpyHostToDevice));
+    CK(cadmm::launch_vstore_identity(P, h->opts.prec, nullptr));
     int rc = rebuild_r_if_primal(h, nullptr);
     if (rc) return rc;
     CK(cudaDeviceSynchronize());
@@ -538,7 +550,6 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
     std::vector<cudaEvent_t> ev(count + 1);
     for (auto& e : ev) CK(cudaEventCreate(&e));
     std::vector<double> acc(count, 0.0);
-    int rc = SDP_OK;
     cudaError_t ce = cadmm::launch_ctrl_arm(h->P.ctrl, reps, 0.0, st);
     for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
         ce = cadmm::launch_iteration(h->P, h->opts.form, h->opts.prec, h->opts.rho, st, ev.data());
@@ -552,7 +563,6 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
     for (auto& e : ev) cudaEventDestroy(e);
     if (ce != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("sdp_time_phases: ") + cudaGetErrorString(ce));
     for (int i = 0; i < count; ++i) ms_out[i] = acc[i] / reps;
-    (void)rc;
     return count;
 }
 

@@ -6,7 +6,9 @@
 //   spmv_cols    x = (r - A^T y) / D       (second pass over A; CSC)
 //   update_dual  v_k = z_k + rho^-1 lambda_k + H_k x, lambda_k = -rho H_k x (Eqs. vkEqn,
 //                DualMultUpdate with the sign Eq. MultUpdateDualSDP implies)
-//   finalize     residuals, objectives, stop test (one CTA, fixed-order reductions)
+// The residuals, objectives and stop test of an iteration are computed by the last CTA to finish
+// the iteration's final kernel (scatter in the primal form, update in the dual form), reading
+// every partial sum in a fixed order.
 // Every kernel starts by reading the device control block and returns at once when the solve is
 // done, so a captured graph holding several iterations can run past convergence at no cost.
 // All reductions use a fixed tree, so results are bitwise reproducible run to run.
@@ -50,13 +52,83 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- residuals and stop test
+// Run by one whole CTA (the last to finish the iteration's final kernel).
+__device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int n_part) {
+    __shared__ double red[33 * 7];
+    Ctrl* C = P.ctrl;
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (form == SDP_PRIMAL) {
+        for (int k = threadIdx.x; k < P.p; k += blockDim.x) {
+            v[0] += P.part_blk[k * 4 + 0];
+            v[1] += P.part_blk[k * 4 + 1];
+            v[2] += P.part_blk[k * 4 + 2];
+        }
+        for (int q = threadIdx.x; q < n_part; q += blockDim.x) {
+            v[3] += P.part_ent[q * 8 + 0];
+            v[4] += P.part_ent[q * 8 + 1];
+        }
+    } else {
+        for (int q = threadIdx.x; q < n_part; q += blockDim.x)
+            for (int k = 0; k < 5; ++k) v[k] += P.part_ent[q * 8 + k];
+    }
+    for (int q = threadIdx.x; q < P.col_ctas; q += blockDim.x) v[5] += P.part_obj[q];
+    for (int i = threadIdx.x; i < P.m; i += blockDim.x) v[6] = fma(P.b[i], P.y[i], v[6]);
+    block_sum<7>(v, red);
+    if (threadIdx.x != 0) return;
+    double eps_p, eps_d, obj_p, obj_d;
+    eps_p = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-12);
+    eps_d = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-12);
+    if (form == SDP_PRIMAL) {
+        obj_p = v[5];
+        obj_d = -rho * v[6];
+    } else {
+        obj_d = v[6];
+        obj_p = -rho * v[5];
+    }
+    const int it = C->iter + 1;
+    C->iter = it;
+    C->eps_p = eps_p;
+    C->eps_d = eps_d;
+    C->obj_p = obj_p;
+    C->obj_d = obj_d;
+    C->ticket = 0;
+    if (!isfinite(eps_p) || !isfinite(eps_d) || !isfinite(obj_p) || !isfinite(obj_d)) {
+        C->status = SDP_ERR_NAN;
+        C->done = 1;
+    } else if (fmax(eps_p, eps_d) < C->tol) {
+        C->status = SDP_OK;
+        C->done = 1;
+    } else if (it >= C->iter_limit) {
+        C->status = SDP_MAX_ITER;
+        C->done = 1;
+    }
+}
+
+// After a CTA has written its partial sums: count it, and let the last one finalize.
+__device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int form, double rho, int n_part) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&P.ctrl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_iteration(P, form, rho, n_part);
+    }
 }
 
 // ---------------------------------------------------------------- scatter (primal form)
 // r = sum_k H_k^T(x_k + rho^-1 lambda_k) - rho^-1 c, summed in ascending k from the first term;
 // also the dual-residual pieces ||sum_k H_k^T(x_k+ - x_k)||^2 and ||sum_k H_k^T lambda_k||^2.
-// use_current = 1 rebuilds r from the current blocks (after a reset or a state upload).
-__global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, int use_current) {
+// use_current = 1 rebuilds r from the current blocks (after a reset or a state upload) and skips
+// the residual work. CTAs [0, ent_ctas) take one entry per thread (heavily shared entries are left
+// to the others); CTAs [ent_ctas, ent_ctas + heavy_ctas) take one heavily shared entry per warp:
+// its lanes form 32 terms at a time and every lane adds them in ascending clique order.
+__global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, double rho, int use_current) {
     __shared__ double red[33 * 2];
     if (P.ctrl->done) return;
     const bool odd = (P.ctrl->iter & 1) != 0;
@@ -65,24 +137,63 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
     const double* xn_buf = use_current ? cur : nxt;
     const double* xo_buf = cur;
     double v[2] = {0.0, 0.0};
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < P.nEL) {
-        const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
-        double acc = 0.0, dsum = 0.0, lsum = 0.0;
-        for (int j = j0; j < j1; ++j) {
-            const int pos = P.sc_pos[j];
-            const double xn = xn_buf[pos], xo = xo_buf[pos], l = P.lam[pos];
-            const double term = __dadd_rn(xn, __dmul_rn(rinv, l));
-            const double dd = xn - xo;
-            if (j == j0) { acc = term; dsum = dd; lsum = l; }
-            else { acc = __dadd_rn(acc, term); dsum += dd; lsum += l; }
+    if ((int)blockIdx.x < P.ent_ctas) {
+        const int e = blockIdx.x * blockDim.x + threadIdx.x;
+        if (e < P.nEL) {
+            const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
+            if (j1 - j0 <= kHeavyCount) {
+                double acc = 0.0, dsum = 0.0, lsum = 0.0;
+                for (int j = j0; j < j1; ++j) {
+                    const int pos = P.sc_pos[j];
+                    const double xn = xn_buf[pos], xo = xo_buf[pos], l = P.lam[pos];
+                    const double term = __dadd_rn(xn, __dmul_rn(rinv, l));
+                    const double dd = xn - xo;
+                    if (j == j0) { acc = term; dsum = dd; lsum = l; }
+                    else { acc = __dadd_rn(acc, term); dsum += dd; lsum += l; }
+                }
+                const double re = __dsub_rn(acc, __dmul_rn(rinv, P.c[e]));
+                P.r[e] = re;
+                P.rsw[e] = re * P.wdinv[e];
+                const double w = (double)P.ew[e];
+                v[0] = w * dsum * dsum;
+                v[1] = w * lsum * lsum;
+            }
         }
-        const double re = __dsub_rn(acc, __dmul_rn(rinv, P.c[e]));
-        P.r[e] = re;
-        P.rsw[e] = re * P.wdinv[e];
-        const double w = (double)P.ew[e];
-        v[0] = w * dsum * dsum;
-        v[1] = w * lsum * lsum;
+    } else {
+        const int lane = threadIdx.x & 31;
+        const int hw = ((int)blockIdx.x - P.ent_ctas) * (kEntThreads / 32) + (threadIdx.x >> 5);
+        if (hw < P.n_heavy) {
+            const int e = P.heavy[hw];
+            const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
+            double acc = 0.0, dsum = 0.0, lsum = 0.0;
+            for (int base = j0; base < j1; base += 32) {
+                const int j = base + lane;
+                double term = 0.0, dd = 0.0, l = 0.0;
+                if (j < j1) {
+                    const int pos = P.sc_pos[j];
+                    const double xn = xn_buf[pos], xo = xo_buf[pos];
+                    l = P.lam[pos];
+                    term = __dadd_rn(xn, __dmul_rn(rinv, l));
+                    dd = xn - xo;
+                }
+                const int cnt = min(32, j1 - base);
+                for (int t = 0; t < cnt; ++t) {
+                    const double tv = __shfl_sync(0xffffffffu, term, t);
+                    const double dv = __shfl_sync(0xffffffffu, dd, t);
+                    const double lv = __shfl_sync(0xffffffffu, l, t);
+                    if (base == j0 && t == 0) { acc = tv; dsum = dv; lsum = lv; }
+                    else { acc = __dadd_rn(acc, tv); dsum += dv; lsum += lv; }
+                }
+            }
+            if (lane == 0) {
+                const double re = __dsub_rn(acc, __dmul_rn(rinv, P.c[e]));
+                P.r[e] = re;
+                P.rsw[e] = re * P.wdinv[e];
+                const double w = (double)P.ew[e];
+                v[0] = w * dsum * dsum;
+                v[1] = w * lsum * lsum;
+            }
+        }
     }
     if (use_current) return;
     block_sum<2>(v, red);
@@ -90,28 +201,59 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
         P.part_ent[blockIdx.x * 8 + 0] = v[0];
         P.part_ent[blockIdx.x * 8 + 1] = v[1];
     }
+    finish_and_maybe_finalize(P, SDP_PRIMAL, rho, P.ent_ctas + P.heavy_ctas);
 }
 
 // ---------------------------------------------------------------- scatter (dual form)
-// r = c - sum_k H_k^T(z_k + rho^-1 lambda_k), ascending k from the first term.
+// r = c - sum_k H_k^T(z_k + rho^-1 lambda_k), ascending k from the first term; the same split
+// between light entries (one per thread) and heavily shared ones (one per warp).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double rinv) {
     if (P.ctrl->done) return;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= P.nEL) return;
     const double* z = P.xk[0];
+    if ((int)blockIdx.x < P.ent_ctas) {
+        const int e = blockIdx.x * blockDim.x + threadIdx.x;
+        if (e >= P.nEL) return;
+        const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
+        if (j1 - j0 > kHeavyCount) return;
+        double acc = 0.0;
+        for (int j = j0; j < j1; ++j) {
+            const int pos = P.sc_pos[j];
+            const double term = __dadd_rn(z[pos], __dmul_rn(rinv, P.lam[pos]));
+            acc = (j == j0) ? term : __dadd_rn(acc, term);
+        }
+        const double re = __dsub_rn(P.c[e], acc);
+        P.r[e] = re;
+        P.rsw[e] = re * P.wdinv[e];
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int hw = ((int)blockIdx.x - P.ent_ctas) * (kEntThreads / 32) + (threadIdx.x >> 5);
+    if (hw >= P.n_heavy) return;
+    const int e = P.heavy[hw];
     const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
     double acc = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const int pos = P.sc_pos[j];
-        const double term = __dadd_rn(z[pos], __dmul_rn(rinv, P.lam[pos]));
-        acc = (j == j0) ? term : __dadd_rn(acc, term);
+    for (int base = j0; base < j1; base += 32) {
+        const int j = base + lane;
+        double term = 0.0;
+        if (j < j1) {
+            const int pos = P.sc_pos[j];
+            term = __dadd_rn(z[pos], __dmul_rn(rinv, P.lam[pos]));
+        }
+        const int cnt = min(32, j1 - base);
+        for (int t = 0; t < cnt; ++t) {
+            const double tv = __shfl_sync(0xffffffffu, term, t);
+            acc = (base == j0 && t == 0) ? tv : __dadd_rn(acc, tv);
+        }
     }
-    const double re = __dsub_rn(P.c[e], acc);
-    P.r[e] = re;
-    P.rsw[e] = re * P.wdinv[e];
+    if (lane == 0) {
+        const double re = __dsub_rn(P.c[e], acc);
+        P.r[e] = re;
+        P.rsw[e] = re * P.wdinv[e];
+    }
 }
 
 // ---------------------------------------------------------------- t = A (w r / D), CSR chunks
+// Four independent accumulators per thread keep several gathers in flight.
 __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     __shared__ double red[33];
     if (P.ctrl->done) return;
@@ -119,10 +261,17 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     const int lo0 = P.a_rowptr[i], hi0 = P.a_rowptr[i + 1];
     const long long len = hi0 - lo0;
     const int lo = lo0 + (int)(len * ch / P.R), hi = lo0 + (int)(len * (ch + 1) / P.R);
-    double acc = 0.0;
-#pragma unroll 4
-    for (int j = lo + threadIdx.x; j < hi; j += blockDim.x) acc = fma(P.a_val[j], P.rsw[P.a_col[j]], acc);
-    double v[1] = {acc};
+    const int bd = blockDim.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = lo + threadIdx.x;
+    for (; j + 3 * bd < hi; j += 4 * bd) {
+        a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
+        a1 = fma(P.a_val[j + bd], P.rsw[P.a_col[j + bd]], a1);
+        a2 = fma(P.a_val[j + 2 * bd], P.rsw[P.a_col[j + 2 * bd]], a2);
+        a3 = fma(P.a_val[j + 3 * bd], P.rsw[P.a_col[j + 3 * bd]], a3);
+    }
+    for (; j < hi; j += bd) a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
+    double v[1] = {(a0 + a1) + (a2 + a3)};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) P.tpart[blockIdx.x] = v[0];
 }
@@ -143,9 +292,14 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int row = blockIdx.x * nw + warp; row < m; row += gridDim.x * nw) {
         const double* Lr = P.Linv + (size_t)row * m;
-        double acc = 0.0;
-        for (int j = lane; j <= row; j += 32) acc = fma(Lr[j], u[j], acc);
-        acc = warp_sum(acc);
+        double a0 = 0.0, a1 = 0.0;
+        int j = lane;
+        for (; j + 32 <= row; j += 64) {
+            a0 = fma(Lr[j], u[j], a0);
+            a1 = fma(Lr[j + 32], u[j + 32], a1);
+        }
+        if (j <= row) a0 = fma(Lr[j], u[j], a0);
+        const double acc = warp_sum(a0 + a1);
         if (lane == 0) P.z1[row] = acc;
     }
 }
@@ -160,9 +314,14 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int row = blockIdx.x * nw + warp; row < m; row += gridDim.x * nw) {
         const double* Lr = P.LinvT + (size_t)row * m;
-        double acc = 0.0;
-        for (int i = row + lane; i < m; i += 32) acc = fma(Lr[i], zs[i], acc);
-        acc = warp_sum(acc);
+        double a0 = 0.0, a1 = 0.0;
+        int i = row + lane;
+        for (; i + 32 < m; i += 64) {
+            a0 = fma(Lr[i], zs[i], a0);
+            a1 = fma(Lr[i + 32], zs[i + 32], a1);
+        }
+        if (i < m) a0 = fma(Lr[i], zs[i], a0);
+        const double acc = warp_sum(a0 + a1);
         if (lane == 0) P.y[row] = acc;
     }
 }
@@ -182,15 +341,21 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
     for (int e0 = blockIdx.x * ngroups; e0 < P.nEL; e0 += gridDim.x * ngroups) {
         const int e = e0 + gid;
         const bool valid = e < P.nEL;
-        double s = 0.0;
+        double s0 = 0.0, s1 = 0.0;
         if (valid) {
             const int lo = P.c_colptr[e], hi = P.c_colptr[e + 1];
-            for (int j = lo + gl; j < hi; j += kColGroup) s = fma(P.c_val[j], ys[P.c_row[j]], s);
+            int j = lo + gl;
+            for (; j + kColGroup < hi; j += 2 * kColGroup) {
+                s0 = fma(P.c_val[j], ys[P.c_row[j]], s0);
+                s1 = fma(P.c_val[j + kColGroup], ys[P.c_row[j + kColGroup]], s1);
+            }
+            if (j < hi) s0 = fma(P.c_val[j], ys[P.c_row[j]], s0);
         }
+        double s = s0 + s1;
 #pragma unroll
         for (int o = kColGroup / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (valid && gl == 0) {
-            const double xe = (P.r[e] - s) / P.D[e];
+            const double xe = (P.r[e] - s) * P.dinv[e];
             P.x[e] = xe;
             obj = fma((double)P.ew[e] * P.c[e], xe, obj);
         }
@@ -226,60 +391,7 @@ __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double 
 #pragma unroll
         for (int k = 0; k < 5; ++k) P.part_ent[blockIdx.x * 8 + k] = v[k];
     }
-}
-
-// ---------------------------------------------------------------- residuals and stop test
-__global__ void __launch_bounds__(256) k_finalize(IterPtrs P, int form, double rho) {
-    __shared__ double red[33 * 7];
-    Ctrl* C = P.ctrl;
-    if (C->done) return;
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (form == SDP_PRIMAL) {
-        for (int k = threadIdx.x; k < P.p; k += blockDim.x) {
-            v[0] += P.part_blk[k * 4 + 0];
-            v[1] += P.part_blk[k * 4 + 1];
-            v[2] += P.part_blk[k * 4 + 2];
-        }
-        for (int q = threadIdx.x; q < P.ent_ctas; q += blockDim.x) {
-            v[3] += P.part_ent[q * 8 + 0];
-            v[4] += P.part_ent[q * 8 + 1];
-        }
-    } else {
-        for (int q = threadIdx.x; q < P.pos_ctas; q += blockDim.x)
-            for (int k = 0; k < 5; ++k) v[k] += P.part_ent[q * 8 + k];
-    }
-    for (int q = threadIdx.x; q < P.col_ctas; q += blockDim.x) v[5] += P.part_obj[q];
-    for (int i = threadIdx.x; i < P.m; i += blockDim.x) v[6] = fma(P.b[i], P.y[i], v[6]);
-    block_sum<7>(v, red);
-    if (threadIdx.x != 0) return;
-    double eps_p, eps_d, obj_p, obj_d;
-    if (form == SDP_PRIMAL) {
-        eps_p = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-12);
-        eps_d = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-12);
-        obj_p = v[5];
-        obj_d = -rho * v[6];
-    } else {
-        eps_p = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-12);
-        eps_d = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-12);
-        obj_d = v[6];
-        obj_p = -rho * v[5];
-    }
-    const int it = C->iter + 1;
-    C->iter = it;
-    C->eps_p = eps_p;
-    C->eps_d = eps_d;
-    C->obj_p = obj_p;
-    C->obj_d = obj_d;
-    if (!isfinite(eps_p) || !isfinite(eps_d) || !isfinite(obj_p) || !isfinite(obj_d)) {
-        C->status = SDP_ERR_NAN;
-        C->done = 1;
-    } else if (fmax(eps_p, eps_d) < C->tol) {
-        C->status = SDP_OK;
-        C->done = 1;
-    } else if (it >= C->iter_limit) {
-        C->status = SDP_MAX_ITER;
-        C->done = 1;
-    }
+    finish_and_maybe_finalize(P, SDP_DUAL, rho, P.pos_ctas);
 }
 
 __global__ void k_ctrl_arm(Ctrl* C, int n_iters, double tol) {
@@ -287,6 +399,7 @@ __global__ void k_ctrl_arm(Ctrl* C, int n_iters, double tol) {
     C->status = SDP_MAX_ITER;
     C->iter_limit = C->iter + n_iters;
     C->tol = tol;
+    C->ticket = 0;
 }
 
 __global__ void k_ctrl_clear(Ctrl* C) { C->done = 0; }
@@ -296,6 +409,7 @@ __global__ void k_ctrl_reset(Ctrl* C) {
     C->iter_limit = 0;
     C->done = 0;
     C->status = SDP_MAX_ITER;
+    C->ticket = 0;
     C->tol = 0.0;
     C->eps_p = C->eps_d = C->obj_p = C->obj_d = 0.0;
 }
@@ -315,6 +429,16 @@ __global__ void k_scatter_plain(const int* sc_ptr, const int* sc_pos, int nEL, c
     out[e] = acc;
 }
 
+// Identity eigenvector blocks (a warm start from them is a cold start).
+template <typename T>
+__global__ void k_vstore_identity(T* vs, const long long* voff, const int* size, int p) {
+    const int k = blockIdx.x;
+    if (k >= p) return;
+    const int N = size[k] + (size[k] & 1);
+    T* b = vs + voff[k];
+    for (int q = threadIdx.x; q < N * N; q += blockDim.x) b[q] = (q / N == q % N) ? T(1) : T(0);
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 ProjArgs proj_args_for(const IterPtrs& P, double rho) {
@@ -331,21 +455,10 @@ ProjArgs proj_args_for(const IterPtrs& P, double rho) {
     a.xk[0] = P.xk[0];
     a.xk[1] = P.xk[1];
     a.part = P.part_blk;
+    a.vstore = P.vstore;
+    a.voff = P.voff;
     a.ctrl = P.ctrl;
     return a;
-}
-
-}  // namespace
-
-int iteration_kernel_count(int form) { return form == SDP_PRIMAL ? 7 : 8; }
-
-cudaError_t iteration_prepare() {
-    // y / z / t staged in shared memory: up to SDP_MAX_CONSTRAINTS doubles.
-    const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // Optional per-kernel timing: when ev != nullptr, ev[i] is recorded before kernel i of the
@@ -373,6 +486,19 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rinv, cudaStream_t
     return cudaGetLastError();
 }
 
+}  // namespace
+
+int iteration_kernel_count(int form) { return form == SDP_PRIMAL ? 6 : 7; }
+
+cudaError_t iteration_prepare() {
+    // y / z / t staged in shared memory: up to SDP_MAX_CONSTRAINTS doubles.
+    const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, cudaStream_t st,
                              cudaEvent_t* ev) {
     const double rinv = 1.0 / rho;
@@ -384,34 +510,41 @@ cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, 
         mk.mark();
         if ((e = launch_project(a, PROJ_PRIMAL, prec, P.smax, st)) != cudaSuccess) return e;
         mk.mark();
-        k_scatter_primal<<<P.ent_ctas, kEntThreads, 0, st>>>(P, rinv, 0);
+        k_scatter_primal<<<P.ent_ctas + P.heavy_ctas, kEntThreads, 0, st>>>(P, rinv, rho, 0);
     } else {
         a.out = P.xk[0];
         mk.mark();
         if ((e = launch_project(a, PROJ_DUAL, prec, P.smax, st)) != cudaSuccess) return e;
         mk.mark();
-        k_scatter_dual<<<P.ent_ctas, kEntThreads, 0, st>>>(P, rinv);
+        k_scatter_dual<<<P.ent_ctas + P.heavy_ctas, kEntThreads, 0, st>>>(P, rinv);
         if ((e = launch_affine(P, form, rinv, st, mk)) != cudaSuccess) return e;
         mk.mark();
         k_update_dual<<<P.pos_ctas, kEntThreads, 0, st>>>(P, rho, rinv);
     }
-    mk.mark();
-    k_finalize<<<1, 256, 0, st>>>(P, form, rho);
     mk.mark();
     return cudaGetLastError();
 }
 
 const char* phase_name(int form, int i) {
     static const char* primal[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols",
-                                   "project_primal", "scatter_primal", "finalize"};
+                                   "project_primal", "scatter_primal+finalize"};
     static const char* dual[] = {"project_dual", "scatter_dual", "spmv_rows", "tri_lower",
-                                 "tri_upper", "spmv_cols", "update_dual", "finalize"};
-    if (form == SDP_PRIMAL) return (i >= 0 && i < 7) ? primal[i] : nullptr;
-    return (i >= 0 && i < 8) ? dual[i] : nullptr;
+                                 "tri_upper", "spmv_cols", "update_dual+finalize"};
+    if (form == SDP_PRIMAL) return (i >= 0 && i < 6) ? primal[i] : nullptr;
+    return (i >= 0 && i < 7) ? dual[i] : nullptr;
 }
 
 cudaError_t launch_primal_rebuild_r(const IterPtrs& P, double rho, cudaStream_t st) {
-    k_scatter_primal<<<P.ent_ctas, kEntThreads, 0, st>>>(P, 1.0 / rho, 1);
+    k_scatter_primal<<<P.ent_ctas + P.heavy_ctas, kEntThreads, 0, st>>>(P, 1.0 / rho, rho, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vstore_identity(const IterPtrs& P, int prec, cudaStream_t st) {
+    if (P.vstore == nullptr || P.p <= 0) return cudaSuccess;
+    if (prec == SDP_PROJ_FP32)
+        k_vstore_identity<float><<<P.p, 256, 0, st>>>(static_cast<float*>(P.vstore), P.voff, P.blk_size, P.p);
+    else
+        k_vstore_identity<double><<<P.p, 256, 0, st>>>(static_cast<double*>(P.vstore), P.voff, P.blk_size, P.p);
     return cudaGetLastError();
 }
 

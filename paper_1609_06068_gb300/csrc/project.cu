@@ -1,17 +1,27 @@
 // Batched projection of small symmetric clique blocks onto the PSD cone (Eqs. XkUpdate, zkUpdate):
 // P(W) = V diag(max(lambda, 0)) V^T, with the eigendecomposition by two-sided cyclic Jacobi.
 //
-// One CTA owns one clique block. The block and the eigenvector matrix V live in shared memory in
-// the projection precision T (float or double). A sweep visits every index pair once in the
-// round-robin ("circle") order: N/2 disjoint pairs per round, N-1 rounds (N = s rounded up to even;
-// an odd block gets a zero padding row/column that never rotates). In a round, one thread per pair
-// computes the rotation that zeroes a_pq (Golub & Van Loan, Sec. 8.5, symmetric Schur 2x2), then
-// every thread applies J^T A J to whole 2x2 tiles (rows of pair I, columns of pair J), so the
-// round needs two barriers and no intermediate copy. Sweeps stop once the off-diagonal Frobenius
-// norm is below tol * ||W||_F. The reconstruction writes only the lower triangle, so the result
-// is exactly symmetric; it is widened to FP64 on store.
-#include <cstdio>
-
+// One CTA owns one clique block (order s, padded to even N; a padded row/column is zero and never
+// rotates). A sweep visits every index pair once in the round-robin ("circle") order: N/2 disjoint
+// pairs per round, N-1 rounds. The matrix is kept in SLOT order: row/column i of the stored matrix
+// belongs to the index that currently occupies slot i, round r pairs slot j with slot H+j, and
+// after each round every index moves one step along a fixed ring (slot 0 stays). Because pairs sit
+// at fixed slots, each thread owns fixed 2x2 tiles of A (rows of pair I, columns of pair J, I <= J)
+// and fixed entries of V in registers, and every shared-memory address it touches is computed once.
+// A round is: the owner of diagonal tile (I, I) computes the rotation that zeroes a_pq (Golub &
+// Van Loan, symmetric Schur 2x2) and publishes (c, s); barrier; every thread applies J^T A J to its
+// tiles and J to its V entries, and writes them to their next-round slots; barrier; every thread
+// reloads its tiles. Sweeps stop once the off-diagonal Frobenius norm is below tol * ||W||_F.
+// Eigenvector order does not matter for P(W), so the slot permutation never has to be undone.
+//
+// Warm start (handle path): the eigenvectors of the previous ADMM iteration's block are kept in
+// HBM; the kernel forms V^T W V with them and starts Jacobi from that nearly diagonal matrix, which
+// usually needs one or two sweeps. Every kWarmPeriod-th iteration starts cold from V = I so that
+// rounding in V cannot accumulate. The result does not depend on the start (P is unique).
+//
+// W is formed in FP64 and scaled by the power of two 2^-e that brings max|W_ij| into [1, 2), then
+// rounded to the projection precision T; the rebuilt lower triangle is widened and unscaled (both
+// scalings are exact).
 #include "sdp_internal.h"
 
 namespace cadmm {
@@ -19,6 +29,9 @@ namespace cadmm {
 namespace {
 
 template <typename T> struct JacobiParams;
+// FP32 stops at off(A) <= 1e-7 ||W||_F, about the FP32 rounding of the rebuild; the projection
+// moves by at most the dropped off-diagonal part (P is 1-Lipschitz). A looser 1e-6 moved the
+// converged ADMM objectives by ~1e-4 relative on the n = 1020 block-arrow workload.
 template <> struct JacobiParams<float> {
     static constexpr float rel_tol = 1.0e-7f;
     static constexpr int max_sweeps = 24;
@@ -29,14 +42,30 @@ template <> struct JacobiParams<double> {
 };
 
 constexpr int kMaxPairs = SDP_MAX_CLIQUE / 2;
+constexpr int kWarmPeriod = 8;
+
+// Threads per CTA and register slots per thread for A tiles (KA) and V entry pairs (KV), by the
+// padded order N: KA * NT >= H(H+1)/2 and KV * NT >= N*H with H = N/2.
+template <int NT_, int KA_, int KV_> struct Shape {
+    static constexpr int NT = NT_, KA = KA_, KV = KV_;
+};
+using ShapeS16 = Shape<64, 1, 2>;    // N <= 16
+using ShapeS32 = Shape<256, 1, 2>;   // N <= 32
+using ShapeS64 = Shape<512, 2, 4>;   // N <= 64
+using ShapeS96 = Shape<512, 3, 9>;   // N <= 96
 
 __device__ __forceinline__ int packed_pos(int a, int b, int s) {
     return b * s - (b * (b - 1)) / 2 + (a - b);  // column-major lower, a >= b
 }
 
-// Slot i of round r in the circle method for N players: slot 0 stays, the rest rotate.
-__device__ __forceinline__ int rr_slot(int i, int r, int N) {
-    return i == 0 ? 0 : 1 + ((i - 1 + r) % (N - 1));
+// Slot that the index now in slot i occupies next round: slot 0 stays; the top row 1..H-1 moves
+// right, the bottom row H..N-1 moves left, and the two rows are joined into one ring.
+__device__ __forceinline__ int ring_next(int i, int H, int N) {
+    if (N == 2 || i == 0) return i;
+    if (i < H - 1) return i + 1;
+    if (i == H - 1) return N - 1;
+    if (i > H) return i - 1;
+    return 1;
 }
 
 template <typename T>
@@ -92,32 +121,81 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return v;
 }
 
-// W_ij of one packed position: the block itself (standalone), H_k x - rho^-1 lambda_k (primal,
-// Eq. XkUpdate; u = H_k x is kept in U for the multiplier update) or v_k - rho^-1 lambda_k (dual,
-// Eq. zkUpdate).
-template <int MODE>
-__device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int pos, double rinv, double* U) {
-    if (MODE == PROJ_PLAIN) return a.in[off + pos];
-    if (MODE == PROJ_PRIMAL) {
-        const double u = a.x[a.gather_idx[off + pos]];
-        U[pos] = u;
-        return __dsub_rn(u, __dmul_rn(rinv, a.lam[off + pos]));
+// ---- Jacobi rotation that zeroes a_pq:
+//   tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2),
+//   s = t c; afterwards a_pp -= t a_pq, a_qq += t a_pq, a_pq = 0.
+// The block is scaled so max|w| lies in [1, 2); off-diagonal entries below 1e-30 count as zero.
+// FP32: the angle only has to be right to a few ulp (the residual it leaves in a_pq is of FP32
+// rounding size, and later rotations remove it), so tau and t use the hardware reciprocal and
+// sqrt(x) = x rsqrt(x). c = 1/sqrt(1 + t^2) is correctly rounded: c^2 + s^2 = 1 to half an ulp
+// keeps V orthogonal over the thousands of rotations a warm-started block goes through (a few-ulp
+// c let V drift by ~1e-5 and moved the converged ADMM objective by ~1e-4).
+__device__ __forceinline__ void rotation(float app, float aqq, float apq, float& c, float& s, float& t) {
+    if (fabsf(apq) < 1.0e-30f) { c = 1.f; s = 0.f; t = 0.f; return; }
+    const float tau = __fdividef(aqq - app, 2.f * apq);
+    const float at = fabsf(tau);
+    float den;
+    if (at > 1.0e15f) {
+        den = 2.f * at;
+    } else {
+        const float x = fmaf(tau, tau, 1.f);
+        den = at + x * rsqrtf(x);
     }
+    t = copysignf(__fdividef(1.f, den), tau);
+    c = __frsqrt_rn(fmaf(t, t, 1.f));
+    s = t * c;
+}
+
+// FP64: GB300's FP64 divide and square root are long dependent chains on a narrow pipe, so the
+// reciprocal and the reciprocal square root start from FP32 estimates (2^-23) and take two
+// Newton steps each (error below 2^-52 before rounding).
+__device__ __forceinline__ double rcp_nr(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {   // x in [1, 2^60]
+    double y = (double)__frsqrt_rn((float)x);
+    const double h = 0.5 * x;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+__device__ __forceinline__ void rotation(double app, double aqq, double apq, double& c, double& s, double& t) {
+    if (fabs(apq) < 1.0e-30) { c = 1.0; s = 0.0; t = 0.0; return; }
+    const double tau = (aqq - app) * rcp_nr(2.0 * apq);
+    const double at = fabs(tau);
+    double den;
+    if (at > 1.0e8) {
+        den = 2.0 * at;                                   // sqrt(1 + tau^2) = |tau| to FP64 precision
+    } else {
+        const double x = fma(tau, tau, 1.0);
+        den = at + x * rsqrt_nr(x);
+    }
+    t = copysign(rcp_nr(den), tau);
+    c = rsqrt_nr(fma(t, t, 1.0));
+    s = t * c;
+}
+
+// W_ij of one packed position: the block itself (standalone), H_k x - rho^-1 lambda_k (primal,
+// Eq. XkUpdate) or v_k - rho^-1 lambda_k (dual, Eq. zkUpdate).
+template <int MODE>
+__device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int pos, double rinv) {
+    if (MODE == PROJ_PLAIN) return a.in[off + pos];
+    if (MODE == PROJ_PRIMAL)
+        return __dsub_rn(a.x[a.gather_idx[off + pos]], __dmul_rn(rinv, a.lam[off + pos]));
     return __dsub_rn(a.v[off + pos], __dmul_rn(rinv, a.lam[off + pos]));
 }
 
-template <typename T>
-__device__ __forceinline__ T t_sqrt(T x);
-template <> __device__ __forceinline__ float t_sqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double t_sqrt<double>(double x) { return sqrt(x); }
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_project(ProjArgs a, double rinv) {
+template <typename T, int MODE, class SH>
+__global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
+    constexpr int KA = SH::KA, KV = SH::KV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T s_c[kMaxPairs], s_s[kMaxPairs], s_t[kMaxPairs];
-    __shared__ int s_p[kMaxPairs], s_q[kMaxPairs];
+    __shared__ T s_c[kMaxPairs], s_s[kMaxPairs];
     __shared__ T red_t[33 * 2];
-    __shared__ double red_d[33 * 3];
+    __shared__ double red_d[33 * 4];
 
     if (a.ctrl != nullptr && a.ctrl->done) return;
 
@@ -125,145 +203,224 @@ __global__ void __launch_bounds__(512) k_project(ProjArgs a, double rinv) {
     const int s = a.size[blk];
     const long long off = a.off[blk];
     const int N = s + (s & 1);
-    const int LD = N + 1;
     const int H = N / 2;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int LD = N + 1;
+    const int tid = threadIdx.x;
+    const int NT = SH::NT;
+    const bool warm = a.vstore != nullptr && a.ctrl != nullptr && (a.ctrl->iter % kWarmPeriod) != 0;
 
-    T* A = reinterpret_cast<T*>(smem_raw);
-    T* V = A + N * LD;
-    T* dp = V + N * LD;
-    const size_t ub = (size_t)(2 * N * LD + N) * sizeof(T);
-    double* U = reinterpret_cast<double*>(smem_raw + ((ub + 15) & ~(size_t)15));
+    T* Ax = reinterpret_cast<T*>(smem_raw);   // exchange buffer for A (slot order)
+    T* Vx = Ax + N * LD;                      // exchange buffer for V (rows: coordinates, cols: slots)
+    T* Wb = Vx + N * LD;                      // W (warm start input / product scratch)
+    T* dp = Wb + N * LD;                      // clipped eigenvalues by slot
 
-    double* xk_new = nullptr;
-    if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
-
-    // ---- load W into A (both triangles), V = I, zero padding
-    for (int q = tid; q < N * N; q += nt) {
-        const int i = q / N, j = q - (q / N) * N;
-        V[i * LD + j] = (i == j) ? T(1) : T(0);
-        if (i >= s || j >= s) A[i * LD + j] = T(0);
-    }
-    // Pass 1 finds max |W_ij|; pass 2 stores W scaled by the power of two 2^-e that brings it to
-    // [1, 2), so squares and rotations stay in range in either precision. The scaling is exact
-    // and is undone on the result.
+    // ---- load W (scaled by 2^-e2) into Wb (warm) or Ax (cold), both triangles, zero padding
     double wmax = 0.0;
-    for (int q = tid; q < s * s; q += nt) {
+    for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
-        const double w = load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv, U);
-        wmax = fmax(wmax, fabs(w));
+        wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv)));
     }
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    for (int q = tid; q < s * s; q += nt) {
+    T* Wt = warm ? Wb : Ax;
+    for (int q = tid; q < N * N; q += NT) {
+        const int i = q / N, j = q - (q / N) * N;
+        if (i >= s || j >= s) Wt[i * LD + j] = T(0);
+    }
+    for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
-        const int pos = packed_pos(ra, cb, s);
-        const double w = (MODE == PROJ_PRIMAL) ? __dsub_rn(U[pos], __dmul_rn(rinv, a.lam[off + pos]))
-                                               : load_w<MODE>(a, off, pos, rinv, U);
-        const T wt = (T)ldexp(w, -e2);
-        A[ra * LD + cb] = wt;
-        A[cb * LD + ra] = wt;
+        const T wt = (T)ldexp(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv), -e2);
+        Wt[ra * LD + cb] = wt;
+        Wt[cb * LD + ra] = wt;
+    }
+    // ---- V: identity (cold) or the previous eigenvectors (warm)
+    T* vglob = nullptr;
+    if (a.vstore != nullptr) vglob = reinterpret_cast<T*>(a.vstore) + a.voff[blk];
+    for (int q = tid; q < N * N; q += NT) {
+        const int i = q / N, j = q - (q / N) * N;
+        Vx[i * LD + j] = warm ? vglob[q] : (i == j ? T(1) : T(0));
     }
     __syncthreads();
+    if (warm) {
+        // Ax = W V, then Wb = V^T Ax: the block in the basis of the previous eigenvectors.
+        for (int q = tid; q < N * N; q += NT) {
+            const int i = q / N, j = q - (q / N) * N;
+            T acc = T(0);
+            for (int k = 0; k < N; ++k) acc = fma(Wb[i * LD + k], Vx[k * LD + j], acc);
+            Ax[i * LD + j] = acc;
+        }
+        __syncthreads();
+        for (int q = tid; q < N * N; q += NT) {
+            const int i = q / N, j = q - (q / N) * N;
+            if (j < i) continue;
+            T acc = T(0);
+            for (int k = 0; k < N; ++k) acc = fma(Vx[k * LD + i], Ax[k * LD + j], acc);
+            Wb[i * LD + j] = acc;
+            Wb[j * LD + i] = acc;
+        }
+        __syncthreads();
+    }
+    const T* A0 = warm ? Wb : Ax;
 
-    // ---- ||W||_F^2
+    // ---- per-thread ownership: tiles (I, J), I <= J, and V entry pairs (row r, pair J)
+    const int ntiles = H * (H + 1) / 2;
+    int tI[KA], tJ[KA];
+    int src[KA][4], dst[KA][4], mir[KA][4];
+    T x[KA][4];
+#pragma unroll
+    for (int t = 0; t < KA; ++t) {
+        int w = tid + t * NT, I = 0;
+        tI[t] = -1;
+        tJ[t] = -1;
+        if (w < ntiles) {
+            while (w >= H - I) { w -= H - I; ++I; }
+            tI[t] = I;
+            tJ[t] = I + w;
+        }
+        const int I0 = tI[t] < 0 ? 0 : tI[t], J0 = tJ[t] < 0 ? 0 : tJ[t];
+        const int r0 = I0, r1 = H + I0, c0 = J0, c1 = H + J0;
+        src[t][0] = r0 * LD + c0; src[t][1] = r0 * LD + c1;
+        src[t][2] = r1 * LD + c0; src[t][3] = r1 * LD + c1;
+        const int nr0 = ring_next(r0, H, N), nr1 = ring_next(r1, H, N);
+        const int nc0 = ring_next(c0, H, N), nc1 = ring_next(c1, H, N);
+        dst[t][0] = nr0 * LD + nc0; dst[t][1] = nr0 * LD + nc1;
+        dst[t][2] = nr1 * LD + nc0; dst[t][3] = nr1 * LD + nc1;
+        mir[t][0] = nc0 * LD + nr0; mir[t][1] = nc1 * LD + nr0;
+        mir[t][2] = nc0 * LD + nr1; mir[t][3] = nc1 * LD + nr1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[t][e] = tI[t] >= 0 ? A0[src[t][e]] : T(0);
+    }
+    int vJ[KV], vsrc[KV][2], vdst[KV][2];
+    T v[KV][2];
+#pragma unroll
+    for (int u = 0; u < KV; ++u) {
+        const int w = tid + u * NT;
+        vJ[u] = w < N * H ? w % H : -1;
+        const int r = w < N * H ? w / H : 0, J = vJ[u] < 0 ? 0 : vJ[u];
+        vsrc[u][0] = r * LD + J;
+        vsrc[u][1] = r * LD + H + J;
+        vdst[u][0] = r * LD + ring_next(J, H, N);
+        vdst[u][1] = r * LD + ring_next(H + J, H, N);
+        v[u][0] = vJ[u] >= 0 ? Vx[vsrc[u][0]] : T(0);
+        v[u][1] = vJ[u] >= 0 ? Vx[vsrc[u][1]] : T(0);
+    }
+
+    // ---- ||W||_F^2 and the stopping threshold
     T nrm[1] = {T(0)};
-    for (int q = tid; q < N * N; q += nt) {
-        const T v = A[(q / N) * LD + (q % N)];
-        nrm[0] += v * v;
+#pragma unroll
+    for (int t = 0; t < KA; ++t) {
+        if (tI[t] < 0) continue;
+        const T q2 = x[t][0] * x[t][0] + x[t][1] * x[t][1] + x[t][2] * x[t][2] + x[t][3] * x[t][3];
+        nrm[0] += tI[t] == tJ[t] ? q2 : T(2) * q2;
     }
     block_sum_t<T, 1>(nrm, red_t);
     const T tol2 = JacobiParams<T>::rel_tol * JacobiParams<T>::rel_tol * nrm[0];
 
     // ---- cyclic Jacobi sweeps
-    for (int sweep = 0; sweep < JacobiParams<T>::max_sweeps && N > 1; ++sweep) {
+    int sweeps = 0;
+    for (int sweep = 0; sweep < JacobiParams<T>::max_sweeps; ++sweep) {
         T off2[1] = {T(0)};
-        for (int q = tid; q < N * N; q += nt) {
-            const int i = q / N, j = q - (q / N) * N;
-            if (i != j) {
-                const T v = A[i * LD + j];
-                off2[0] += v * v;
-            }
+#pragma unroll
+        for (int t = 0; t < KA; ++t) {
+            if (tI[t] < 0) continue;
+            if (tI[t] == tJ[t]) off2[0] += x[t][1] * x[t][1] + x[t][2] * x[t][2];
+            else off2[0] += T(2) * (x[t][0] * x[t][0] + x[t][1] * x[t][1] + x[t][2] * x[t][2] + x[t][3] * x[t][3]);
         }
         block_sum_t<T, 1>(off2, red_t);
         if (!(off2[0] > tol2)) break;
-
+        ++sweeps;
         for (int r = 0; r < N - 1; ++r) {
-            if (tid < H) {
-                int p = rr_slot(tid, r, N), q = rr_slot(N - 1 - tid, r, N);
-                if (p > q) { const int t = p; p = q; q = t; }
-                const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
-                T c = T(1), sn = T(0), t = T(0);
-                if (apq != T(0)) {
-                    const T tau = (aqq - app) / (T(2) * apq);
-                    t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + t_sqrt<T>(T(1) + tau * tau));
-                    c = T(1) / t_sqrt<T>(T(1) + t * t);
-                    sn = t * c;
-                }
-                s_p[tid] = p; s_q[tid] = q;
-                s_c[tid] = c; s_s[tid] = sn; s_t[tid] = t;
-            }
-            __syncthreads();
-            // A <- J^T A J on 2x2 tiles (I <= J; the mirror tile is written by the same thread)
-            for (int w = tid; w < H * H; w += nt) {
-                const int I = w / H, J = w - (w / H) * H;
-                if (I > J) continue;
-                const int pI = s_p[I], qI = s_q[I];
-                if (I == J) {
-                    const T apq = A[pI * LD + qI], t = s_t[I];
-                    A[pI * LD + pI] -= t * apq;
-                    A[qI * LD + qI] += t * apq;
-                    A[pI * LD + qI] = T(0);
-                    A[qI * LD + pI] = T(0);
-                } else {
-                    const int pJ = s_p[J], qJ = s_q[J];
-                    const T cI = s_c[I], sI = s_s[I], cJ = s_c[J], sJ = s_s[J];
-                    const T x00 = A[pI * LD + pJ], x01 = A[pI * LD + qJ];
-                    const T x10 = A[qI * LD + pJ], x11 = A[qI * LD + qJ];
-                    const T y00 = cI * x00 - sI * x10, y01 = cI * x01 - sI * x11;
-                    const T y10 = sI * x00 + cI * x10, y11 = sI * x01 + cI * x11;
-                    const T z00 = y00 * cJ - y01 * sJ, z01 = y00 * sJ + y01 * cJ;
-                    const T z10 = y10 * cJ - y11 * sJ, z11 = y10 * sJ + y11 * cJ;
-                    A[pI * LD + pJ] = z00; A[pI * LD + qJ] = z01;
-                    A[qI * LD + pJ] = z10; A[qI * LD + qJ] = z11;
-                    A[pJ * LD + pI] = z00; A[qJ * LD + pI] = z01;
-                    A[pJ * LD + qI] = z10; A[qJ * LD + qI] = z11;
+#pragma unroll
+            for (int t = 0; t < KA; ++t) {
+                if (tI[t] >= 0 && tI[t] == tJ[t]) {
+                    T c, sn, tt;
+                    rotation(x[t][0], x[t][3], x[t][1], c, sn, tt);
+                    s_c[tI[t]] = c;
+                    s_s[tI[t]] = sn;
+                    // J^T X J applied exactly (no a_pq := 0): an angle that is a few ulp off leaves
+                    // a residual of that size in a_pq, which later rotations remove, instead of
+                    // silently dropping it from the spectrum.
+                    const T a00 = x[t][0], a01 = x[t][1], a11 = x[t][3];
+                    const T y00 = c * a00 - sn * a01, y01 = c * a01 - sn * a11;
+                    const T y10 = sn * a00 + c * a01, y11 = sn * a01 + c * a11;
+                    x[t][0] = y00 * c - y01 * sn;
+                    x[t][1] = y00 * sn + y01 * c;
+                    x[t][2] = x[t][1];
+                    x[t][3] = y10 * sn + y11 * c;
                 }
             }
-            // V <- V J
-            for (int w = tid; w < N * H; w += nt) {
-                const int i = w / H, J = w - (w / H) * H;
-                const int pJ = s_p[J], qJ = s_q[J];
-                const T c = s_c[J], sn = s_s[J];
-                const T vp = V[i * LD + pJ], vq = V[i * LD + qJ];
-                V[i * LD + pJ] = c * vp - sn * vq;
-                V[i * LD + qJ] = sn * vp + c * vq;
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < KA; ++t) {
+                if (tI[t] < 0) continue;
+                if (tI[t] != tJ[t]) {
+                    const T cI = s_c[tI[t]], sI = s_s[tI[t]], cJ = s_c[tJ[t]], sJ = s_s[tJ[t]];
+                    const T y00 = cI * x[t][0] - sI * x[t][2], y01 = cI * x[t][1] - sI * x[t][3];
+                    const T y10 = sI * x[t][0] + cI * x[t][2], y11 = sI * x[t][1] + cI * x[t][3];
+                    x[t][0] = y00 * cJ - y01 * sJ;
+                    x[t][1] = y00 * sJ + y01 * cJ;
+                    x[t][2] = y10 * cJ - y11 * sJ;
+                    x[t][3] = y10 * sJ + y11 * cJ;
+                }
+                // the tile and its mirror move to the slots their indices occupy next round
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    Ax[dst[t][e]] = x[t][e];
+                    Ax[mir[t][e]] = x[t][e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KV; ++u) {
+                if (vJ[u] < 0) continue;
+                const T c = s_c[vJ[u]], sn = s_s[vJ[u]];
+                const T p0 = v[u][0], p1 = v[u][1];
+                Vx[vdst[u][0]] = c * p0 - sn * p1;
+                Vx[vdst[u][1]] = sn * p0 + c * p1;
             }
             __syncthreads();
+#pragma unroll
+            for (int t = 0; t < KA; ++t)
+                if (tI[t] >= 0) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x[t][e] = Ax[src[t][e]];
+                }
+#pragma unroll
+            for (int u = 0; u < KV; ++u)
+                if (vJ[u] >= 0) {
+                    v[u][0] = Vx[vsrc[u][0]];
+                    v[u][1] = Vx[vsrc[u][1]];
+                }
         }
     }
 
-    // ---- clip eigenvalues, rebuild the lower triangle of V diag(max(lambda,0)) V^T
-    for (int i = tid; i < N; i += nt) {
-        const T d = A[i * LD + i];
-        dp[i] = d > T(0) ? d : T(0);
-    }
+    // ---- eigenvalues (diagonal of A, by slot), clipped; V is current in Vx
+#pragma unroll
+    for (int t = 0; t < KA; ++t)
+        if (tI[t] >= 0 && tI[t] == tJ[t]) {
+            dp[tI[t]] = x[t][0] > T(0) ? x[t][0] : T(0);
+            dp[H + tI[t]] = x[t][3] > T(0) ? x[t][3] : T(0);
+        }
     __syncthreads();
+    if (vglob != nullptr)
+        for (int q = tid; q < N * N; q += NT) vglob[q] = Vx[(q / N) * LD + (q % N)];
 
+    // ---- rebuild the lower triangle of V diag(max(lambda, 0)) V^T and apply the epilogue
     double pv[3] = {0.0, 0.0, 0.0};
-    for (int q = tid; q < s * s; q += nt) {
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
+    for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
-        const T* Va = V + ra * LD;
-        const T* Vb = V + cb * LD;
+        const T* Va = Vx + ra * LD;
+        const T* Vb = Vx + cb * LD;
         T acc = T(0);
-        for (int i = 0; i < N; ++i) acc += (Va[i] * dp[i]) * Vb[i];
+        for (int i = 0; i < N; ++i) acc = fma(Va[i] * dp[i], Vb[i], acc);
         const double xv = ldexp((double)acc, e2);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
-            const double u = U[pos];
+            const double u = a.x[a.gather_idx[off + pos]];
             const double l = a.lam[off + pos];
             const double d = xv - u;
             xk_new[off + pos] = xv;
@@ -284,62 +441,304 @@ __global__ void __launch_bounds__(512) k_project(ProjArgs a, double rinv) {
             a.part[blk * 4 + 2] = pv[2];
         }
     }
+    if (a.part != nullptr && tid == 0) a.part[blk * 4 + 3] = (double)sweeps;   // Jacobi sweeps used
 }
 
-template <typename T, int MODE>
+// ---------------------------------------------------------------------------------------------
+// FP32, padded order N <= 32: one-sided (Hestenes) Jacobi, one CTA of four warps per clique.
+//
+// Lane j holds column j of G = B V and of V, with B = W + sigma I and sigma = ||W||_F, so B is
+// positive semidefinite and its eigenvalues are lambda(W) + sigma (for an indefinite W, one-sided
+// Jacobi alone would confuse eigenvalues +mu and -mu). Warp w holds rows 8w .. 8w+7 of every
+// column, in registers. A rotation of columns (i, j) makes g_i and g_j orthogonal (Golub & Van
+// Loan's 2x2 formula on the Gram entries alpha = g_i.g_i, beta = g_j.g_j, gamma = g_i.g_j): the
+// partner column's rows arrive by warp shuffles, the four warps' partial gammas meet in shared
+// memory (one barrier per round), and both lanes of a pair compute the same rotation from the same
+// sums. Rounds follow the round-robin schedule, so a sweep of N-1 rounds meets every pair once.
+// After a sweep whose largest |gamma| / sqrt(alpha beta) is below the tolerance, V holds the
+// eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since G = B V).
+constexpr int kOSWarps = 4;
+constexpr int kOSRows = 8;                 // rows per warp: 4 x 8 = 32
+constexpr float kOneSidedTol = 1.0e-6f;
+constexpr int kOneSidedMaxSweeps = 20;
+
+// Round-robin partner of player i in round rd for N players (N even, n = N - 1 odd): player n
+// meets player rd; every other i meets (2 rd - i) mod n, or player n when that is i itself.
+__device__ __forceinline__ int rr_partner(int i, int rd, int N) {
+    if (i >= N) return i;
+    const int n = N - 1;
+    if (i == n) return rd;
+    int j = (2 * rd - i) % n;
+    if (j < 0) j += n;
+    return j == i ? n : j;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double rinv) {
+    __shared__ float Ws[32][33];                 // W, then V for the rebuild
+    __shared__ float Vs[32][33];                 // previous eigenvectors (warm start)
+    __shared__ float s_gam[2][kOSWarps][32];     // partial gamma per warp, by round parity
+    __shared__ float s_red[kOSWarps][32];
+    __shared__ float dp[32];
+    __shared__ double red_d[33 * 3];
+    __shared__ float red_f[33 * 2];
+
+    if (a.ctrl != nullptr && a.ctrl->done) return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int NT = 32 * kOSWarps;
+    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
+    const int s = a.size[blk];
+    const long long off = a.off[blk];
+    const int N = s + (s & 1);
+    const int r0 = w * kOSRows;
+    const bool warm = a.vstore != nullptr && a.ctrl != nullptr && (a.ctrl->iter % kWarmPeriod) != 0;
+    float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+
+    // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s
+    double wmax = 0.0;
+    for (int q = tid; q < s * s; q += NT) {
+        const int ra = q % s, cb = q / s;
+        if (ra < cb) continue;
+        wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv)));
+    }
+    wmax = block_max(wmax, red_d);
+    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    for (int q = tid; q < 32 * 32; q += NT) {
+        const int i = q >> 5, j = q & 31;
+        if (i >= s || j >= s) Ws[i][j] = 0.f;
+        if (warm) Vs[i][j] = (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
+    }
+    for (int q = tid; q < s * s; q += NT) {
+        const int ra = q % s, cb = q / s;
+        if (ra < cb) continue;
+        const float wt = (float)ldexp(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv), -e2);
+        Ws[ra][cb] = wt;
+        Ws[cb][ra] = wt;
+    }
+    __syncthreads();
+
+    // ---- shift sigma = ||W||_F and the initial columns: G = B V, V = I (cold) or stored
+    float sq[1] = {0.f};
+#pragma unroll
+    for (int k = 0; k < kOSRows; ++k) sq[0] = fmaf(Ws[r0 + k][lane], Ws[r0 + k][lane], sq[0]);
+    block_sum_t<float, 1>(sq, red_f);
+    const float sigma = sqrtf(sq[0]);
+    float g[kOSRows], v[kOSRows];
+    if (warm) {
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) {
+            const int r = r0 + k;
+            v[k] = Vs[r][lane];
+            float acc = sigma * v[k];
+            for (int m = 0; m < 32; ++m) acc = fmaf(Ws[r][m], Vs[m][lane], acc);
+            g[k] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) {
+            const int r = r0 + k;
+            v[k] = r == lane ? 1.f : 0.f;
+            g[k] = Ws[r][lane] + ((r == lane && lane < N) ? sigma : 0.f);
+        }
+    }
+    if (lane >= N) {
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) g[k] = 0.f;
+    }
+
+    // ---- sweeps
+    int sweeps = 0;
+    for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
+        float pa = 0.f;
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) pa = fmaf(g[k], g[k], pa);
+        s_red[w][lane] = pa;
+        __syncthreads();
+        float alpha = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
+        float worst = 0.f;
+        for (int rd = 0; rd < N - 1; ++rd) {
+            const int p = rr_partner(lane, rd, N);
+            float gp[kOSRows];
+            float pg = 0.f;
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) {
+                gp[k] = __shfl_sync(0xffffffffu, g[k], p);
+                pg = fmaf(g[k], gp[k], pg);
+            }
+            const int buf = rd & 1;
+            s_gam[buf][w][lane] = pg;
+            __syncthreads();
+            const float gam = (s_gam[buf][0][lane] + s_gam[buf][1][lane]) + (s_gam[buf][2][lane] + s_gam[buf][3][lane]);
+            const float beta = __shfl_sync(0xffffffffu, alpha, p);
+            const bool first = lane < p;
+            const float ai = first ? alpha : beta, aj = first ? beta : alpha;
+            float c = 1.f, sn = 0.f, t = 0.f;
+            if (p != lane && fabsf(gam) > 1.0e-30f) {
+                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
+                const float zeta = __fdividef(aj - ai, 2.f * gam);
+                const float az = fabsf(zeta);
+                float den;
+                if (az > 1.0e15f) {
+                    den = 2.f * az;
+                } else {
+                    const float x = fmaf(zeta, zeta, 1.f);
+                    den = az + x * rsqrtf(x);
+                }
+                t = copysignf(__fdividef(1.f, den), zeta);
+                c = __frsqrt_rn(fmaf(t, t, 1.f));
+                sn = t * c;
+            }
+            // g_i' = c g_i - s g_j (lane i),  g_j' = s g_i + c g_j (lane j)
+            const float sg = first ? -sn : sn;
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) g[k] = fmaf(sg, gp[k], c * g[k]);
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) {
+                const float vp = __shfl_sync(0xffffffffu, v[k], p);
+                v[k] = fmaf(sg, vp, c * v[k]);
+            }
+            alpha = first ? ai - t * gam : aj + t * gam;
+        }
+        ++sweeps;
+        float wr[1] = {worst};
+        // largest squared ratio of the sweep over the whole CTA
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wr[0] = fmaxf(wr[0], __shfl_xor_sync(0xffffffffu, wr[0], o));
+        if (lane == 0) s_red[w][0] = wr[0];
+        __syncthreads();
+        const float wmx = fmaxf(fmaxf(s_red[0][0], s_red[1][0]), fmaxf(s_red[2][0], s_red[3][0]));
+        __syncthreads();
+        if (wmx < kOneSidedTol * kOneSidedTol) break;
+    }
+
+    // ---- eigenvalues lambda_j = v_j . g_j - sigma, clipped; V into Ws (and HBM)
+    float pr = 0.f;
+#pragma unroll
+    for (int k = 0; k < kOSRows; ++k) pr = fmaf(v[k], g[k], pr);
+    s_red[w][lane] = pr;
+    __syncthreads();
+    if (w == 0) {
+        const float lam = ((s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane])) - sigma;
+        dp[lane] = (lane < N && lam > 0.f) ? lam : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kOSRows; ++k) Ws[r0 + k][lane] = v[k];
+    if (vglob != nullptr && lane < N) {
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k)
+            if (r0 + k < N) vglob[(r0 + k) * N + lane] = v[k];
+    }
+    __syncthreads();
+
+    // ---- rebuild the lower triangle of V diag(max(lambda, 0)) V^T and apply the epilogue
+    double pv[3] = {0.0, 0.0, 0.0};
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
+    for (int q = tid; q < s * s; q += NT) {
+        const int ra = q % s, cb = q / s;
+        if (ra < cb) continue;
+        float acc = 0.f;
+        for (int i = 0; i < N; ++i) acc = fmaf(Ws[ra][i] * dp[i], Ws[cb][i], acc);
+        const double xv = ldexp((double)acc, e2);
+        const int pos = packed_pos(ra, cb, s);
+        if (MODE == PROJ_PRIMAL) {
+            const double u = a.x[a.gather_idx[off + pos]];
+            const double l = a.lam[off + pos];
+            const double d = xv - u;
+            xk_new[off + pos] = xv;
+            a.lam[off + pos] = l + a.rho * d;                  // Eq. LambdakUpdate
+            const double wgt = (ra == cb) ? 1.0 : 2.0;
+            pv[0] += wgt * d * d;
+            pv[1] += wgt * xv * xv;
+            pv[2] += wgt * u * u;
+        } else {
+            a.out[off + pos] = xv;
+        }
+    }
+    if (MODE == PROJ_PRIMAL) {
+        block_sum_t<double, 3>(pv, red_d);
+        if (tid == 0) {
+            a.part[blk * 4 + 0] = pv[0];
+            a.part[blk * 4 + 1] = pv[1];
+            a.part[blk * 4 + 2] = pv[2];
+        }
+    }
+    if (a.part != nullptr && tid == 0) a.part[blk * 4 + 3] = (double)sweeps;
+}
+
+template <typename T, int MODE, class SH>
 cudaError_t prepare_one() {
-    const size_t smem =
-        project_smem_bytes(SDP_MAX_CLIQUE, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
-    return cudaFuncSetAttribute(k_project<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    const size_t smem = project_smem_bytes(SDP_MAX_CLIQUE, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
+    return cudaFuncSetAttribute(k_project<T, MODE, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T, int MODE>
-cudaError_t launch_one(const ProjArgs& a, int smax, cudaStream_t st) {
+cudaError_t prepare_mode() {
+    cudaError_t e;
+    if ((e = prepare_one<T, MODE, ShapeS16>()) != cudaSuccess) return e;
+    if ((e = prepare_one<T, MODE, ShapeS32>()) != cudaSuccess) return e;
+    if ((e = prepare_one<T, MODE, ShapeS64>()) != cudaSuccess) return e;
+    return prepare_one<T, MODE, ShapeS96>();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_mode(const ProjArgs& a, int smax, cudaStream_t st) {
     const size_t smem = project_smem_bytes(smax, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
     const double rinv = 1.0 / a.rho;
-    k_project<T, MODE><<<a.count, project_threads(smax), smem, st>>>(a, rinv);
+    const int N = smax + (smax & 1);
+    if (sizeof(T) == 4 && N <= 32) {
+        k_project_os<MODE><<<a.count, 32 * kOSWarps, 0, st>>>(a, rinv);
+        return cudaGetLastError();
+    }
+    if (N <= 16) k_project<T, MODE, ShapeS16><<<a.count, ShapeS16::NT, smem, st>>>(a, rinv);
+    else if (N <= 32) k_project<T, MODE, ShapeS32><<<a.count, ShapeS32::NT, smem, st>>>(a, rinv);
+    else if (N <= 64) k_project<T, MODE, ShapeS64><<<a.count, ShapeS64::NT, smem, st>>>(a, rinv);
+    else k_project<T, MODE, ShapeS96><<<a.count, ShapeS96::NT, smem, st>>>(a, rinv);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t project_smem_bytes(int smax, int prec, int mode) {
+    (void)mode;
     const int N = smax + (smax & 1);
     const int LD = N + 1;
     const size_t tsz = prec == SDP_PROJ_FP32 ? 4 : 8;
-    size_t bytes = ((size_t)2 * N * LD + N) * tsz;
-    bytes = (bytes + 15) & ~(size_t)15;
-    if (mode == PROJ_PRIMAL) bytes += (size_t)N * (N + 1) / 2 * sizeof(double);
-    return bytes;
+    return ((size_t)3 * N * LD + N) * tsz;
 }
 
 int project_threads(int smax) {
-    if (smax <= 16) return 64;
-    if (smax <= 32) return 256;
-    return 512;
+    const int N = smax + (smax & 1);
+    if (N <= 16) return ShapeS16::NT;
+    if (N <= 32) return ShapeS32::NT;
+    return ShapeS64::NT;
+}
+
+size_t project_vstore_elems(int s) {
+    const int N = s + (s & 1);
+    return (size_t)N * N;
 }
 
 cudaError_t project_prepare() {
     cudaError_t e;
-    if ((e = prepare_one<float, PROJ_PLAIN>()) != cudaSuccess) return e;
-    if ((e = prepare_one<float, PROJ_PRIMAL>()) != cudaSuccess) return e;
-    if ((e = prepare_one<float, PROJ_DUAL>()) != cudaSuccess) return e;
-    if ((e = prepare_one<double, PROJ_PLAIN>()) != cudaSuccess) return e;
-    if ((e = prepare_one<double, PROJ_PRIMAL>()) != cudaSuccess) return e;
-    return prepare_one<double, PROJ_DUAL>();
+    if ((e = prepare_mode<float, PROJ_PLAIN>()) != cudaSuccess) return e;
+    if ((e = prepare_mode<float, PROJ_PRIMAL>()) != cudaSuccess) return e;
+    if ((e = prepare_mode<float, PROJ_DUAL>()) != cudaSuccess) return e;
+    if ((e = prepare_mode<double, PROJ_PLAIN>()) != cudaSuccess) return e;
+    if ((e = prepare_mode<double, PROJ_PRIMAL>()) != cudaSuccess) return e;
+    return prepare_mode<double, PROJ_DUAL>();
 }
 
 cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     if (prec == SDP_PROJ_FP32) {
-        if (mode == PROJ_PLAIN) return launch_one<float, PROJ_PLAIN>(a, smax, st);
-        if (mode == PROJ_PRIMAL) return launch_one<float, PROJ_PRIMAL>(a, smax, st);
-        return launch_one<float, PROJ_DUAL>(a, smax, st);
+        if (mode == PROJ_PLAIN) return launch_mode<float, PROJ_PLAIN>(a, smax, st);
+        if (mode == PROJ_PRIMAL) return launch_mode<float, PROJ_PRIMAL>(a, smax, st);
+        return launch_mode<float, PROJ_DUAL>(a, smax, st);
     }
-    if (mode == PROJ_PLAIN) return launch_one<double, PROJ_PLAIN>(a, smax, st);
-    if (mode == PROJ_PRIMAL) return launch_one<double, PROJ_PRIMAL>(a, smax, st);
-    return launch_one<double, PROJ_DUAL>(a, smax, st);
+    if (mode == PROJ_PLAIN) return launch_mode<double, PROJ_PLAIN>(a, smax, st);
+    if (mode == PROJ_PRIMAL) return launch_mode<double, PROJ_PRIMAL>(a, smax, st);
+    return launch_mode<double, PROJ_DUAL>(a, smax, st);
 }
 
 }  // namespace cadmm

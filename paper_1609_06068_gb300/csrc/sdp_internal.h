@@ -17,6 +17,7 @@ struct Ctrl {
     int iter_limit;  // the call stops when iter reaches this
     int done;        // nonzero: remaining kernels return immediately
     int status;      // SDP_OK / SDP_MAX_ITER / SDP_ERR_NAN once done
+    unsigned int ticket;  // CTAs of the iteration's last kernel that have finished (last one finalizes)
     double tol;
     double eps_p, eps_d, obj_p, obj_d;
 };
@@ -31,11 +32,13 @@ struct HostProblem {
     std::vector<int> blk_off;                   // [p+1]
     std::vector<int> blk_size;                  // [p]
     std::vector<int> order;                     // [p] cliques by descending size
+    std::vector<long long> voff;                // [p+1] eigenvector block offsets (N_k^2 each)
     std::vector<int> gather_idx;                // [SL]
     std::vector<unsigned char> pos_w;           // [SL] 1 on block diagonals, 2 elsewhere
     std::vector<int> sc_ptr;                    // [nEL+1]
     std::vector<int> sc_pos;                    // [SL]
-    std::vector<double> D, wdinv, c, b;         // D, w/D, c on E_L; b
+    std::vector<int> heavy;                     // E_L entries covered by more than kHeavyCount cliques
+    std::vector<double> D, dinv, wdinv, c, b;   // D, 1/D, w/D, c on E_L; b
     std::vector<unsigned char> ew;              // [nEL] weight 1 (diagonal) or 2
     std::vector<int> a_rowptr, a_col;           // CSR of A (rows = constraints)
     std::vector<double> a_val;
@@ -71,9 +74,15 @@ struct ProjArgs {
     double* lam;
     const double* v;
     double* xk[2];          // primal ping-pong buffers, chosen by ctrl->iter parity
-    double* part;           // [count * 4] per-clique residual partials
+    double* part;           // [count * 4] per-clique residual partials and Jacobi sweep counts
+    void* vstore;           // per-clique eigenvectors kept for warm starts (NULL: always cold)
+    const long long* voff;  // [*] element offset of each clique's N x N block in vstore
     const Ctrl* ctrl;       // NULL for the standalone entry
 };
+
+// Entries covered by more cliques than this are scattered by a whole warp (in ascending clique
+// order, so the sum is the same as the sequential one).
+constexpr int kHeavyCount = 16;
 
 struct IterPtrs {
     // problem
@@ -81,7 +90,8 @@ struct IterPtrs {
     const int* blk_off; const long long* blk_off64; const int* blk_size; const int* order;
     const int* gather_idx; const unsigned char* pos_w;
     const int* sc_ptr; const int* sc_pos;
-    const double* D; const double* wdinv; const double* c; const double* b;
+    const int* heavy; int n_heavy, heavy_ctas;     // warp-per-entry scatter of heavily shared entries
+    const double* D; const double* dinv; const double* wdinv; const double* c; const double* b;
     const unsigned char* ew;
     const int* a_rowptr; const int* a_col; const double* a_val;
     const int* c_colptr; const unsigned short* c_row; const double* c_val;
@@ -89,9 +99,11 @@ struct IterPtrs {
     // state
     double* x; double* y; double* r; double* rsw; double* z1;
     double* xk[2]; double* lam; double* vk;
+    void* vstore;         // eigenvector blocks for warm starts (projection precision)
+    const long long* voff;
     double* tpart;        // [m * R]
     double* part_blk;     // [p * 4]
-    double* part_ent;     // [ent_ctas * 8]
+    double* part_ent;     // [(max(ent_ctas + heavy_ctas, pos_ctas)) * 8]
     double* part_obj;     // [col_ctas]
     int ent_ctas, col_ctas, pos_ctas;
     Ctrl* ctrl;
@@ -102,6 +114,8 @@ cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cuda
 cudaError_t project_prepare();   // raises the dynamic shared-memory limit of every variant
 size_t project_smem_bytes(int smax, int prec, int mode);
 int project_threads(int smax);
+size_t project_vstore_elems(int s);   // N*N with N = s rounded up to even
+cudaError_t launch_vstore_identity(const IterPtrs& P, int prec, cudaStream_t st);
 
 cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, cudaStream_t st,
                              cudaEvent_t* ev = nullptr);

@@ -75,6 +75,12 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     }
     hp.blk_off[p] = (int)SL;
     hp.SL = (int)SL;
+    hp.voff.resize(p + 1);
+    hp.voff[0] = 0;
+    for (int k = 0; k < p; ++k) {
+        const long long Nk = hp.blk_size[k] + (hp.blk_size[k] & 1);
+        hp.voff[k + 1] = hp.voff[k] + Nk * Nk;
+    }
 
     // Processing order: largest cliques first (stable), so the longest eigensolves start first.
     hp.order.resize(p);
@@ -129,11 +135,15 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         std::vector<int> fillp(hp.sc_ptr.begin(), hp.sc_ptr.end() - 1);
         for (long long q = 0; q < SL; ++q) hp.sc_pos[fillp[hp.gather_idx[q]]++] = (int)q;
     }
+    for (int e = 0; e < nEL; ++e)
+        if (hp.sc_ptr[e + 1] - hp.sc_ptr[e] > kHeavyCount) hp.heavy.push_back(e);
     // D = sum_k H_k^T H_k (Section III.B.1): number of cliques covering each entry.
     hp.D.resize(nEL);
+    hp.dinv.resize(nEL);
     hp.wdinv.resize(nEL);
     for (int e = 0; e < nEL; ++e) {
         hp.D[e] = (double)(hp.sc_ptr[e + 1] - hp.sc_ptr[e]);
+        hp.dinv[e] = 1.0 / hp.D[e];
         hp.wdinv[e] = (double)hp.ew[e] / hp.D[e];
     }
 

@@ -65,8 +65,9 @@ def test_iteration_from_oracle_state(name, form):
         cadmm.sdp_set_state(s.h, **oracle_state_to_abi(sdp, st))
         r = s.iterate(1)
         compare_state(s.state(), sdp, nxt)
-        assert abs(r["eps_p"] - nxt["eps_p"]) <= 1e-8 * nxt["eps_p"]
-        assert abs(r["eps_d"] - nxt["eps_d"]) <= 1e-8 * nxt["eps_d"]
+        # residuals are ratios of norms; near rounding level only an absolute bound is meaningful
+        assert abs(r["eps_p"] - nxt["eps_p"]) <= 1e-8 * nxt["eps_p"] + 1e-12
+        assert abs(r["eps_d"] - nxt["eps_d"]) <= 1e-8 * nxt["eps_d"] + 1e-12
 
 
 @pytest.mark.parametrize("form", ["primal", "dual"])
