@@ -181,6 +181,25 @@ int project_psd_batched(const double* in, double* out, const int* sizes, const l
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
 const char* sdp_phase_name(int form, int i);
 
+/* Batched PSD projection that allocates nothing (no counterpart in the paper: it exists for
+ * callers, not for the method). Same arguments, kernels and results as project_psd_batched, for
+ * callers that may not allocate device memory: code embedded in a host framework that owns all
+ * device memory through a pool sized up front, and latency-bound loops where a cudaMalloc (which
+ * may synchronize the device) is not acceptable. The per-call block schedule goes into a fixed
+ * array compiled into the library (SDP_NOALLOC_MAX_BLOCKS blocks, 384 KiB, held by every GPU that
+ * loads the library until the process exits) instead of an allocated buffer.
+ *   - count > SDP_NOALLOC_MAX_BLOCKS returns SDP_ERR_UNSUPPORTED; other errors as for
+ *     project_psd_batched.
+ *   - The first call on each device looks up the array's device address and prepares the kernels;
+ *     make that first call before any stream capture.
+ *   - Every call reuses the same array, which keeps the last call's schedule. Each call
+ *     overwrites every entry it reads, so nothing needs clearing, but calls that overlap on the
+ *     GPU (e.g. on two streams) race on the array: order them on one stream or synchronize.
+ *   - Blocks run in the caller's order rather than largest first. */
+#define SDP_NOALLOC_MAX_BLOCKS 32768
+int project_psd_batched_noalloc(const double* in, double* out, const int* sizes,
+                                const long long* offsets, int count, int prec, void* cuda_stream);
+
 void sdp_free(sdp_handle h);
 const char* sdp_status_string(int status);
 const char* sdp_last_error(void);

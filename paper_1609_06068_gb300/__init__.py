@@ -40,9 +40,10 @@ PRECS = {"fp64": SDP_PROJ_FP64, "fp32": SDP_PROJ_FP32}
 EXPORTS = [
     "sdp_setup", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
-    "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name", "sdp_free",
-    "sdp_status_string", "sdp_last_error",
+    "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
+    "project_psd_batched_noalloc", "sdp_free", "sdp_status_string", "sdp_last_error",
 ]
+SDP_NOALLOC_MAX_BLOCKS = 32768
 
 
 class SDPError(RuntimeError):
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "project_psd_batched": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "sdp_time_phases": (_I, [_P, _I, _P, _P, _I]),
         "sdp_phase_name": (ctypes.c_char_p, [_I, _I]),
+        "project_psd_batched_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "sdp_free": (None, [_P]),
         "sdp_status_string": (ctypes.c_char_p, [_I]),
         "sdp_last_error": (ctypes.c_char_p, []),
@@ -280,6 +282,19 @@ def project_psd_batched(inp, out, sizes, offsets, prec="fp64", stream=None):
                                               _ptr(sizes), _ptr(offsets), len(sizes),
                                               PRECS.get(prec, prec), _stream(stream)),
            "project_psd_batched")
+
+
+def project_psd_batched_noalloc(inp, out, sizes, offsets, prec="fp64", stream=None):
+    """project_psd_batched without any device allocation (fixed in-library schedule array of
+    SDP_NOALLOC_MAX_BLOCKS blocks; calls must not overlap on the GPU)."""
+    sizes = _arr(sizes, np.int32)
+    offsets = _arr(offsets, np.int64)
+    if len(sizes) != len(offsets):
+        raise ValueError("sizes and offsets differ in length")
+    need = int((offsets + sizes.astype(np.int64) * (sizes + 1) // 2).max()) if len(sizes) else 0
+    _check(load_library().project_psd_batched_noalloc(
+        _dev_ptr(inp, need, "inp"), _dev_ptr(out, need, "out"), _ptr(sizes), _ptr(offsets), len(sizes),
+        PRECS.get(prec, prec), _stream(stream)), "project_psd_batched_noalloc")
 
 
 def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:

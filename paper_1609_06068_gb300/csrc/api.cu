@@ -65,6 +65,10 @@ int check_opts(const admm_opts* o) {
 
 }  // namespace
 
+namespace cadmm {
+int record_error(int code, const std::string& msg) { return set_err(code, msg); }
+}  // namespace cadmm
+
 struct sdp_ctx {
     int device = 0;
     admm_opts opts{};

@@ -127,6 +127,7 @@ cudaError_t launch_ctrl_arm(Ctrl* ctrl, int n_iters, double tol, cudaStream_t st
 cudaError_t launch_ctrl_reset(Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_ctrl_clear(Ctrl* ctrl, cudaStream_t st);
 int iteration_kernel_count(int form);
+int record_error(int code, const std::string& msg);   // sets the message sdp_last_error() returns
 cudaError_t iteration_prepare();  // raises the dynamic shared-memory limit of the m-sized kernels
 
 }  // namespace cadmm
