@@ -31,7 +31,7 @@ METRIC = "ADMM iter/s & time-to-1e-4 residual: batched FP32 vs plain FP64, one G
 UNIT = "iter/s"
 FLUSH_BYTES = 256 << 20          # > 129 MB L2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 # Device constants used for the ALU roofline (GB300: 152 SMs, 128 FP32 lanes per SM, FP64 at
 # 1.25 TFLOP/s nominal for the whole GPU).
 NUM_SMS = 152
@@ -184,13 +184,17 @@ def roofline(phases, inst_sizes, cfg, prec, peaks, clocks):
     name = max(phases, key=phases.get)
     bound, amount, unit = kernel_model(name, inst_sizes, cfg, prec)
     ms = phases[name]
+    # DRAM bytes of one launch from the committed ncu summary, used only while the kernel sources
+    # are the ones that were profiled.
     traffic = None
     try:
+        sha = source_sha()
         with open(TRAFFIC_FILE) as f:
-            tr = json.load(f)
-        entry = tr.get(f"{name}:{prec}")
-        if entry and entry.get("source_sha") == source_sha():
-            traffic = entry["dram_bytes_per_launch"]
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and not line.startswith("#") and parts[0] == name and parts[1] == prec \
+                        and parts[3] == sha:
+                    traffic = float(parts[2])
     except (OSError, ValueError):
         pass
     if bound == "alu":
