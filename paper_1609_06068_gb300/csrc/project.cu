@@ -455,11 +455,13 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
 // partner column's rows arrive by warp shuffles, the four warps' partial gammas meet in shared
 // memory (one barrier per round), and both lanes of a pair compute the same rotation from the same
 // sums. Rounds follow the round-robin schedule, so a sweep of N-1 rounds meets every pair once.
-// After a sweep whose largest |gamma| / sqrt(alpha beta) is below the tolerance, V holds the
-// eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since G = B V).
+// After a sweep whose largest |gamma| / sqrt(alpha beta) was below kOneSidedStop when it began,
+// V holds the eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since G = B V).
 constexpr int kOSWarps = 4;
 constexpr int kOSRows = 8;                 // rows per warp: 4 x 8 = 32
-constexpr float kOneSidedTol = 1.0e-6f;
+// Cyclic Jacobi converges quadratically: a sweep that starts with every pair within
+// kOneSidedStop of orthogonal leaves them within about its square, below FP32 resolution.
+constexpr float kOneSidedStop = 1.0e-4f;
 constexpr int kOneSidedMaxSweeps = 20;
 
 // Round-robin partner of player i in round rd for N players (N even, n = N - 1 odd): player n
@@ -477,6 +479,8 @@ template <int MODE>
 __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double rinv) {
     __shared__ float Ws[32][33];                 // W, then V for the rebuild
     __shared__ float Vs[32][33];                 // previous eigenvectors (warm start)
+    __shared__ float Ss[32][33];                 // V^T V of the previous eigenvectors
+    __shared__ unsigned char s_partner[32][32];  // round-robin partner by round and lane
     __shared__ float s_gam[2][kOSWarps][32];     // partial gamma per warp, by round parity
     __shared__ float s_red[kOSWarps][32];
     __shared__ float dp[32];
@@ -491,8 +495,11 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     const long long off = a.off[blk];
     const int N = s + (s & 1);
     const int r0 = w * kOSRows;
-    const bool warm = a.vstore != nullptr && a.ctrl != nullptr && (a.ctrl->iter % kWarmPeriod) != 0;
+    // Warm start whenever eigenvectors are kept (they are the identity right after a reset); the
+    // stored V is re-orthonormalized below, so no periodic cold start is needed.
+    const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+    for (int q = tid; q < 32 * 32; q += NT) s_partner[q >> 5][q & 31] = (unsigned char)rr_partner(q & 31, q >> 5, N);
 
     // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s
     double wmax = 0.0;
@@ -525,10 +532,31 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     const float sigma = sqrtf(sq[0]);
     float g[kOSRows], v[kOSRows];
     if (warm) {
+        // One Newton-Schulz step V <- V (3I - V^T V) / 2 removes the rounding drift that the
+        // rotations of earlier iterations left in the stored eigenvectors (quadratic in it).
+        for (int q = tid; q < 32 * 32; q += NT) {
+            const int i = q >> 5, j = q & 31;
+            if (j < i) continue;
+            float acc = 0.f;
+            for (int r = 0; r < 32; ++r) acc = fmaf(Vs[r][i], Vs[r][j], acc);
+            Ss[i][j] = acc;
+            Ss[j][i] = acc;
+        }
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < kOSRows; ++k) {
             const int r = r0 + k;
-            v[k] = Vs[r][lane];
+            float acc = 0.f;
+            for (int m = 0; m < 32; ++m) acc = fmaf(Vs[r][m], Ss[m][lane], acc);
+            v[k] = fmaf(-0.5f, acc, 1.5f * Vs[r][lane]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) Vs[r0 + k][lane] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) {
+            const int r = r0 + k;
             float acc = sigma * v[k];
             for (int m = 0; m < 32; ++m) acc = fmaf(Ws[r][m], Vs[m][lane], acc);
             g[k] = acc;
@@ -557,7 +585,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
         float alpha = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
         float worst = 0.f;
         for (int rd = 0; rd < N - 1; ++rd) {
-            const int p = rr_partner(lane, rd, N);
+            const int p = s_partner[rd][lane];
             float gp[kOSRows];
             float pg = 0.f;
 #pragma unroll
@@ -608,7 +636,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
         __syncthreads();
         const float wmx = fmaxf(fmaxf(s_red[0][0], s_red[1][0]), fmaxf(s_red[2][0], s_red[3][0]));
         __syncthreads();
-        if (wmx < kOneSidedTol * kOneSidedTol) break;
+        if (wmx < kOneSidedStop * kOneSidedStop) break;
     }
 
     // ---- eigenvalues lambda_j = v_j . g_j - sigma, clipped; V into Ws (and HBM)
