@@ -167,8 +167,9 @@ def kernel_model(name, inst_sizes, cfg, prec):
         return "alu", flops, "flop"
     if name in ("spmv_rows",):
         return "hbm", nnz * 12.0 + nEL * 8.0, "byte"
-    if name in ("spmv_cols",):
+    if name == "spmv_cols":
         return "hbm", nnz * 10.0 + (nEL + 1) * 4.0 + nEL * (8 * 3 + 1) + m * 8.0, "byte"
+
     if name in ("tri_lower", "tri_upper"):
         return "hbm", m * (m + 1) / 2 * 8.0 + 2 * m * 8.0, "byte"
     if name.startswith("scatter_dual"):

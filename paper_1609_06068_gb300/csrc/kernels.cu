@@ -8,7 +8,7 @@
 //                DualMultUpdate with the sign Eq. MultUpdateDualSDP implies)
 // The residuals, objectives and stop test of an iteration are computed by the last CTA to finish
 // the iteration's final kernel (scatter in the primal form, update in the dual form), reading
-// every partial sum in a fixed order.
+// every partial sum in a fixed order. Kernels are launched with programmatic dependent launch.
 // Every kernel starts by reading the device control block and returns at once when the solve is
 // done, so a captured graph holding several iterations can run past convergence at no cost.
 // All reductions use a fixed tree, so results are bitwise reproducible run to run.
@@ -130,6 +130,7 @@ __device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int
 // its lanes form 32 terms at a time and every lane adds them in ascending clique order.
 __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, double rho, int use_current) {
     __shared__ double red[33 * 2];
+    pdl_wait();
     if (P.ctrl->done) return;
     const bool odd = (P.ctrl->iter & 1) != 0;
     const double* cur = odd ? P.xk[1] : P.xk[0];
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
         }
     }
     if (use_current) return;
+    pdl_trigger();
     block_sum<2>(v, red);
     if (threadIdx.x == 0) {
         P.part_ent[blockIdx.x * 8 + 0] = v[0];
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
 // r = c - sum_k H_k^T(z_k + rho^-1 lambda_k), ascending k from the first term; the same split
 // between light entries (one per thread) and heavily shared ones (one per warp).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double rinv) {
+    pdl_wait();
     if (P.ctrl->done) return;
     const double* z = P.xk[0];
     if ((int)blockIdx.x < P.ent_ctas) {
@@ -256,6 +259,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
 // Four independent accumulators per thread keep several gathers in flight.
 __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     __shared__ double red[33];
+    pdl_wait();
     if (P.ctrl->done) return;
     const int i = blockIdx.x / P.R, ch = blockIdx.x - (blockIdx.x / P.R) * P.R;
     const int lo0 = P.a_rowptr[i], hi0 = P.a_rowptr[i + 1];
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
         a3 = fma(P.a_val[j + 3 * bd], P.rsw[P.a_col[j + 3 * bd]], a3);
     }
     for (; j < hi; j += bd) a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
+    pdl_trigger();
     double v[1] = {(a0 + a1) + (a2 + a3)};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) P.tpart[blockIdx.x] = v[0];
@@ -280,6 +285,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
 // rhs2 = b (primal) or -rho^-1 b (dual). One warp per row of L^-1.
 __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double rinv, int form) {
     extern __shared__ double u[];
+    pdl_wait();
     if (P.ctrl->done) return;
     const int m = P.m, R = P.R;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -307,6 +313,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
 // ---------------------------------------------------------------- y = L^-T z
 __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
     extern __shared__ double zs[];
+    pdl_wait();
     if (P.ctrl->done) return;
     const int m = P.m;
     for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = P.z1[i];
@@ -332,6 +339,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
 __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
     extern __shared__ double ys[];
     __shared__ double red[33];
+    pdl_wait();
     if (P.ctrl->done) return;
     for (int i = threadIdx.x; i < P.m; i += blockDim.x) ys[i] = P.y[i];
     __syncthreads();
@@ -360,38 +368,42 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
             obj = fma((double)P.ew[e] * P.c[e], xe, obj);
         }
     }
+    pdl_trigger();
     double v[1] = {obj};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) P.part_obj[blockIdx.x] = v[0];
 }
 
 // ---------------------------------------------------------------- dual-form multiplier update
+// v_k = z_k + rho^-1 lambda_k + H_k x (Eq. vkEqn), lambda_k = -rho H_k x (Eq. DualMultUpdate with
+// the sign Eq. MultUpdateDualSDP implies), and the residual sums; the last CTA finalizes.
 __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double rho, double rinv) {
     __shared__ double red[33 * 5];
+    pdl_wait();
     if (P.ctrl->done) return;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos < P.SL) {
+    for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < P.SL; pos += gridDim.x * blockDim.x) {
         const double u = P.x[P.gather_idx[pos]];
         const double z = P.xk[0][pos], l = P.lam[pos], vo = P.vk[pos];
-        const double vn = __dadd_rn(__dadd_rn(z, __dmul_rn(rinv, l)), u);   // Eq. vkEqn
-        const double ln = __dmul_rn(-rho, u);                                // Eq. DualMultUpdate
+        const double vn = __dadd_rn(__dadd_rn(z, __dmul_rn(rinv, l)), u);
+        const double ln = __dmul_rn(-rho, u);
         P.vk[pos] = vn;
         P.lam[pos] = ln;
         const double w = (double)P.pos_w[pos];
         const double d1 = z - vn, d2 = vn - vo;
-        v[0] = w * d1 * d1;
-        v[1] = w * z * z;
-        v[2] = w * vn * vn;
-        v[3] = w * d2 * d2;
-        v[4] = w * ln * ln;
+        v[0] = fma(w * d1, d1, v[0]);
+        v[1] = fma(w * z, z, v[1]);
+        v[2] = fma(w * vn, vn, v[2]);
+        v[3] = fma(w * d2, d2, v[3]);
+        v[4] = fma(w * ln, ln, v[4]);
     }
+    pdl_trigger();
     block_sum<5>(v, red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) P.part_ent[blockIdx.x * 8 + k] = v[k];
     }
-    finish_and_maybe_finalize(P, SDP_DUAL, rho, P.pos_ctas);
+    finish_and_maybe_finalize(P, SDP_DUAL, rho, (int)gridDim.x);
 }
 
 __global__ void k_ctrl_arm(Ctrl* C, int n_iters, double tol) {
@@ -473,17 +485,23 @@ struct Marks {
     }
 };
 
-cudaError_t launch_affine(const IterPtrs& P, int form, double rinv, cudaStream_t st, Marks& mk) {
+cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, cudaStream_t st, Marks& mk) {
+    cudaError_t e;
     mk.mark();
-    k_spmv_rows<<<P.m * P.R, kRowThreads, 0, st>>>(P);
+    if ((e = launch_pdl(k_spmv_rows, dim3(P.m * P.R), dim3(kRowThreads), 0, st, P)) != cudaSuccess) return e;
     const int tri_ctas = cdiv(P.m, kTriThreads / 32);
+    const size_t msm = (size_t)P.m * sizeof(double);
     mk.mark();
-    k_tri_lower<<<tri_ctas, kTriThreads, (size_t)P.m * sizeof(double), st>>>(P, rinv, form);
+    if ((e = launch_pdl(k_tri_lower, dim3(tri_ctas), dim3(kTriThreads), msm, st, P, rinv, form)) != cudaSuccess) return e;
     mk.mark();
-    k_tri_upper<<<tri_ctas, kTriThreads, (size_t)P.m * sizeof(double), st>>>(P);
+    if ((e = launch_pdl(k_tri_upper, dim3(tri_ctas), dim3(kTriThreads), msm, st, P)) != cudaSuccess) return e;
     mk.mark();
-    k_spmv_cols<<<P.col_ctas, kColThreads, (size_t)P.m * sizeof(double), st>>>(P);
-    return cudaGetLastError();
+    if ((e = launch_pdl(k_spmv_cols, dim3(P.col_ctas), dim3(kColThreads), msm, st, P)) != cudaSuccess) return e;
+    if (form == SDP_DUAL) {
+        mk.mark();
+        return launch_pdl(k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -506,20 +524,22 @@ cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, 
     Marks mk{ev, st, 0};
     cudaError_t e;
     if (form == SDP_PRIMAL) {
-        if ((e = launch_affine(P, form, rinv, st, mk)) != cudaSuccess) return e;
+        if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_project(a, PROJ_PRIMAL, prec, P.smax, st)) != cudaSuccess) return e;
         mk.mark();
-        k_scatter_primal<<<P.ent_ctas + P.heavy_ctas, kEntThreads, 0, st>>>(P, rinv, rho, 0);
+        if ((e = launch_pdl(k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
+                            rho, 0)) != cudaSuccess)
+            return e;
     } else {
         a.out = P.xk[0];
         mk.mark();
         if ((e = launch_project(a, PROJ_DUAL, prec, P.smax, st)) != cudaSuccess) return e;
         mk.mark();
-        k_scatter_dual<<<P.ent_ctas + P.heavy_ctas, kEntThreads, 0, st>>>(P, rinv);
-        if ((e = launch_affine(P, form, rinv, st, mk)) != cudaSuccess) return e;
-        mk.mark();
-        k_update_dual<<<P.pos_ctas, kEntThreads, 0, st>>>(P, rho, rinv);
+        if ((e = launch_pdl(k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
+                            rinv)) != cudaSuccess)
+            return e;
+        if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
     }
     mk.mark();
     return cudaGetLastError();

@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     __shared__ T red_t[33 * 2];
     __shared__ double red_d[33 * 4];
 
+    pdl_wait();
     if (a.ctrl != nullptr && a.ctrl->done) return;
 
     const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
@@ -407,6 +408,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
         for (int q = tid; q < N * N; q += NT) vglob[q] = Vx[(q / N) * LD + (q % N)];
 
     // ---- rebuild the lower triangle of V diag(max(lambda, 0)) V^T and apply the epilogue
+    pdl_trigger();
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
@@ -487,6 +489,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     __shared__ double red_d[33 * 3];
     __shared__ float red_f[33 * 2];
 
+    pdl_wait();
     if (a.ctrl != nullptr && a.ctrl->done) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int NT = 32 * kOSWarps;
@@ -659,6 +662,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     __syncthreads();
 
     // ---- rebuild the lower triangle of V diag(max(lambda, 0)) V^T and apply the epilogue
+    pdl_trigger();
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
@@ -714,15 +718,12 @@ cudaError_t launch_mode(const ProjArgs& a, int smax, cudaStream_t st) {
     const size_t smem = project_smem_bytes(smax, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
     const double rinv = 1.0 / a.rho;
     const int N = smax + (smax & 1);
-    if (sizeof(T) == 4 && N <= 32) {
-        k_project_os<MODE><<<a.count, 32 * kOSWarps, 0, st>>>(a, rinv);
-        return cudaGetLastError();
-    }
-    if (N <= 16) k_project<T, MODE, ShapeS16><<<a.count, ShapeS16::NT, smem, st>>>(a, rinv);
-    else if (N <= 32) k_project<T, MODE, ShapeS32><<<a.count, ShapeS32::NT, smem, st>>>(a, rinv);
-    else if (N <= 64) k_project<T, MODE, ShapeS64><<<a.count, ShapeS64::NT, smem, st>>>(a, rinv);
-    else k_project<T, MODE, ShapeS96><<<a.count, ShapeS96::NT, smem, st>>>(a, rinv);
-    return cudaGetLastError();
+    if (sizeof(T) == 4 && N <= 32)
+        return launch_pdl(k_project_os<MODE>, dim3(a.count), dim3(32 * kOSWarps), 0, st, a, rinv);
+    if (N <= 16) return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
+    if (N <= 32) return launch_pdl(k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st, a, rinv);
+    if (N <= 64) return launch_pdl(k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st, a, rinv);
+    return launch_pdl(k_project<T, MODE, ShapeS96>, dim3(a.count), dim3(ShapeS96::NT), smem, st, a, rinv);
 }
 
 }  // namespace

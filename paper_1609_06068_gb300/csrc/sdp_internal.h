@@ -109,6 +109,37 @@ struct IterPtrs {
     Ctrl* ctrl;
 };
 
+// Programmatic dependent launch (a kernel scheduled while its predecessor finishes, waiting for it
+// in pdl_wait()) is wired through every iteration kernel but switched off: on GB300 it made the
+// captured iteration slower (FP32 projection 9.8k -> 9.0k iter/s, FP64 1.8k -> 0.9k iter/s on the
+// n = 1020 block-arrow workload). With the attribute off, pdl_wait()/pdl_trigger() are no-ops.
+constexpr bool kUsePDL = false;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = kUsePDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+#ifdef __CUDACC__
+// First statement of every kernel of an iteration: wait until the previous kernel in the stream
+// has completed and its writes are visible.
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
+// Called once a CTA's main work is done: the next kernel may start launching (its CTAs then wait
+// in pdl_wait). Triggering late keeps waiting CTAs off the SMs while this kernel still computes.
+__device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCompletion(); }
+#endif
+
 // Kernel launchers (kernels.cu / project.cu). All return cudaError_t of the launch.
 cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cudaStream_t st);
 cudaError_t project_prepare();   // raises the dynamic shared-memory limit of every variant
