@@ -447,20 +447,21 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP32, padded order N <= 32: one-sided (Hestenes) Jacobi, one CTA of four warps per clique.
+// FP32, padded order N <= 32 * CPL (CPL = 1, 2): one-sided (Hestenes) Jacobi, one CTA of 4 * CPL
+// warps per clique. Larger blocks and FP64 use the two-sided kernel above.
 //
-// Lane j holds column j of G = B V and of V, with B = W + sigma I and sigma = ||W||_F, so B is
-// positive semidefinite and its eigenvalues are lambda(W) + sigma (for an indefinite W, one-sided
-// Jacobi alone would confuse eigenvalues +mu and -mu). Warp w holds rows 8w .. 8w+7 of every
-// column, in registers. A rotation of columns (i, j) makes g_i and g_j orthogonal (Golub & Van
-// Loan's 2x2 formula on the Gram entries alpha = g_i.g_i, beta = g_j.g_j, gamma = g_i.g_j): the
-// partner column's rows arrive by warp shuffles, the four warps' partial gammas meet in shared
-// memory (one barrier per round), and both lanes of a pair compute the same rotation from the same
-// sums. Rounds follow the round-robin schedule, so a sweep of N-1 rounds meets every pair once.
-// After a sweep whose largest |gamma| / sqrt(alpha beta) was below kOneSidedStop when it began,
-// V holds the eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since G = B V).
-constexpr int kOSWarps = 4;
-constexpr int kOSRows = 8;                 // rows per warp: 4 x 8 = 32
+// Lane j holds columns j, j + 32, ... (CPL of them) of G = B V and of V, with B = W + sigma I and
+// sigma = ||W||_F, so B is positive semidefinite and its eigenvalues are lambda(W) + sigma (for an
+// indefinite W, one-sided Jacobi alone would confuse eigenvalues +mu and -mu). Warp w holds rows
+// 8w .. 8w+7 of every column, in registers. A rotation of columns (i, j) makes g_i and g_j
+// orthogonal (Golub & Van Loan's 2x2 formula on the Gram entries alpha = g_i.g_i, beta = g_j.g_j,
+// gamma = g_i.g_j): the partner column's rows arrive by warp shuffles, the warps' partial gammas
+// meet in shared memory (one barrier per round), and both ends of a pair compute the same rotation
+// from the same sums. Rounds follow the round-robin schedule, so a sweep of N-1 rounds meets every
+// pair once. After a sweep whose largest |gamma| / sqrt(alpha beta) was below kOneSidedStop when
+// it began, V holds the eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since
+// G = B V). Warm start: the stored eigenvectors, re-orthonormalized by one Newton-Schulz step.
+constexpr int kOSRows = 8;                 // rows per warp
 // Cyclic Jacobi converges quadratically: a sweep that starts with every pair within
 // kOneSidedStop of orthogonal leaves them within about its square, below FP32 resolution.
 constexpr float kOneSidedStop = 1.0e-4f;
@@ -477,22 +478,35 @@ __device__ __forceinline__ int rr_partner(int i, int rd, int N) {
     return j == i ? n : j;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double rinv) {
-    __shared__ float Ws[32][33];                 // W, then V for the rebuild
-    __shared__ float Vs[32][33];                 // previous eigenvectors (warm start)
-    __shared__ float Ss[32][33];                 // V^T V of the previous eigenvectors
-    __shared__ unsigned char s_partner[32][32];  // round-robin partner by round and lane
-    __shared__ float s_gam[2][kOSWarps][32];     // partial gamma per warp, by round parity
-    __shared__ float s_red[kOSWarps][32];
-    __shared__ float dp[32];
+template <int CPL>
+struct OSLayout {
+    static constexpr int NP = 32 * CPL;          // players (columns) and rows
+    static constexpr int NW = 4 * CPL;           // warps
+    static constexpr int LD = NP + 1;
+    // dynamic shared memory: W, V, V^T V (floats), then the partner table (bytes)
+    static constexpr size_t kMatBytes = (size_t)3 * NP * LD * sizeof(float);
+    static constexpr size_t kBytes = kMatBytes + (size_t)NP * NP;
+};
+
+template <int MODE, int CPL>
+__global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(ProjArgs a, double rinv) {
+    using L = OSLayout<CPL>;
+    constexpr int NP = L::NP, NW = L::NW, LD = L::LD;
+    extern __shared__ __align__(16) unsigned char smem_os[];
+    float* Ws = reinterpret_cast<float*>(smem_os);           // W, then V for the rebuild
+    float* Vs = Ws + NP * LD;                                // previous eigenvectors (warm start)
+    float* Ss = Vs + NP * LD;                                // V^T V of the previous eigenvectors
+    unsigned char* s_partner = smem_os + L::kMatBytes;       // [round][player]
+    __shared__ float s_gam[2][NW][NP];                       // partial gamma per warp, by parity
+    __shared__ float s_red[NW][NP];
+    __shared__ float dp[NP];
     __shared__ double red_d[33 * 3];
     __shared__ float red_f[33 * 2];
 
     pdl_wait();
     if (a.ctrl != nullptr && a.ctrl->done) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int NT = 32 * kOSWarps;
+    const int NT = 32 * NW;
     const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
     const int s = a.size[blk];
     const long long off = a.off[blk];
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     // stored V is re-orthonormalized below, so no periodic cold start is needed.
     const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
-    for (int q = tid; q < 32 * 32; q += NT) s_partner[q >> 5][q & 31] = (unsigned char)rr_partner(q & 31, q >> 5, N);
+    for (int q = tid; q < NP * NP; q += NT) s_partner[q] = (unsigned char)rr_partner(q % NP, q / NP, N);
 
     // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s
     double wmax = 0.0;
@@ -513,151 +527,233 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
     }
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    for (int q = tid; q < 32 * 32; q += NT) {
-        const int i = q >> 5, j = q & 31;
-        if (i >= s || j >= s) Ws[i][j] = 0.f;
-        if (warm) Vs[i][j] = (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
+    for (int q = tid; q < NP * NP; q += NT) {
+        const int i = q / NP, j = q % NP;
+        if (i >= s || j >= s) Ws[i * LD + j] = 0.f;
+        if (warm) Vs[i * LD + j] = (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
     }
     for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
         const float wt = (float)ldexp(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv), -e2);
-        Ws[ra][cb] = wt;
-        Ws[cb][ra] = wt;
+        Ws[ra * LD + cb] = wt;
+        Ws[cb * LD + ra] = wt;
     }
     __syncthreads();
 
     // ---- shift sigma = ||W||_F and the initial columns: G = B V, V = I (cold) or stored
     float sq[1] = {0.f};
 #pragma unroll
-    for (int k = 0; k < kOSRows; ++k) sq[0] = fmaf(Ws[r0 + k][lane], Ws[r0 + k][lane], sq[0]);
+    for (int h = 0; h < CPL; ++h)
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) {
+            const float wv = Ws[(r0 + k) * LD + lane + 32 * h];
+            sq[0] = fmaf(wv, wv, sq[0]);
+        }
     block_sum_t<float, 1>(sq, red_f);
     const float sigma = sqrtf(sq[0]);
-    float g[kOSRows], v[kOSRows];
+    float g[CPL][kOSRows], v[CPL][kOSRows];
     if (warm) {
         // One Newton-Schulz step V <- V (3I - V^T V) / 2 removes the rounding drift that the
         // rotations of earlier iterations left in the stored eigenvectors (quadratic in it).
-        for (int q = tid; q < 32 * 32; q += NT) {
-            const int i = q >> 5, j = q & 31;
+        for (int q = tid; q < NP * NP; q += NT) {
+            const int i = q / NP, j = q % NP;
             if (j < i) continue;
             float acc = 0.f;
-            for (int r = 0; r < 32; ++r) acc = fmaf(Vs[r][i], Vs[r][j], acc);
-            Ss[i][j] = acc;
-            Ss[j][i] = acc;
+            for (int r = 0; r < NP; ++r) acc = fmaf(Vs[r * LD + i], Vs[r * LD + j], acc);
+            Ss[i * LD + j] = acc;
+            Ss[j * LD + i] = acc;
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) {
-            const int r = r0 + k;
-            float acc = 0.f;
-            for (int m = 0; m < 32; ++m) acc = fmaf(Vs[r][m], Ss[m][lane], acc);
-            v[k] = fmaf(-0.5f, acc, 1.5f * Vs[r][lane]);
-        }
+        for (int h = 0; h < CPL; ++h)
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) {
+                const int r = r0 + k, c = lane + 32 * h;
+                float acc = 0.f;
+                for (int m = 0; m < NP; ++m) acc = fmaf(Vs[r * LD + m], Ss[m * LD + c], acc);
+                v[h][k] = fmaf(-0.5f, acc, 1.5f * Vs[r * LD + c]);
+            }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) Vs[r0 + k][lane] = v[k];
+        for (int h = 0; h < CPL; ++h)
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) Vs[(r0 + k) * LD + lane + 32 * h] = v[h][k];
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) {
-            const int r = r0 + k;
-            float acc = sigma * v[k];
-            for (int m = 0; m < 32; ++m) acc = fmaf(Ws[r][m], Vs[m][lane], acc);
-            g[k] = acc;
-        }
+        for (int h = 0; h < CPL; ++h)
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) {
+                const int r = r0 + k, c = lane + 32 * h;
+                float acc = sigma * v[h][k];
+                for (int m = 0; m < NP; ++m) acc = fmaf(Ws[r * LD + m], Vs[m * LD + c], acc);
+                g[h][k] = acc;
+            }
     } else {
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) {
-            const int r = r0 + k;
-            v[k] = r == lane ? 1.f : 0.f;
-            g[k] = Ws[r][lane] + ((r == lane && lane < N) ? sigma : 0.f);
-        }
-    }
-    if (lane >= N) {
+        for (int h = 0; h < CPL; ++h)
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) g[k] = 0.f;
+            for (int k = 0; k < kOSRows; ++k) {
+                const int r = r0 + k, c = lane + 32 * h;
+                v[h][k] = r == c ? 1.f : 0.f;
+                g[h][k] = Ws[r * LD + c] + ((r == c && c < N) ? sigma : 0.f);
+            }
     }
+#pragma unroll
+    for (int h = 0; h < CPL; ++h)
+        if (lane + 32 * h >= N) {
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) g[h][k] = 0.f;
+        }
 
     // ---- sweeps
     int sweeps = 0;
     for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
-        float pa = 0.f;
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) pa = fmaf(g[k], g[k], pa);
-        s_red[w][lane] = pa;
+        for (int h = 0; h < CPL; ++h) {
+            float pa = 0.f;
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) pa = fmaf(g[h][k], g[h][k], pa);
+            s_red[w][lane + 32 * h] = pa;
+        }
         __syncthreads();
-        float alpha = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
+        float alpha[CPL];
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) {
+            float acc = 0.f;
+            for (int ww = 0; ww < NW; ++ww) acc += s_red[ww][lane + 32 * h];
+            alpha[h] = acc;
+        }
         float worst = 0.f;
         for (int rd = 0; rd < N - 1; ++rd) {
-            const int p = s_partner[rd][lane];
-            float gp[kOSRows];
-            float pg = 0.f;
-#pragma unroll
-            for (int k = 0; k < kOSRows; ++k) {
-                gp[k] = __shfl_sync(0xffffffffu, g[k], p);
-                pg = fmaf(g[k], gp[k], pg);
-            }
+            int p[CPL];
+            float gp[CPL][kOSRows];
             const int buf = rd & 1;
-            s_gam[buf][w][lane] = pg;
-            __syncthreads();
-            const float gam = (s_gam[buf][0][lane] + s_gam[buf][1][lane]) + (s_gam[buf][2][lane] + s_gam[buf][3][lane]);
-            const float beta = __shfl_sync(0xffffffffu, alpha, p);
-            const bool first = lane < p;
-            const float ai = first ? alpha : beta, aj = first ? beta : alpha;
-            float c = 1.f, sn = 0.f, t = 0.f;
-            if (p != lane && fabsf(gam) > 1.0e-30f) {
-                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
-                const float zeta = __fdividef(aj - ai, 2.f * gam);
-                const float az = fabsf(zeta);
-                float den;
-                if (az > 1.0e15f) {
-                    den = 2.f * az;
-                } else {
-                    const float x = fmaf(zeta, zeta, 1.f);
-                    den = az + x * rsqrtf(x);
-                }
-                t = copysignf(__fdividef(1.f, den), zeta);
-                c = __frsqrt_rn(fmaf(t, t, 1.f));
-                sn = t * c;
-            }
-            // g_i' = c g_i - s g_j (lane i),  g_j' = s g_i + c g_j (lane j)
-            const float sg = first ? -sn : sn;
 #pragma unroll
-            for (int k = 0; k < kOSRows; ++k) g[k] = fmaf(sg, gp[k], c * g[k]);
+            for (int h = 0; h < CPL; ++h) {
+                p[h] = s_partner[rd * NP + lane + 32 * h];
+                const int pl = p[h] & 31, ph = p[h] >> 5;
+                float pg = 0.f;
+#pragma unroll
+                for (int k = 0; k < kOSRows; ++k) {
+                    float val = 0.f;
+#pragma unroll
+                    for (int hs = 0; hs < CPL; ++hs) {
+                        const float t = __shfl_sync(0xffffffffu, g[hs][k], pl);
+                        if (hs == ph) val = t;
+                    }
+                    gp[h][k] = val;
+                    pg = fmaf(g[h][k], val, pg);
+                }
+                s_gam[buf][w][lane + 32 * h] = pg;
+            }
+            __syncthreads();
+            float c[CPL], sg[CPL], tt[CPL], gam[CPL];
+            bool first[CPL];
+            float ai[CPL], aj[CPL];
+#pragma unroll
+            for (int h = 0; h < CPL; ++h) {
+                float gsum = 0.f;
+                for (int ww = 0; ww < NW; ++ww) gsum += s_gam[buf][ww][lane + 32 * h];
+                gam[h] = gsum;
+                // the partner's alpha: lane p & 31 holds it in slot p >> 5
+                const int pl = p[h] & 31, ph = p[h] >> 5;
+                float beta = 0.f;
+#pragma unroll
+                for (int hs = 0; hs < CPL; ++hs) {
+                    const float t = __shfl_sync(0xffffffffu, alpha[hs], pl);
+                    if (hs == ph) beta = t;
+                }
+                const int me = lane + 32 * h;
+                first[h] = me < p[h];
+                ai[h] = first[h] ? alpha[h] : beta;
+                aj[h] = first[h] ? beta : alpha[h];
+                float cc = 1.f, sn = 0.f, t = 0.f;
+                if (p[h] != me && fabsf(gsum) > 1.0e-30f) {
+                    worst = fmaxf(worst, __fdividef(gsum * gsum, fmaxf(ai[h] * aj[h], 1.0e-30f)));
+                    const float zeta = __fdividef(aj[h] - ai[h], 2.f * gsum);
+                    const float az = fabsf(zeta);
+                    float den;
+                    if (az > 1.0e15f) {
+                        den = 2.f * az;
+                    } else {
+                        const float x = fmaf(zeta, zeta, 1.f);
+                        den = az + x * rsqrtf(x);
+                    }
+                    t = copysignf(__fdividef(1.f, den), zeta);
+                    cc = __frsqrt_rn(fmaf(t, t, 1.f));
+                    sn = t * cc;
+                }
+                c[h] = cc;
+                tt[h] = t;
+                sg[h] = first[h] ? -sn : sn;     // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j)
+            }
+#pragma unroll
+            for (int h = 0; h < CPL; ++h) {
+#pragma unroll
+                for (int k = 0; k < kOSRows; ++k) g[h][k] = fmaf(sg[h], gp[h][k], c[h] * g[h][k]);
+            }
 #pragma unroll
             for (int k = 0; k < kOSRows; ++k) {
-                const float vp = __shfl_sync(0xffffffffu, v[k], p);
-                v[k] = fmaf(sg, vp, c * v[k]);
+                float vp[CPL];
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const int pl = p[h] & 31, ph = p[h] >> 5;
+                    float val = 0.f;
+#pragma unroll
+                    for (int hs = 0; hs < CPL; ++hs) {
+                        const float t = __shfl_sync(0xffffffffu, v[hs][k], pl);
+                        if (hs == ph) val = t;
+                    }
+                    vp[h] = val;
+                }
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) v[h][k] = fmaf(sg[h], vp[h], c[h] * v[h][k]);
             }
-            alpha = first ? ai - t * gam : aj + t * gam;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                alpha[h] = first[h] ? ai[h] - tt[h] * gam[h] : aj[h] + tt[h] * gam[h];
         }
         ++sweeps;
-        float wr[1] = {worst};
-        // largest squared ratio of the sweep over the whole CTA
+        float wr = worst;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wr[0] = fmaxf(wr[0], __shfl_xor_sync(0xffffffffu, wr[0], o));
-        if (lane == 0) s_red[w][0] = wr[0];
+        for (int o = 16; o > 0; o >>= 1) wr = fmaxf(wr, __shfl_xor_sync(0xffffffffu, wr, o));
+        if (lane == 0) s_red[w][0] = wr;
         __syncthreads();
-        const float wmx = fmaxf(fmaxf(s_red[0][0], s_red[1][0]), fmaxf(s_red[2][0], s_red[3][0]));
+        float wmx = 0.f;
+        for (int ww = 0; ww < NW; ++ww) wmx = fmaxf(wmx, s_red[ww][0]);
         __syncthreads();
         if (wmx < kOneSidedStop * kOneSidedStop) break;
     }
 
     // ---- eigenvalues lambda_j = v_j . g_j - sigma, clipped; V into Ws (and HBM)
-    float pr = 0.f;
 #pragma unroll
-    for (int k = 0; k < kOSRows; ++k) pr = fmaf(v[k], g[k], pr);
-    s_red[w][lane] = pr;
+    for (int h = 0; h < CPL; ++h) {
+        float pr = 0.f;
+#pragma unroll
+        for (int k = 0; k < kOSRows; ++k) pr = fmaf(v[h][k], g[h][k], pr);
+        s_red[w][lane + 32 * h] = pr;
+    }
     __syncthreads();
-    if (w == 0) {
-        const float lam = ((s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane])) - sigma;
-        dp[lane] = (lane < N && lam > 0.f) ? lam : 0.f;
+    for (int c = tid; c < NP; c += NT) {
+        float acc = 0.f;
+        for (int ww = 0; ww < NW; ++ww) acc += s_red[ww][c];
+        const float lam = acc - sigma;
+        dp[c] = (c < N && lam > 0.f) ? lam : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < kOSRows; ++k) Ws[r0 + k][lane] = v[k];
-    if (vglob != nullptr && lane < N) {
+    for (int h = 0; h < CPL; ++h)
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k)
-            if (r0 + k < N) vglob[(r0 + k) * N + lane] = v[k];
+        for (int k = 0; k < kOSRows; ++k) Ws[(r0 + k) * LD + lane + 32 * h] = v[h][k];
+    if (vglob != nullptr) {
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) {
+            const int c = lane + 32 * h;
+            if (c >= N) continue;
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k)
+                if (r0 + k < N) vglob[(r0 + k) * N + c] = v[h][k];
+        }
     }
     __syncthreads();
 
@@ -670,7 +766,7 @@ __global__ void __launch_bounds__(32 * kOSWarps) k_project_os(ProjArgs a, double
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
         float acc = 0.f;
-        for (int i = 0; i < N; ++i) acc = fmaf(Ws[ra][i] * dp[i], Ws[cb][i], acc);
+        for (int i = 0; i < N; ++i) acc = fmaf(Ws[ra * LD + i] * dp[i], Ws[cb * LD + i], acc);
         const double xv = ldexp((double)acc, e2);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
@@ -704,9 +800,19 @@ cudaError_t prepare_one() {
     return cudaFuncSetAttribute(k_project<T, MODE, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+template <int MODE, int CPL>
+cudaError_t prepare_os() {
+    return cudaFuncSetAttribute(k_project_os<MODE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)OSLayout<CPL>::kBytes);
+}
+
 template <typename T, int MODE>
 cudaError_t prepare_mode() {
     cudaError_t e;
+    if (sizeof(T) == 4) {
+        if ((e = prepare_os<MODE, 1>()) != cudaSuccess) return e;
+        if ((e = prepare_os<MODE, 2>()) != cudaSuccess) return e;
+    }
     if ((e = prepare_one<T, MODE, ShapeS16>()) != cudaSuccess) return e;
     if ((e = prepare_one<T, MODE, ShapeS32>()) != cudaSuccess) return e;
     if ((e = prepare_one<T, MODE, ShapeS64>()) != cudaSuccess) return e;
@@ -719,7 +825,9 @@ cudaError_t launch_mode(const ProjArgs& a, int smax, cudaStream_t st) {
     const double rinv = 1.0 / a.rho;
     const int N = smax + (smax & 1);
     if (sizeof(T) == 4 && N <= 32)
-        return launch_pdl(k_project_os<MODE>, dim3(a.count), dim3(32 * kOSWarps), 0, st, a, rinv);
+        return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
+    if (sizeof(T) == 4 && N <= 64)
+        return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
     if (N <= 16) return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
     if (N <= 32) return launch_pdl(k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st, a, rinv);
     if (N <= 64) return launch_pdl(k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st, a, rinv);

@@ -26,6 +26,24 @@ inline long long find_entry(const std::vector<long long>& keys, long long k) {
     return (long long)(it - keys.begin());
 }
 
+// Runs f(i) for i in [0, n) on up to hardware_concurrency threads (contiguous slices).
+template <typename F>
+void parallel_for(int n, F f) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min(hw, n));
+    if (nt == 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            const int lo = (int)((long long)n * t / nt), hi = (int)((long long)n * (t + 1) / nt);
+            for (int i = lo; i < hi; ++i) f(i);
+        });
+    for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
@@ -169,19 +187,24 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     }
     hp.b.assign(b, b + m);
 
-    // ---- A on E_L: CSR by constraint (duplicates merged), then CSC by entry.
-    hp.a_rowptr.assign(m + 1, 0);
-    std::vector<std::pair<int, double>> row;
-    for (int i = 0; i < m; ++i) {
-        row.clear();
+    // ---- A on E_L: CSR by constraint (duplicates merged), then CSC by entry. Constraints are
+    // converted in parallel; the first failing constraint (lowest index) decides the error.
+    std::vector<std::vector<std::pair<int, double>>> rows(m);
+    std::vector<int> row_err(m, SDP_OK);
+    std::vector<std::string> row_msg(m);
+    parallel_for(m, [&](int i) {
+        std::vector<std::pair<int, double>>& row = rows[i];
+        row.reserve((size_t)(A_ptr[i + 1] - A_ptr[i]));
         for (long long t = A_ptr[i]; t < A_ptr[i + 1]; ++t) {
             const long long r = A_row[t], cc = A_col[t];
-            if (r < 0 || r >= n || cc < 0 || cc >= n) return fail(err, SDP_ERR_ARG, "A index out of range");
-            if (r < cc) return fail(err, SDP_ERR_ARG, "A must be given as lower coordinates (row >= col)");
+            if (r < 0 || r >= n || cc < 0 || cc >= n) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A index out of range"; return; }
+            if (r < cc) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A must be given as lower coordinates (row >= col)"; return; }
             const long long e = find_entry(keys, key_of(r, cc, n));
             if (e < 0) {
                 if (A_val[t] == 0.0) continue;
-                return fail(err, SDP_ERR_CLIQUE, "a nonzero of A is not covered by the cliques");
+                row_err[i] = SDP_ERR_CLIQUE;
+                row_msg[i] = "a nonzero of A is not covered by the cliques";
+                return;
             }
             row.emplace_back((int)e, A_val[t]);
         }
@@ -192,13 +215,30 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             if (w > 0 && row[w - 1].first == row[t].first) row[w - 1].second += row[t].second;
             else row[w++] = row[t];
         }
-        for (size_t t = 0; t < w; ++t) {
-            if (row[t].second == 0.0) continue;
-            hp.a_col.push_back(row[t].first);
-            hp.a_val.push_back(row[t].second);
-        }
-        if ((long long)hp.a_col.size() >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "nnz(A) >= 2^31");
-        hp.a_rowptr[i + 1] = (int)hp.a_col.size();
+        size_t k = 0;
+        for (size_t t = 0; t < w; ++t)
+            if (row[t].second != 0.0) row[k++] = row[t];
+        row.resize(k);
+    });
+    for (int i = 0; i < m; ++i)
+        if (row_err[i] != SDP_OK) return fail(err, row_err[i], row_msg[i]);
+    hp.a_rowptr.assign(m + 1, 0);
+    {
+        long long total = 0;
+        for (int i = 0; i < m; ++i) total += (long long)rows[i].size();
+        if (total >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "nnz(A) >= 2^31");
+        hp.a_col.resize(total);
+        hp.a_val.resize(total);
+        for (int i = 0; i < m; ++i) hp.a_rowptr[i + 1] = hp.a_rowptr[i] + (int)rows[i].size();
+        parallel_for(m, [&](int i) {
+            size_t q = hp.a_rowptr[i];
+            for (const auto& pr : rows[i]) {
+                hp.a_col[q] = pr.first;
+                hp.a_val[q] = pr.second;
+                ++q;
+            }
+            std::vector<std::pair<int, double>>().swap(rows[i]);
+        });
     }
     hp.nnz = (long long)hp.a_col.size();
     hp.c_colptr.assign(nEL + 1, 0);

@@ -159,8 +159,8 @@ def block_arrow_instance(l: int, d: int, h: int, m: int, density: float, seed: i
     np.add.at(rowsum, pat_col[offdiag], np.abs(Z0_val[offdiag]))
     Z0_val[~offdiag] = rowsum[pat_row[~offdiag]] + 1.0
 
-    C_val = Z0_val.copy()
-    np.add.at(C_val, A_pos.ravel(), (A_val * y0[:, None]).ravel())
+    # C = 𝒜*(y0) + Z0 on the pattern
+    C_val = Z0_val + np.bincount(A_pos.ravel(), weights=(A_val * y0[:, None]).ravel(), minlength=nl)
 
     md = dict(l=l, d=d, h=h, density=density, seed=seed)
     if meta:
