@@ -86,7 +86,28 @@ typedef struct {
     long long nE_lower;    /* |E_L| */
     long long S_lower;     /* S_L   */
     long long nnz_A;       /* stored nonzeros of A on E_L (after merging duplicates) */
+    int batch;             /* problems in the handle (1 for sdp_setup, count for sdp_setup_batch) */
 } sdp_sizes;
+
+/* One problem of a batch: the arguments of sdp_setup, with the same meaning, in a struct. */
+typedef struct {
+    int n, m;
+    const long long* A_ptr;
+    const int* A_row;
+    const int* A_col;
+    const double* A_val;
+    const double* b;
+    long long C_nnz;
+    const int* C_row;
+    const int* C_col;
+    const double* C_val;
+    long long pat_nnz;
+    const int* pat_row;
+    const int* pat_col;
+    int p;
+    const int* clique_ptr;
+    const int* clique_vtx;
+} sdp_problem;
 
 /* Residual definitions (the paper cites Boyd et al. 2011 for them without restating; this build
  * reads them as follows, with Euclidean norms over the full symmetric vectors):
@@ -115,6 +136,37 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
               long long pat_nnz, const int* pat_row, const int* pat_col,
               int p, const int* clique_ptr, const int* clique_vtx,
               const admm_opts* opts, sdp_handle* out);
+
+/* ---- batches of independent problems (not in the paper: many SDPs solved in one set of launches)
+ * sdp_setup_batch builds one handle for `count` independent problems. The handle holds their
+ * block-diagonal union: the vertices, constraints, cliques, E_L entries and packed positions of
+ * problem q follow those of problem q-1 (sdp_batch_layout gives the offsets), so every vector the
+ * handle reads or returns (sdp_get_state, sdp_set_state, sdp_get_solution, sdp_get_maps, the
+ * device buffers of sdp_gather / sdp_scatter) is the concatenation of the problems' vectors, and
+ * each problem's L^-1 is its own block. Every kernel of an iteration covers all problems at once;
+ * no CTA works on two problems. Each problem keeps its own residuals, objectives and stop test
+ * (the definitions below): a problem whose residuals fall below tol, or become NaN/Inf, is frozen
+ * (its iterates stop changing) at that iteration, which is what a separate solve of it would
+ * return. A call ends when every problem is frozen or its budget is used. For a batch,
+ * admm_result.status is SDP_ERR_NAN if a problem stopped on NaN/Inf, else SDP_OK if all converged,
+ * else SDP_MAX_ITER; eps_p / eps_d are the maxima over the problems and the objectives their sums
+ * (the objectives of the union). admm_reset, sdp_set_state and sdp_set_opts unfreeze every problem.
+ * Errors as sdp_setup (the message names the failing problem); count >= 1. A handle from
+ * sdp_setup behaves as a batch of one, except that it is never frozen (a later admm_iterate
+ * continues from the converged state). */
+int sdp_setup_batch(int count, const sdp_problem* problems, const admm_opts* opts, sdp_handle* out);
+
+/* Offsets of each problem inside the handle's vectors, [batch + 1] host arrays each (any may be
+ * NULL): vertices, constraints, cliques, E_L entries and packed positions. */
+int sdp_batch_layout(sdp_handle h, int* vtx_off, int* row_off, int* clique_off, long long* ent_off,
+                     long long* pos_off);
+
+/* Per-problem outcome of the iterations so far, [batch] host arrays each (any may be NULL): the
+ * iteration count (the iteration at which the problem was frozen, else all iterations run), its
+ * status (SDP_OK converged, SDP_MAX_ITER, SDP_ERR_NAN), residuals and objectives of its last
+ * iteration. */
+int sdp_batch_results(sdp_handle h, int* iters, int* status, double* eps_p, double* eps_d,
+                      double* obj_primal, double* obj_dual);
 
 /* Replace the options (rho, tol, form, precision may all change; the KKT factor does not depend
  * on them). Takes effect at the next admm_iterate / admm_solve. Does not reset the iterates. */
@@ -174,12 +226,14 @@ int project_psd_batched(const double* in, double* out, const int* sizes, const l
                         int count, int prec, void* cuda_stream);
 
 /* Profiling: run `reps` iterations kernel by kernel (no graph) on cuda_stream with CUDA events
- * between the kernels, and write the average device milliseconds of each kernel of one iteration
- * to ms_out[0 .. count-1] in launch order (count = 7 primal, 8 dual; returns count, or < 0 on
- * error; max_out is the capacity of ms_out). The iterations really run and advance the state, with
- * the stop test disabled. sdp_phase_name(form, i) names kernel i. */
+ * between the phases, and write the average device milliseconds of each phase of one iteration
+ * to ms_out[0 .. count-1] in launch order (count = 6 primal, 7 dual, one more for the per-problem
+ * stop test of a batch; the projection phase covers all of its launches). Returns count, or < 0
+ * on error; max_out is the capacity of ms_out. The iterations really run and advance the state,
+ * with the stop test disabled. sdp_phase_name(h, i) names phase i for the handle's current form
+ * (NULL when out of range). */
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
-const char* sdp_phase_name(int form, int i);
+const char* sdp_phase_name(sdp_handle h, int i);
 
 /* Batched PSD projection that allocates nothing (no counterpart in the paper: it exists for
  * callers, not for the method). Same arguments, kernels and results as project_psd_batched, for

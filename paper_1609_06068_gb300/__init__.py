@@ -38,7 +38,7 @@ PRECS = {"fp64": SDP_PROJ_FP64, "fp32": SDP_PROJ_FP32}
 
 # Symbols the header declares (checked by the CPU test suite against the built library).
 EXPORTS = [
-    "sdp_setup", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
+    "sdp_setup", "sdp_setup_batch", "sdp_batch_layout", "sdp_batch_results", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "sdp_free", "sdp_status_string", "sdp_last_error",
@@ -68,7 +68,16 @@ class admm_result(ctypes.Structure):
 class sdp_sizes(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
                 ("max_clique", ctypes.c_int), ("nE_lower", ctypes.c_longlong),
-                ("S_lower", ctypes.c_longlong), ("nnz_A", ctypes.c_longlong)]
+                ("S_lower", ctypes.c_longlong), ("nnz_A", ctypes.c_longlong), ("batch", ctypes.c_int)]
+
+
+class sdp_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("A_ptr", ctypes.c_void_p),
+                ("A_row", ctypes.c_void_p), ("A_col", ctypes.c_void_p), ("A_val", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("C_nnz", ctypes.c_longlong), ("C_row", ctypes.c_void_p),
+                ("C_col", ctypes.c_void_p), ("C_val", ctypes.c_void_p), ("pat_nnz", ctypes.c_longlong),
+                ("pat_row", ctypes.c_void_p), ("pat_col", ctypes.c_void_p), ("p", ctypes.c_int),
+                ("clique_ptr", ctypes.c_void_p), ("clique_vtx", ctypes.c_void_p)]
 
 
 _lib = None
@@ -89,6 +98,9 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "sdp_setup": (_I, [_I, _I, _P, _P, _P, _P, _P, _LL, _P, _P, _P, _LL, _P, _P, _I, _P, _P,
                            ctypes.POINTER(admm_opts), ctypes.POINTER(_P)]),
+        "sdp_setup_batch": (_I, [_I, ctypes.POINTER(sdp_problem), ctypes.POINTER(admm_opts), ctypes.POINTER(_P)]),
+        "sdp_batch_layout": (_I, [_P, _P, _P, _P, _P, _P]),
+        "sdp_batch_results": (_I, [_P, _P, _P, _P, _P, _P, _P]),
         "sdp_set_opts": (_I, [_P, ctypes.POINTER(admm_opts)]),
         "admm_reset": (_I, [_P, _P]),
         "admm_iterate": (_I, [_P, _I, _P, ctypes.POINTER(admm_result)]),
@@ -102,7 +114,7 @@ def load_library(path: str = LIB_PATH):
         "sdp_scatter": (_I, [_P, _P, _P, _P]),
         "project_psd_batched": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "sdp_time_phases": (_I, [_P, _I, _P, _P, _I]),
-        "sdp_phase_name": (ctypes.c_char_p, [_I, _I]),
+        "sdp_phase_name": (ctypes.c_char_p, [_P, _I]),
         "project_psd_batched_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "sdp_free": (None, [_P]),
         "sdp_status_string": (ctypes.c_char_p, [_I]),
@@ -170,36 +182,90 @@ def _result(r: admm_result) -> dict:
 
 # ------------------------------------------------------------------------------- entry points
 
-def sdp_setup(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliques=None,
-              clique_ptr=None, clique_vtx=None, pat_row=None, pat_col=None, opts=None):
-    """Set up the decomposed problem on the current CUDA device; returns the opaque handle."""
-    lib = load_library()
+def _problem_arrays(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliques=None,
+                    clique_ptr=None, clique_vtx=None, pat_row=None, pat_col=None):
+    """The host arrays of one problem, converted to the ABI's types (kept alive by the caller)."""
     if cliques is not None:
         sizes = np.array([len(c) for c in cliques], dtype=np.int64)
         clique_ptr = np.concatenate([[0], np.cumsum(sizes)])
         clique_vtx = np.concatenate([np.asarray(c) for c in cliques]) if len(cliques) else np.zeros(0)
-    A_ptr = _arr(A_ptr, np.int64)
-    A_row, A_col, A_val = _arr(A_row, np.int32), _arr(A_col, np.int32), _arr(A_val, np.float64)
-    b = _arr(b, np.float64)
-    C_row, C_col, C_val = _arr(C_row, np.int32), _arr(C_col, np.int32), _arr(C_val, np.float64)
-    clique_ptr, clique_vtx = _arr(clique_ptr, np.int32), _arr(clique_vtx, np.int32)
-    pr = _arr(pat_row, np.int32) if pat_row is not None else None
-    pc = _arr(pat_col, np.int32) if pat_col is not None else None
+    d = dict(n=int(n), A_ptr=_arr(A_ptr, np.int64), A_row=_arr(A_row, np.int32), A_col=_arr(A_col, np.int32),
+             A_val=_arr(A_val, np.float64), b=_arr(b, np.float64), C_row=_arr(C_row, np.int32),
+             C_col=_arr(C_col, np.int32), C_val=_arr(C_val, np.float64),
+             clique_ptr=_arr(clique_ptr, np.int32), clique_vtx=_arr(clique_vtx, np.int32),
+             pat_row=_arr(pat_row, np.int32) if pat_row is not None else None,
+             pat_col=_arr(pat_col, np.int32) if pat_col is not None else None)
+    return d
+
+
+def _problem_struct(d: dict) -> sdp_problem:
+    pr = d["pat_row"]
+    return sdp_problem(d["n"], len(d["b"]), _ptr(d["A_ptr"]), _ptr(d["A_row"]), _ptr(d["A_col"]),
+                       _ptr(d["A_val"]), _ptr(d["b"]), len(d["C_val"]), _ptr(d["C_row"]), _ptr(d["C_col"]),
+                       _ptr(d["C_val"]), 0 if pr is None else len(pr), _ptr(pr), _ptr(d["pat_col"]),
+                       len(d["clique_ptr"]) - 1, _ptr(d["clique_ptr"]), _ptr(d["clique_vtx"]))
+
+
+def sdp_setup(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliques=None,
+              clique_ptr=None, clique_vtx=None, pat_row=None, pat_col=None, opts=None):
+    """Set up the decomposed problem on the current CUDA device; returns the opaque handle."""
+    lib = load_library()
+    d = _problem_arrays(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliques, clique_ptr,
+                        clique_vtx, pat_row, pat_col)
+    pr = d["pat_row"]
     opts = opts if opts is not None else make_opts()
     h = ctypes.c_void_p()
-    rc = lib.sdp_setup(int(n), len(b), _ptr(A_ptr), _ptr(A_row), _ptr(A_col), _ptr(A_val), _ptr(b),
-                       len(C_val), _ptr(C_row), _ptr(C_col), _ptr(C_val),
-                       0 if pr is None else len(pr), _ptr(pr), _ptr(pc),
-                       len(clique_ptr) - 1, _ptr(clique_ptr), _ptr(clique_vtx),
+    rc = lib.sdp_setup(d["n"], len(d["b"]), _ptr(d["A_ptr"]), _ptr(d["A_row"]), _ptr(d["A_col"]),
+                       _ptr(d["A_val"]), _ptr(d["b"]), len(d["C_val"]), _ptr(d["C_row"]), _ptr(d["C_col"]),
+                       _ptr(d["C_val"]), 0 if pr is None else len(pr), _ptr(pr), _ptr(d["pat_col"]),
+                       len(d["clique_ptr"]) - 1, _ptr(d["clique_ptr"]), _ptr(d["clique_vtx"]),
                        ctypes.byref(opts), ctypes.byref(h))
     _check(rc, "sdp_setup")
-    _FORM_OF[h.value] = opts.form
     return h
+
+
+def sdp_setup_batch(problems, opts=None):
+    """One handle for a list of independent problems (dicts with the keyword arguments of
+    ``sdp_setup``: n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val and cliques or
+    clique_ptr/clique_vtx)."""
+    lib = load_library()
+    keep = [_problem_arrays(**{k: v for k, v in pr.items() if k in _PROBLEM_KEYS}) for pr in problems]
+    arr = (sdp_problem * len(keep))(*[_problem_struct(d) for d in keep])
+    opts = opts if opts is not None else make_opts()
+    h = ctypes.c_void_p()
+    _check(lib.sdp_setup_batch(len(keep), arr, ctypes.byref(opts), ctypes.byref(h)), "sdp_setup_batch")
+    return h
+
+
+_PROBLEM_KEYS = ("n", "A_ptr", "A_row", "A_col", "A_val", "b", "C_row", "C_col", "C_val", "cliques",
+                 "clique_ptr", "clique_vtx", "pat_row", "pat_col")
+
+
+def sdp_batch_layout(h) -> dict:
+    """Offsets of each problem in the handle's vectors (arrays of batch + 1 entries)."""
+    q = sdp_get_sizes(h)["batch"]
+    out = dict(vtx_off=np.zeros(q + 1, np.int32), row_off=np.zeros(q + 1, np.int32),
+               clique_off=np.zeros(q + 1, np.int32), ent_off=np.zeros(q + 1, np.int64),
+               pos_off=np.zeros(q + 1, np.int64))
+    _check(load_library().sdp_batch_layout(h, *[_ptr(out[k]) for k in
+                                                ("vtx_off", "row_off", "clique_off", "ent_off", "pos_off")]),
+           "sdp_batch_layout")
+    return out
+
+
+def sdp_batch_results(h) -> dict:
+    """Per-problem iterations, status, residuals and objectives (arrays of batch entries)."""
+    q = sdp_get_sizes(h)["batch"]
+    out = dict(iters=np.zeros(q, np.int32), status=np.zeros(q, np.int32), eps_p=np.zeros(q),
+               eps_d=np.zeros(q), obj_primal=np.zeros(q), obj_dual=np.zeros(q))
+    _check(load_library().sdp_batch_results(h, *[_ptr(out[k]) for k in
+                                                 ("iters", "status", "eps_p", "eps_d", "obj_primal", "obj_dual")]),
+           "sdp_batch_results")
+    return out
 
 
 def sdp_set_opts(h, opts: admm_opts):
     _check(load_library().sdp_set_opts(h, ctypes.byref(opts)), "sdp_set_opts")
-    _FORM_OF[getattr(h, "value", h)] = opts.form
 
 
 def admm_reset(h, stream=None):
@@ -304,20 +370,13 @@ def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:
     n = lib.sdp_time_phases(h, int(reps), _stream(stream), _ptr(ms), len(ms))
     if n < 0:
         _check(n, "sdp_time_phases")
-    form = _form_of(h)
-    return {lib.sdp_phase_name(form, i).decode(): float(ms[i]) for i in range(n)}
+    return {lib.sdp_phase_name(h, i).decode(): float(ms[i]) for i in range(n)}
 
 
-def sdp_phase_name(form: int, i: int) -> str | None:
-    r = load_library().sdp_phase_name(int(form), int(i))
+def sdp_phase_name(h, i: int) -> str | None:
+    """Name of phase i of an iteration for the handle's current form."""
+    r = load_library().sdp_phase_name(h, int(i))
     return None if r is None else r.decode()
-
-
-_FORM_OF = {}
-
-
-def _form_of(h) -> int:
-    return _FORM_OF.get(getattr(h, "value", h), SDP_PRIMAL)
 
 
 def sdp_free(h):
@@ -336,12 +395,23 @@ def sdp_last_error() -> str:
 class ChordalADMM:
     """Owns one handle: ``with ChordalADMM(inst_arrays, opts) as s: s.solve()``."""
 
-    def __init__(self, arrays: dict, opts: admm_opts | None = None):
+    def __init__(self, arrays, opts: admm_opts | None = None):
+        """``arrays``: one problem (a dict of sdp_setup's keyword arguments) or a list of them (a
+        batch, set up with sdp_setup_batch)."""
         self.opts = opts if opts is not None else make_opts()
-        self.h = sdp_setup(arrays["n"], arrays["A_ptr"], arrays["A_row"], arrays["A_col"],
-                           arrays["A_val"], arrays["b"], arrays["C_row"], arrays["C_col"],
-                           arrays["C_val"], cliques=arrays["cliques"], opts=self.opts)
+        if isinstance(arrays, dict):
+            self.h = sdp_setup(arrays["n"], arrays["A_ptr"], arrays["A_row"], arrays["A_col"],
+                               arrays["A_val"], arrays["b"], arrays["C_row"], arrays["C_col"],
+                               arrays["C_val"], cliques=arrays["cliques"], opts=self.opts)
+        else:
+            self.h = sdp_setup_batch(list(arrays), self.opts)
         self.sizes = sdp_get_sizes(self.h)
+
+    def batch_layout(self):
+        return sdp_batch_layout(self.h)
+
+    def batch_results(self):
+        return sdp_batch_results(self.h)
 
     def set_opts(self, **kw):
         d = {f: getattr(self.opts, f) for f, _ in admm_opts._fields_}

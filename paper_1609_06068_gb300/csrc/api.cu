@@ -72,10 +72,12 @@ int record_error(int code, const std::string& msg) { return set_err(code, msg); 
 struct sdp_ctx {
     int device = 0;
     admm_opts opts{};
-    int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0;
+    int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0, ninst = 1;
     long long nnz = 0;
     // host copies needed after setup
     std::vector<int> pat_row, pat_col, blk_off, gather_idx;
+    std::vector<int> inst_vtx, inst_row, inst_cl, inst_e, inst_pos;
+    cadmm::ProjPlan plan[2]{};    // projection launches per precision (SDP_PROJ_FP64, SDP_PROJ_FP32)
     std::vector<void*> allocs;
     IterPtrs P{};
     cudaStream_t cap_stream = nullptr;
@@ -129,7 +131,8 @@ int capture_graph(sdp_ctx* h, int iters, cudaGraphExec_t* out) {
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < iters && le == cudaSuccess; ++i)
-        le = cadmm::launch_iteration(h->P, h->opts.form, h->opts.prec, h->opts.rho, h->cap_stream);
+        le = cadmm::launch_iteration(h->P, h->plan[h->opts.prec], h->opts.form, h->opts.prec, h->opts.rho,
+                                     h->cap_stream);
     const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -175,6 +178,12 @@ int rebuild_r_if_primal(sdp_ctx* h, cudaStream_t st) {
     return SDP_OK;
 }
 
+// Every problem of a batch iterates again (after a reset, a state upload or new options).
+int unfreeze(sdp_ctx* h, cudaStream_t st) {
+    CK(cadmm::launch_inst_reset(h->P, st));
+    return SDP_OK;
+}
+
 int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
     const double t0 = now_s();
     int rc = ensure_graphs(h);
@@ -216,13 +225,198 @@ int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
         out->obj_primal = c.obj_p;
         out->obj_dual = c.obj_d;
         out->seconds = now_s() - t0;
-        out->kernel_launches = 1 + launched_iters * cadmm::iteration_kernel_count(h->opts.form);
+        out->kernel_launches =
+            1 + launched_iters * cadmm::iteration_kernel_count(h->P, h->plan[h->opts.prec], h->opts.form);
     }
     if (c.status == SDP_ERR_NAN) set_err(SDP_ERR_NAN, "a residual or objective became NaN/Inf");
     return c.status;
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// CTA schedules. No CTA spans two problems; within a problem the ranges follow the element order,
+// so a single problem gets the same split as an unscheduled grid would.
+struct Schedules {
+    std::vector<cadmm::Sched> row, tri, col, pos, ent, heavy;
+    std::vector<int> row_cta, inst_col_cta, inst_pos_cta, inst_ent_cta, inst_heavy_cta;
+};
+
+Schedules build_schedules(const HostProblem& hp, int num_sms) {
+    Schedules S;
+    const int Q = hp.ninst;
+    // CSR chunks: about two waves of CTAs over all of A, at least 2048 nonzeros each, <= 64 per row.
+    const long long target = std::max<long long>(2048, (hp.nnz + 2LL * num_sms - 1) / (2LL * num_sms));
+    S.row_cta.assign(hp.m + 1, 0);
+    for (int q = 0; q < Q; ++q)
+        for (int i = hp.inst_row[q]; i < hp.inst_row[q + 1]; ++i) {
+            const int lo0 = hp.a_rowptr[i], hi0 = hp.a_rowptr[i + 1];
+            const long long len = hi0 - lo0;
+            const int R = (int)std::max<long long>(1, std::min<long long>(64, (len + target - 1) / target));
+            for (int ch = 0; ch < R; ++ch)
+                S.row.push_back({q, lo0 + (int)(len * ch / R), lo0 + (int)(len * (ch + 1) / R), i});
+            S.row_cta[i + 1] = (int)S.row.size();
+        }
+    // L^-1 / L^-T products: 8 rows (one per warp) per CTA.
+    for (int q = 0; q < Q; ++q)
+        for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1]; r += 8)
+            S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
+    // CSC: about four CTAs per SM over all of A; each CTA a whole number of 32-column rounds.
+    S.inst_col_cta.assign(Q + 1, 0);
+    const long long col_target = std::max<long long>(1, (hp.nnz + 4LL * num_sms - 1) / (4LL * num_sms));
+    for (int q = 0; q < Q; ++q) {
+        const int e0 = hp.inst_e[q], e1 = hp.inst_e[q + 1];
+        const long long nq = e1 - e0;
+        const long long nnzq = (long long)hp.c_colptr[e1] - hp.c_colptr[e0];
+        long long k = std::max<long long>(1, (nnzq + col_target / 2) / col_target);
+        k = std::min<long long>(k, std::max<long long>(1, (nq + 31) / 32));
+        long long chunk = (nq + k - 1) / k;
+        chunk = std::max<long long>(32, (chunk + 31) / 32 * 32);
+        for (long long lo = e0; lo < e1; lo += chunk)
+            S.col.push_back({q, (int)lo, (int)std::min<long long>(lo + chunk, e1), 0});
+        S.inst_col_cta[q + 1] = (int)S.col.size();
+    }
+    // Packed positions and light entries: 256 per CTA; heavy entries: 8 (one per warp) per CTA.
+    S.inst_pos_cta.assign(Q + 1, 0);
+    S.inst_ent_cta.assign(Q + 1, 0);
+    S.inst_heavy_cta.assign(Q + 1, 0);
+    size_t h = 0;
+    for (int q = 0; q < Q; ++q) {
+        for (int lo = hp.inst_pos[q]; lo < hp.inst_pos[q + 1]; lo += 256)
+            S.pos.push_back({q, lo, std::min(lo + 256, hp.inst_pos[q + 1]), 0});
+        S.inst_pos_cta[q + 1] = (int)S.pos.size();
+        for (int lo = hp.inst_e[q]; lo < hp.inst_e[q + 1]; lo += 256)
+            S.ent.push_back({q, lo, std::min(lo + 256, hp.inst_e[q + 1]), 0});
+        S.inst_ent_cta[q + 1] = (int)S.ent.size();
+        const size_t h0 = h;
+        while (h < hp.heavy.size() && hp.heavy[h] < hp.inst_e[q + 1]) ++h;
+        for (size_t lo = h0; lo < h; lo += 8)
+            S.heavy.push_back({q, (int)lo, (int)std::min(lo + 8, h), 0});
+        S.inst_heavy_cta[q + 1] = (int)S.heavy.size();
+    }
+    return S;
+}
+
+int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
+    sdp_ctx* h = new sdp_ctx();
+    std::unique_ptr<sdp_ctx> guard(h);
+    CK(cudaGetDevice(&h->device));
+    h->opts = *opts;
+    h->n = hp.n; h->m = hp.m; h->p = hp.p; h->smax = hp.smax;
+    h->nEL = hp.nEL; h->SL = hp.SL; h->nnz = hp.nnz; h->ninst = hp.ninst;
+    h->pat_row = hp.pat_row; h->pat_col = hp.pat_col;
+    h->blk_off = hp.blk_off; h->gather_idx = hp.gather_idx;
+    h->inst_vtx = hp.inst_vtx; h->inst_row = hp.inst_row; h->inst_cl = hp.inst_cl;
+    h->inst_e = hp.inst_e; h->inst_pos = hp.inst_pos;
+    h->plan[SDP_PROJ_FP64] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP64, nullptr);
+    h->plan[SDP_PROJ_FP32] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP32, nullptr);
+    CK(cadmm::project_prepare());
+    CK(cadmm::iteration_prepare());
+
+    int num_sms = 0;
+    CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    const Schedules S = build_schedules(hp, num_sms);
+    IterPtrs& P = h->P;
+    P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
+    P.ninst = hp.ninst;
+    P.mmax = 0;
+    for (int q = 0; q < hp.ninst; ++q) P.mmax = std::max(P.mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
+    P.row_ctas = (int)S.row.size();
+    P.tri_ctas = (int)S.tri.size();
+    P.col_ctas = (int)S.col.size();
+    P.pos_ctas = (int)S.pos.size();
+    P.ent_ctas = (int)S.ent.size();
+    P.heavy_ctas = (int)S.heavy.size();
+    P.n_heavy = (int)hp.heavy.size();
+    std::vector<int> blk_inst(hp.p);
+    for (int q = 0; q < hp.ninst; ++q)
+        for (int k = hp.inst_cl[q]; k < hp.inst_cl[q + 1]; ++k) blk_inst[k] = q;
+
+    int rc;
+    std::vector<long long> off64(hp.blk_off.begin(), hp.blk_off.end());
+#define UP(field, vec)                                             \
+    do {                                                           \
+        auto* tmp_ = const_cast<std::remove_const_t<std::remove_pointer_t<decltype(P.field)>>*>(P.field); \
+        rc = h->upload(&tmp_, vec);                                \
+        if (rc) return rc;                                         \
+        P.field = tmp_;                                            \
+    } while (0)
+    UP(inst_cl, hp.inst_cl);
+    UP(inst_row, hp.inst_row);
+    UP(mblk_off, hp.mblk_off);
+    UP(blk_inst, blk_inst);
+    UP(row_sched, S.row);
+    UP(row_cta, S.row_cta);
+    UP(tri_sched, S.tri);
+    UP(col_sched, S.col);
+    UP(pos_sched, S.pos);
+    UP(ent_sched, S.ent);
+    UP(heavy_sched, S.heavy);
+    UP(inst_col_cta, S.inst_col_cta);
+    UP(inst_pos_cta, S.inst_pos_cta);
+    UP(inst_ent_cta, S.inst_ent_cta);
+    UP(inst_heavy_cta, S.inst_heavy_cta);
+    UP(blk_off, hp.blk_off);
+    UP(blk_off64, off64);
+    UP(blk_size, hp.blk_size);
+    UP(voff, hp.voff);
+    UP(order, hp.order);
+    UP(gather_idx, hp.gather_idx);
+    UP(pos_w, hp.pos_w);
+    UP(sc_ptr, hp.sc_ptr);
+    UP(sc_pos, hp.sc_pos);
+    UP(heavy, hp.heavy);
+    UP(D, hp.D);
+    UP(dinv, hp.dinv);
+    UP(wdinv, hp.wdinv);
+    UP(c, hp.c);
+    UP(b, hp.b);
+    UP(ew, hp.ew);
+    UP(a_rowptr, hp.a_rowptr);
+    UP(a_col, hp.a_col);
+    UP(a_val, hp.a_val);
+    UP(c_colptr, hp.c_colptr);
+    UP(c_row, hp.c_row);
+    UP(c_val, hp.c_val);
+    UP(Linv, hp.Linv);
+    UP(LinvT, hp.LinvT);
+#undef UP
+    if ((rc = h->dalloc(&P.inst_res, (size_t)hp.ninst * 4))) return rc;
+    if ((rc = h->dalloc(&P.inst_conv, (size_t)hp.ninst))) return rc;
+    if ((rc = h->dalloc(&P.inst_stat, (size_t)hp.ninst))) return rc;
+    if ((rc = h->dalloc(&P.x, hp.nEL))) return rc;
+    if ((rc = h->dalloc(&P.y, hp.m))) return rc;
+    if ((rc = h->dalloc(&P.r, hp.nEL))) return rc;
+    if ((rc = h->dalloc(&P.rsw, hp.nEL))) return rc;
+    if ((rc = h->dalloc(&P.z1, hp.m))) return rc;
+    if ((rc = h->dalloc(&P.xk[0], hp.SL))) return rc;
+    if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
+    if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
+    if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
+    if ((rc = h->dalloc(&P.tpart, (size_t)P.row_ctas))) return rc;
+    if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
+    if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas + P.heavy_ctas, P.pos_ctas) * 8))) return rc;
+    if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_ctas))) return rc;
+    if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
+    {
+        double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
+        if ((rc = h->dalloc(&vs, (size_t)hp.voff[hp.p]))) return rc;
+        P.vstore = vs;
+    }
+    CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+    guard.release();
+    *out = h;
+    rc = admm_reset(h, nullptr);
+    if (rc) {
+        delete h;
+        *out = nullptr;
+        return rc;
+    }
+    CK(cudaDeviceSynchronize());
+    return SDP_OK;
+}
 
 }  // namespace
 
@@ -243,106 +437,68 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         rc = cadmm::build_host_problem(n, m, A_ptr, A_row, A_col, A_val, b, C_nnz, C_row, C_col, C_val,
                                        pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, hp, err);
         if (rc) return set_err(rc, err);
-
-        sdp_ctx* h = new sdp_ctx();
-        std::unique_ptr<sdp_ctx> guard(h);
-        CK(cudaGetDevice(&h->device));
-        h->opts = *opts;
-        h->n = hp.n; h->m = hp.m; h->p = hp.p; h->smax = hp.smax;
-        h->nEL = hp.nEL; h->SL = hp.SL; h->nnz = hp.nnz;
-        h->pat_row = hp.pat_row; h->pat_col = hp.pat_col;
-        h->blk_off = hp.blk_off; h->gather_idx = hp.gather_idx;
-        CK(cadmm::project_prepare());
-        CK(cadmm::iteration_prepare());
-
-        int num_sms = 0;
-        CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
-        IterPtrs& P = h->P;
-        P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
-        // CTAs per CSR row: enough row chunks for ~2 waves, each chunk >= 2048 nonzeros.
-        {
-            const long long avg = std::max<long long>(1, hp.nnz / hp.m);
-            long long R = (2LL * num_sms + hp.m - 1) / hp.m;
-            R = std::min<long long>(R, std::max<long long>(1, avg / 2048));
-            P.R = (int)std::max<long long>(1, std::min<long long>(R, 64));
-        }
-        P.ent_ctas = (hp.nEL + 255) / 256;
-        P.n_heavy = (int)hp.heavy.size();
-        P.heavy_ctas = (P.n_heavy + 7) / 8;
-        P.pos_ctas = (hp.SL + 255) / 256;
-        P.col_ctas = std::max(1, std::min(num_sms * kColCtasPerSm, (hp.nEL + 31) / 32));
-
-        std::vector<long long> off64(hp.blk_off.begin(), hp.blk_off.end());
-#define UP(field, vec)                                             \
-    do {                                                           \
-        auto* tmp_ = const_cast<std::remove_const_t<std::remove_pointer_t<decltype(P.field)>>*>(P.field); \
-        rc = h->upload(&tmp_, vec);                                \
-        if (rc) return rc;                                         \
-        P.field = tmp_;                                            \
-    } while (0)
-        UP(blk_off, hp.blk_off);
-        UP(blk_off64, off64);
-        UP(blk_size, hp.blk_size);
-        UP(voff, hp.voff);
-        UP(order, hp.order);
-        UP(gather_idx, hp.gather_idx);
-        UP(pos_w, hp.pos_w);
-        UP(sc_ptr, hp.sc_ptr);
-        UP(sc_pos, hp.sc_pos);
-        UP(heavy, hp.heavy);
-        UP(D, hp.D);
-        UP(dinv, hp.dinv);
-        UP(wdinv, hp.wdinv);
-        UP(c, hp.c);
-        UP(b, hp.b);
-        UP(ew, hp.ew);
-        UP(a_rowptr, hp.a_rowptr);
-        UP(a_col, hp.a_col);
-        UP(a_val, hp.a_val);
-        UP(c_colptr, hp.c_colptr);
-        UP(c_row, hp.c_row);
-        UP(c_val, hp.c_val);
-        UP(Linv, hp.Linv);
-        UP(LinvT, hp.LinvT);
-#undef UP
-        if ((rc = h->dalloc(&P.x, hp.nEL))) return rc;
-        if ((rc = h->dalloc(&P.y, hp.m))) return rc;
-        if ((rc = h->dalloc(&P.r, hp.nEL))) return rc;
-        if ((rc = h->dalloc(&P.rsw, hp.nEL))) return rc;
-        if ((rc = h->dalloc(&P.z1, hp.m))) return rc;
-        if ((rc = h->dalloc(&P.xk[0], hp.SL))) return rc;
-        if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
-        if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
-        if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
-        if ((rc = h->dalloc(&P.tpart, (size_t)hp.m * P.R))) return rc;
-        if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
-        if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas + P.heavy_ctas, P.pos_ctas) * 8))) return rc;
-        if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_ctas))) return rc;
-        if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
-        {
-            double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
-            if ((rc = h->dalloc(&vs, (size_t)hp.voff[hp.p]))) return rc;
-            P.vstore = vs;
-        }
-        CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
-        CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
-        guard.release();
-        *out = h;
-        rc = admm_reset(h, nullptr);
-        if (rc) {
-            delete h;
-            *out = nullptr;
-            return rc;
-        }
-        CK(cudaDeviceSynchronize());
-        return SDP_OK;
+        return create_handle(hp, opts, out);
     } catch (const std::bad_alloc&) {
         return set_err(SDP_ERR_ARG, "host out of memory");
     } catch (...) {
         return set_err(SDP_ERR_ARG, "unexpected exception in sdp_setup");
     }
+}
+
+int sdp_setup_batch(int count, const sdp_problem* problems, const admm_opts* opts, sdp_handle* out) {
+    try {
+        if (!out) return set_err(SDP_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (count < 1 || !problems) return set_err(SDP_ERR_ARG, "count must be >= 1 and problems non-NULL");
+        int rc = check_opts(opts);
+        if (rc) return rc;
+        HostProblem hp;
+        std::string err;
+        rc = cadmm::build_host_problem_batch(count, problems, hp, err);
+        if (rc) return set_err(rc, err);
+        return create_handle(hp, opts, out);
+    } catch (const std::bad_alloc&) {
+        return set_err(SDP_ERR_ARG, "host out of memory");
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_setup_batch");
+    }
+}
+
+int sdp_batch_layout(sdp_handle h, int* vtx_off, int* row_off, int* clique_off, long long* ent_off,
+                     long long* pos_off) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    for (int q = 0; q <= h->ninst; ++q) {
+        if (vtx_off) vtx_off[q] = h->inst_vtx[q];
+        if (row_off) row_off[q] = h->inst_row[q];
+        if (clique_off) clique_off[q] = h->inst_cl[q];
+        if (ent_off) ent_off[q] = h->inst_e[q];
+        if (pos_off) pos_off[q] = h->inst_pos[q];
+    }
+    return SDP_OK;
+}
+
+int sdp_batch_results(sdp_handle h, int* iters, int* status, double* eps_p, double* eps_d,
+                      double* obj_primal, double* obj_dual) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    const int q = h->ninst;
+    Ctrl c{};
+    std::vector<int> conv(q), stat(q);
+    std::vector<double> res((size_t)q * 4);
+    CK(cudaMemcpy(&c, h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(conv.data(), h->P.inst_conv, sizeof(int) * q, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(stat.data(), h->P.inst_stat, sizeof(int) * q, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(res.data(), h->P.inst_res, sizeof(double) * 4 * q, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < q; ++k) {
+        if (iters) iters[k] = (h->ninst > 1 && conv[k] >= 0) ? conv[k] : c.iter;
+        if (status) status[k] = stat[k];
+        if (eps_p) eps_p[k] = res[k * 4 + 0];
+        if (eps_d) eps_d[k] = res[k * 4 + 1];
+        if (obj_primal) obj_primal[k] = res[k * 4 + 2];
+        if (obj_dual) obj_dual[k] = res[k * 4 + 3];
+    }
+    return SDP_OK;
 }
 
 int sdp_set_opts(sdp_handle h, const admm_opts* opts) {
@@ -358,7 +514,8 @@ int sdp_set_opts(sdp_handle h, const admm_opts* opts) {
         rc = rebuild_r_if_primal(h, nullptr);
         if (rc) return rc;
     }
-    if (rebuild || new_prec) CK(cudaDeviceSynchronize());
+    if ((rc = unfreeze(h, nullptr))) return rc;
+    CK(cudaDeviceSynchronize());
     return SDP_OK;
 }
 
@@ -377,6 +534,8 @@ int admm_reset(sdp_handle h, void* cuda_stream) {
     CK(cudaMemsetAsync(P.vk, 0, sizeof(double) * std::max(1, P.SL), st));
     CK(cadmm::launch_ctrl_reset(P.ctrl, st));
     CK(cadmm::launch_vstore_identity(P, h->opts.prec, st));
+    int rc = unfreeze(h, st);
+    if (rc) return rc;
     return rebuild_r_if_primal(h, st);
 }
 
@@ -400,6 +559,7 @@ int sdp_get_sizes(sdp_handle h, sdp_sizes* out) {
     if (!h || !out) return set_err(SDP_ERR_ARG, "NULL argument");
     out->n = h->n; out->m = h->m; out->p = h->p; out->max_clique = h->smax;
     out->nE_lower = h->nEL; out->S_lower = h->SL; out->nnz_A = h->nnz;
+    out->batch = h->ninst;
     return SDP_OK;
 }
 
@@ -436,7 +596,9 @@ int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* 
     if (blk_b) CK(cudaMemcpy(P.lam, blk_b, sl, cudaMemcpyHostToDevice));
     if (blk_c) CK(cudaMemcpy(P.vk, blk_c, sl, cudaMemcpyHostToDevice));
     CK(cadmm::launch_vstore_identity(P, h->opts.prec, nullptr));
-    int rc = rebuild_r_if_primal(h, nullptr);
+    int rc = unfreeze(h, nullptr);
+    if (rc) return rc;
+    rc = rebuild_r_if_primal(h, nullptr);
     if (rc) return rc;
     CK(cudaDeviceSynchronize());
     return SDP_OK;
@@ -531,12 +693,19 @@ int project_psd_batched(const double* in, double* out, const int* sizes, const l
         a.size = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) + (size_t)count * sizeof(long long));
         a.order = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) +
                                                (size_t)count * (sizeof(long long) + sizeof(int)));
-        a.count = count;
         a.rho = 1.0;
         a.in = in;
         a.out = out;
         a.ctrl = nullptr;
-        e = cadmm::launch_project(a, cadmm::PROJ_PLAIN, prec, smax, st);
+        // One launch per run of blocks that share a kernel variant, largest blocks first.
+        const std::vector<int> sz(sizes, sizes + count);
+        const cadmm::ProjPlan plan = cadmm::make_proj_plan(order, sz, prec, nullptr);
+        const int* d_order = a.order;
+        for (int r = 0; r < plan.runs && e == cudaSuccess; ++r) {
+            a.order = d_order + plan.start[r];
+            a.count = plan.count[r];
+            e = cadmm::launch_project_variant(a, cadmm::PROJ_PLAIN, prec, plan.variant[r], plan.smax[r], st);
+        }
     }
     // The pageable host copy above returns once the data is staged, so `host` may go away.
     const cudaError_t fe = cudaFreeAsync(d, st);
@@ -547,7 +716,7 @@ int project_psd_batched(const double* in, double* out, const int* sizes, const l
 
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out) {
     if (!h || reps < 1 || !ms_out) return set_err(SDP_ERR_ARG, "bad argument");
-    const int count = cadmm::iteration_kernel_count(h->opts.form);
+    const int count = cadmm::phase_count(h->P, h->opts.form);
     if (max_out < count) return set_err(SDP_ERR_ARG, "ms_out too small");
     CK(cudaSetDevice(h->device));
     cudaStream_t st = as_stream(cuda_stream);
@@ -556,7 +725,8 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
     std::vector<double> acc(count, 0.0);
     cudaError_t ce = cadmm::launch_ctrl_arm(h->P.ctrl, reps, 0.0, st);
     for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
-        ce = cadmm::launch_iteration(h->P, h->opts.form, h->opts.prec, h->opts.rho, st, ev.data());
+        ce = cadmm::launch_iteration(h->P, h->plan[h->opts.prec], h->opts.form, h->opts.prec, h->opts.rho, st,
+                                     ev.data());
         if (ce == cudaSuccess) ce = cudaEventSynchronize(ev[count]);
         for (int i = 0; i < count && ce == cudaSuccess; ++i) {
             float ms = 0.f;
@@ -570,7 +740,10 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
     return count;
 }
 
-const char* sdp_phase_name(int form, int i) { return cadmm::phase_name(form, i); }
+const char* sdp_phase_name(sdp_handle h, int i) {
+    if (!h) return nullptr;
+    return cadmm::phase_name(h->opts.form, h->ninst > 1, i);
+}
 
 void sdp_free(sdp_handle h) { delete h; }
 

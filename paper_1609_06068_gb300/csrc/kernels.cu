@@ -6,9 +6,11 @@
 //   spmv_cols    x = (r - A^T y) / D       (second pass over A; CSC)
 //   update_dual  v_k = z_k + rho^-1 lambda_k + H_k x, lambda_k = -rho H_k x (Eqs. vkEqn,
 //                DualMultUpdate with the sign Eq. MultUpdateDualSDP implies)
-// The residuals, objectives and stop test of an iteration are computed by the last CTA to finish
-// the iteration's final kernel (scatter in the primal form, update in the dual form), reading
-// every partial sum in a fixed order. Kernels are launched with programmatic dependent launch.
+// For a single problem the residuals, objectives and stop test of an iteration are computed by the
+// last CTA to finish the iteration's final kernel (scatter in the primal form, update in the dual
+// form), reading every partial sum in a fixed order. For a batch, each CTA works on one problem
+// (its Sched entry) and a separate kernel finalizes every problem, one warp each; CTAs of a problem
+// that has stopped return at once.
 // Every kernel starts by reading the device control block and returns at once when the solve is
 // done, so a captured graph holding several iterations can run past convergence at no cost.
 // All reductions use a fixed tree, so results are bitwise reproducible run to run.
@@ -96,17 +98,138 @@ __device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int 
     C->obj_p = obj_p;
     C->obj_d = obj_d;
     C->ticket = 0;
+    int st = SDP_MAX_ITER;
     if (!isfinite(eps_p) || !isfinite(eps_d) || !isfinite(obj_p) || !isfinite(obj_d)) {
-        C->status = SDP_ERR_NAN;
+        st = C->status = SDP_ERR_NAN;
         C->done = 1;
     } else if (fmax(eps_p, eps_d) < C->tol) {
-        C->status = SDP_OK;
+        st = C->status = SDP_OK;
         C->done = 1;
     } else if (it >= C->iter_limit) {
         C->status = SDP_MAX_ITER;
         C->done = 1;
     }
+    P.inst_res[0] = eps_p;
+    P.inst_res[1] = eps_d;
+    P.inst_res[2] = obj_p;
+    P.inst_res[3] = obj_d;
+    P.inst_stat[0] = st;
 }
+
+// Residuals and stop test of every problem of a batch: one warp per problem sums its partials in
+// a fixed order; the last CTA then sets the iteration's global outcome.
+__global__ void __launch_bounds__(256) k_finalize_batch(IterPtrs P, int form, double rho) {
+    __shared__ double red[33 * 4];
+    __shared__ int red_i[33 * 2];
+    __shared__ bool s_last;
+    Ctrl* C = P.ctrl;
+    if (C->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int it = C->iter + 1;
+    if (q < P.ninst && P.inst_conv[q] < 0) {
+        double v[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (form == SDP_PRIMAL) {
+            for (int k = P.inst_cl[q] + lane; k < P.inst_cl[q + 1]; k += 32) {
+                v[0] += P.part_blk[k * 4 + 0];
+                v[1] += P.part_blk[k * 4 + 1];
+                v[2] += P.part_blk[k * 4 + 2];
+            }
+            for (int c = P.inst_ent_cta[q] + lane; c < P.inst_ent_cta[q + 1]; c += 32) {
+                v[3] += P.part_ent[c * 8 + 0];
+                v[4] += P.part_ent[c * 8 + 1];
+            }
+            for (int c = P.inst_heavy_cta[q] + lane; c < P.inst_heavy_cta[q + 1]; c += 32) {
+                v[3] += P.part_ent[(P.ent_ctas + c) * 8 + 0];
+                v[4] += P.part_ent[(P.ent_ctas + c) * 8 + 1];
+            }
+        } else {
+            for (int c = P.inst_pos_cta[q] + lane; c < P.inst_pos_cta[q + 1]; c += 32)
+                for (int k = 0; k < 5; ++k) v[k] += P.part_ent[c * 8 + k];
+        }
+        for (int c = P.inst_col_cta[q] + lane; c < P.inst_col_cta[q + 1]; c += 32) v[5] += P.part_obj[c];
+        for (int i = P.inst_row[q] + lane; i < P.inst_row[q + 1]; i += 32) v[6] = fma(P.b[i], P.y[i], v[6]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
+        if (lane == 0) {
+            const double eps_p = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-12);
+            const double eps_d = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-12);
+            const double obj_p = form == SDP_PRIMAL ? v[5] : -rho * v[5];
+            const double obj_d = form == SDP_PRIMAL ? -rho * v[6] : v[6];
+            P.inst_res[q * 4 + 0] = eps_p;
+            P.inst_res[q * 4 + 1] = eps_d;
+            P.inst_res[q * 4 + 2] = obj_p;
+            P.inst_res[q * 4 + 3] = obj_d;
+            if (!isfinite(eps_p) || !isfinite(eps_d) || !isfinite(obj_p) || !isfinite(obj_d)) {
+                P.inst_stat[q] = SDP_ERR_NAN;
+                P.inst_conv[q] = it;
+            } else if (fmax(eps_p, eps_d) < C->tol) {
+                P.inst_stat[q] = SDP_OK;
+                P.inst_conv[q] = it;
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // Global outcome: residual maxima and objective sums over all problems (their last values).
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    int active = 0, nan = 0;
+    for (int k = threadIdx.x; k < P.ninst; k += blockDim.x) {
+        v[0] = fmax(v[0], P.inst_res[k * 4 + 0]);
+        v[1] = fmax(v[1], P.inst_res[k * 4 + 1]);
+        v[2] += P.inst_res[k * 4 + 2];
+        v[3] += P.inst_res[k * 4 + 3];
+        active += P.inst_conv[k] < 0;
+        nan += P.inst_stat[k] == SDP_ERR_NAN;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+        active += __shfl_xor_sync(0xffffffffu, active, o);
+        nan += __shfl_xor_sync(0xffffffffu, nan, o);
+    }
+    const int nw = blockDim.x >> 5;
+    if (lane == 0) {
+        for (int k = 0; k < 4; ++k) red[warp * 4 + k] = v[k];
+        red_i[warp * 2 + 0] = active;
+        red_i[warp * 2 + 1] = nan;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
+    int ga = 0, gn = 0;
+    for (int w = 0; w < nw; ++w) {
+        g[0] = fmax(g[0], red[w * 4 + 0]);
+        g[1] = fmax(g[1], red[w * 4 + 1]);
+        g[2] += red[w * 4 + 2];
+        g[3] += red[w * 4 + 3];
+        ga += red_i[w * 2 + 0];
+        gn += red_i[w * 2 + 1];
+    }
+    C->iter = it;
+    C->eps_p = g[0];
+    C->eps_d = g[1];
+    C->obj_p = g[2];
+    C->obj_d = g[3];
+    C->ticket = 0;
+    if (ga == 0) {
+        C->status = gn > 0 ? SDP_ERR_NAN : SDP_OK;
+        C->done = 1;
+    } else if (it >= C->iter_limit) {
+        C->status = gn > 0 ? SDP_ERR_NAN : SDP_MAX_ITER;
+        C->done = 1;
+    }
+}
+
+// True when CTA work for problem q must be skipped: it belongs to a batch and has stopped.
+__device__ __forceinline__ bool stopped(const IterPtrs& P, int q) { return P.ninst > 1 && P.inst_conv[q] >= 0; }
 
 // After a CTA has written its partial sums: count it, and let the last one finalize.
 __device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int form, double rho, int n_part) {
@@ -138,9 +261,12 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
     const double* xn_buf = use_current ? cur : nxt;
     const double* xo_buf = cur;
     double v[2] = {0.0, 0.0};
-    if ((int)blockIdx.x < P.ent_ctas) {
-        const int e = blockIdx.x * blockDim.x + threadIdx.x;
-        if (e < P.nEL) {
+    const bool light = (int)blockIdx.x < P.ent_ctas;
+    const Sched sc = light ? P.ent_sched[blockIdx.x] : P.heavy_sched[blockIdx.x - P.ent_ctas];
+    if (!use_current && stopped(P, sc.q)) return;
+    if (light) {
+        const int e = sc.lo + threadIdx.x;
+        if (e < sc.hi) {
             const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
             if (j1 - j0 <= kHeavyCount) {
                 double acc = 0.0, dsum = 0.0, lsum = 0.0;
@@ -162,8 +288,8 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
         }
     } else {
         const int lane = threadIdx.x & 31;
-        const int hw = ((int)blockIdx.x - P.ent_ctas) * (kEntThreads / 32) + (threadIdx.x >> 5);
-        if (hw < P.n_heavy) {
+        const int hw = sc.lo + (threadIdx.x >> 5);
+        if (hw < sc.hi) {
             const int e = P.heavy[hw];
             const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
             double acc = 0.0, dsum = 0.0, lsum = 0.0;
@@ -203,7 +329,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
         P.part_ent[blockIdx.x * 8 + 0] = v[0];
         P.part_ent[blockIdx.x * 8 + 1] = v[1];
     }
-    finish_and_maybe_finalize(P, SDP_PRIMAL, rho, P.ent_ctas + P.heavy_ctas);
+    if (P.ninst == 1) finish_and_maybe_finalize(P, SDP_PRIMAL, rho, P.ent_ctas + P.heavy_ctas);
 }
 
 // ---------------------------------------------------------------- scatter (dual form)
@@ -213,9 +339,12 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
     pdl_wait();
     if (P.ctrl->done) return;
     const double* z = P.xk[0];
-    if ((int)blockIdx.x < P.ent_ctas) {
-        const int e = blockIdx.x * blockDim.x + threadIdx.x;
-        if (e >= P.nEL) return;
+    const bool light = (int)blockIdx.x < P.ent_ctas;
+    const Sched sc = light ? P.ent_sched[blockIdx.x] : P.heavy_sched[blockIdx.x - P.ent_ctas];
+    if (stopped(P, sc.q)) return;
+    if (light) {
+        const int e = sc.lo + threadIdx.x;
+        if (e >= sc.hi) return;
         const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
         if (j1 - j0 > kHeavyCount) return;
         double acc = 0.0;
@@ -230,8 +359,8 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int hw = ((int)blockIdx.x - P.ent_ctas) * (kEntThreads / 32) + (threadIdx.x >> 5);
-    if (hw >= P.n_heavy) return;
+    const int hw = sc.lo + (threadIdx.x >> 5);
+    if (hw >= sc.hi) return;
     const int e = P.heavy[hw];
     const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
     double acc = 0.0;
@@ -261,10 +390,9 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     __shared__ double red[33];
     pdl_wait();
     if (P.ctrl->done) return;
-    const int i = blockIdx.x / P.R, ch = blockIdx.x - (blockIdx.x / P.R) * P.R;
-    const int lo0 = P.a_rowptr[i], hi0 = P.a_rowptr[i + 1];
-    const long long len = hi0 - lo0;
-    const int lo = lo0 + (int)(len * ch / P.R), hi = lo0 + (int)(len * (ch + 1) / P.R);
+    const Sched sc = P.row_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
+    const int lo = sc.lo, hi = sc.hi;
     const int bd = blockDim.x;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int j = lo + threadIdx.x;
@@ -287,17 +415,22 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
     extern __shared__ double u[];
     pdl_wait();
     if (P.ctrl->done) return;
-    const int m = P.m, R = P.R;
+    const Sched sc = P.tri_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double t = 0.0;
-        for (int c = 0; c < R; ++c) t += P.tpart[i * R + c];
-        const double rhs2 = form == SDP_PRIMAL ? P.b[i] : -__dmul_rn(rinv, P.b[i]);
+        for (int c = P.row_cta[r0 + i]; c < P.row_cta[r0 + i + 1]; ++c) t += P.tpart[c];
+        const double bi = P.b[r0 + i];
+        const double rhs2 = form == SDP_PRIMAL ? bi : -__dmul_rn(rinv, bi);
         u[i] = t - rhs2;
     }
     __syncthreads();
+    const double* Lb = P.Linv + P.mblk_off[sc.q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int row = blockIdx.x * nw + warp; row < m; row += gridDim.x * nw) {
-        const double* Lr = P.Linv + (size_t)row * m;
+    for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
+        const int row = grow - r0;
+        const double* Lr = Lb + (size_t)row * m;
         double a0 = 0.0, a1 = 0.0;
         int j = lane;
         for (; j + 32 <= row; j += 64) {
@@ -306,7 +439,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
         }
         if (j <= row) a0 = fma(Lr[j], u[j], a0);
         const double acc = warp_sum(a0 + a1);
-        if (lane == 0) P.z1[row] = acc;
+        if (lane == 0) P.z1[grow] = acc;
     }
 }
 
@@ -315,12 +448,16 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
     extern __shared__ double zs[];
     pdl_wait();
     if (P.ctrl->done) return;
-    const int m = P.m;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = P.z1[i];
+    const Sched sc = P.tri_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = P.z1[r0 + i];
     __syncthreads();
+    const double* Lb = P.LinvT + P.mblk_off[sc.q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int row = blockIdx.x * nw + warp; row < m; row += gridDim.x * nw) {
-        const double* Lr = P.LinvT + (size_t)row * m;
+    for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
+        const int row = grow - r0;
+        const double* Lr = Lb + (size_t)row * m;
         double a0 = 0.0, a1 = 0.0;
         int i = row + lane;
         for (; i + 32 < m; i += 64) {
@@ -329,7 +466,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
         }
         if (i < m) a0 = fma(Lr[i], zs[i], a0);
         const double acc = warp_sum(a0 + a1);
-        if (lane == 0) P.y[row] = acc;
+        if (lane == 0) P.y[grow] = acc;
     }
 }
 
@@ -341,14 +478,17 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
     __shared__ double red[33];
     pdl_wait();
     if (P.ctrl->done) return;
-    for (int i = threadIdx.x; i < P.m; i += blockDim.x) ys[i] = P.y[i];
+    const Sched sc = P.col_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = P.y[r0 + i];
     __syncthreads();
     const int gid = threadIdx.x / kColGroup, gl = threadIdx.x % kColGroup;
     const int ngroups = blockDim.x / kColGroup;
     double obj = 0.0;
-    for (int e0 = blockIdx.x * ngroups; e0 < P.nEL; e0 += gridDim.x * ngroups) {
+    for (int e0 = sc.lo; e0 < sc.hi; e0 += ngroups) {
         const int e = e0 + gid;
-        const bool valid = e < P.nEL;
+        const bool valid = e < sc.hi;
         double s0 = 0.0, s1 = 0.0;
         if (valid) {
             const int lo = P.c_colptr[e], hi = P.c_colptr[e + 1];
@@ -381,8 +521,10 @@ __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double 
     __shared__ double red[33 * 5];
     pdl_wait();
     if (P.ctrl->done) return;
+    const Sched sc = P.pos_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < P.SL; pos += gridDim.x * blockDim.x) {
+    for (int pos = sc.lo + threadIdx.x; pos < sc.hi; pos += blockDim.x) {
         const double u = P.x[P.gather_idx[pos]];
         const double z = P.xk[0][pos], l = P.lam[pos], vo = P.vk[pos];
         const double vn = __dadd_rn(__dadd_rn(z, __dmul_rn(rinv, l)), u);
@@ -403,7 +545,7 @@ __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double 
 #pragma unroll
         for (int k = 0; k < 5; ++k) P.part_ent[blockIdx.x * 8 + k] = v[k];
     }
-    finish_and_maybe_finalize(P, SDP_DUAL, rho, (int)gridDim.x);
+    if (P.ninst == 1) finish_and_maybe_finalize(P, SDP_DUAL, rho, (int)gridDim.x);
 }
 
 __global__ void k_ctrl_arm(Ctrl* C, int n_iters, double tol) {
@@ -470,7 +612,30 @@ ProjArgs proj_args_for(const IterPtrs& P, double rho) {
     a.vstore = P.vstore;
     a.voff = P.voff;
     a.ctrl = P.ctrl;
+    a.blk_inst = P.ninst > 1 ? P.blk_inst : nullptr;
+    a.inst_conv = P.ninst > 1 ? P.inst_conv : nullptr;
     return a;
+}
+
+// All runs of the projection plan, largest cliques first.
+cudaError_t launch_project_plan(const ProjArgs& a, const IterPtrs& P, const ProjPlan& plan, int mode, int prec,
+                                cudaStream_t st) {
+    for (int r = 0; r < plan.runs; ++r) {
+        ProjArgs b = a;
+        b.order = P.order + plan.start[r];
+        b.count = plan.count[r];
+        const cudaError_t e = launch_project_variant(b, mode, prec, plan.variant[r], plan.smax[r], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+__global__ void k_inst_reset(IterPtrs P) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P.ninst) return;
+    P.inst_conv[q] = -1;
+    P.inst_stat[q] = SDP_MAX_ITER;
+    for (int k = 0; k < 4; ++k) P.inst_res[q * 4 + k] = 0.0;
 }
 
 // Optional per-kernel timing: when ev != nullptr, ev[i] is recorded before kernel i of the
@@ -488,15 +653,14 @@ struct Marks {
 cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, cudaStream_t st, Marks& mk) {
     cudaError_t e;
     mk.mark();
-    if ((e = launch_pdl(k_spmv_rows, dim3(P.m * P.R), dim3(kRowThreads), 0, st, P)) != cudaSuccess) return e;
-    const int tri_ctas = cdiv(P.m, kTriThreads / 32);
-    const size_t msm = (size_t)P.m * sizeof(double);
+    if ((e = launch_pdl(k_spmv_rows, dim3(P.row_ctas), dim3(kRowThreads), 0, st, P)) != cudaSuccess) return e;
+    const size_t mbytes = (size_t)P.mmax * sizeof(double);   // the largest problem's y, staged
     mk.mark();
-    if ((e = launch_pdl(k_tri_lower, dim3(tri_ctas), dim3(kTriThreads), msm, st, P, rinv, form)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) return e;
     mk.mark();
-    if ((e = launch_pdl(k_tri_upper, dim3(tri_ctas), dim3(kTriThreads), msm, st, P)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
     mk.mark();
-    if ((e = launch_pdl(k_spmv_cols, dim3(P.col_ctas), dim3(kColThreads), msm, st, P)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_spmv_cols, dim3(P.col_ctas), dim3(kColThreads), mbytes, st, P)) != cudaSuccess) return e;
     if (form == SDP_DUAL) {
         mk.mark();
         return launch_pdl(k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);
@@ -506,7 +670,11 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
 
 }  // namespace
 
-int iteration_kernel_count(int form) { return form == SDP_PRIMAL ? 6 : 7; }
+int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form) {
+    return (form == SDP_PRIMAL ? 5 : 6) + plan.runs + (P.ninst > 1 ? 1 : 0);
+}
+
+int phase_count(const IterPtrs& P, int form) { return (form == SDP_PRIMAL ? 6 : 7) + (P.ninst > 1 ? 1 : 0); }
 
 cudaError_t iteration_prepare() {
     // y / z / t staged in shared memory: up to SDP_MAX_CONSTRAINTS doubles.
@@ -517,8 +685,8 @@ cudaError_t iteration_prepare() {
     return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, cudaStream_t st,
-                             cudaEvent_t* ev) {
+cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,
+                             cudaStream_t st, cudaEvent_t* ev) {
     const double rinv = 1.0 / rho;
     ProjArgs a = proj_args_for(P, rho);
     Marks mk{ev, st, 0};
@@ -526,7 +694,7 @@ cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, 
     if (form == SDP_PRIMAL) {
         if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
         mk.mark();
-        if ((e = launch_project(a, PROJ_PRIMAL, prec, P.smax, st)) != cudaSuccess) return e;
+        if ((e = launch_project_plan(a, P, plan, PROJ_PRIMAL, prec, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
                             rho, 0)) != cudaSuccess)
@@ -534,24 +702,40 @@ cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, 
     } else {
         a.out = P.xk[0];
         mk.mark();
-        if ((e = launch_project(a, PROJ_DUAL, prec, P.smax, st)) != cudaSuccess) return e;
+        if ((e = launch_project_plan(a, P, plan, PROJ_DUAL, prec, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
                             rinv)) != cudaSuccess)
             return e;
         if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
     }
+    if (P.ninst > 1) {
+        mk.mark();
+        const int ctas = (P.ninst + 7) / 8;
+        if ((e = launch_pdl(k_finalize_batch, dim3(ctas), dim3(256), 0, st, P, form, rho)) != cudaSuccess) return e;
+    }
     mk.mark();
     return cudaGetLastError();
 }
 
-const char* phase_name(int form, int i) {
+const char* phase_name(int form, bool batch, int i) {
     static const char* primal[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols",
-                                   "project_primal", "scatter_primal+finalize"};
+                                   "project_primal", "scatter_primal+finalize", "finalize_batch"};
     static const char* dual[] = {"project_dual", "scatter_dual", "spmv_rows", "tri_lower",
-                                 "tri_upper", "spmv_cols", "update_dual+finalize"};
-    if (form == SDP_PRIMAL) return (i >= 0 && i < 6) ? primal[i] : nullptr;
-    return (i >= 0 && i < 7) ? dual[i] : nullptr;
+                                 "tri_upper", "spmv_cols", "update_dual+finalize", "finalize_batch"};
+    static const char* primal_b[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols",
+                                     "project_primal", "scatter_primal", "finalize_batch"};
+    static const char* dual_b[] = {"project_dual", "scatter_dual", "spmv_rows", "tri_lower",
+                                   "tri_upper", "spmv_cols", "update_dual", "finalize_batch"};
+    const int n = (form == SDP_PRIMAL ? 6 : 7) + (batch ? 1 : 0);
+    if (i < 0 || i >= n) return nullptr;
+    if (form == SDP_PRIMAL) return batch ? primal_b[i] : primal[i];
+    return batch ? dual_b[i] : dual[i];
+}
+
+cudaError_t launch_inst_reset(const IterPtrs& P, cudaStream_t st) {
+    k_inst_reset<<<(P.ninst + 255) / 256, 256, 0, st>>>(P);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_primal_rebuild_r(const IterPtrs& P, double rho, cudaStream_t st) {

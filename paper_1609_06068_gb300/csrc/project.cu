@@ -22,6 +22,8 @@
 // W is formed in FP64 and scaled by the power of two 2^-e that brings max|W_ij| into [1, 2), then
 // rounded to the projection precision T; the rebuilt lower triangle is widened and unscaled (both
 // scalings are exact).
+#include <algorithm>
+
 #include "sdp_internal.h"
 
 namespace cadmm {
@@ -189,6 +191,24 @@ __device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int p
     return __dsub_rn(a.v[off + pos], __dmul_rn(rinv, a.lam[off + pos]));
 }
 
+// Batches: true when clique blk belongs to a problem that has stopped, so the CTA must return.
+// In the primal form the iteration right after the stop copies the block's current x_k to the
+// other ping-pong buffer first, so both hold it for every later parity.
+template <int MODE>
+__device__ __forceinline__ bool block_stopped(const ProjArgs& a, int blk, int s, long long off) {
+    if (a.inst_conv == nullptr) return false;
+    const int cv = a.inst_conv[a.blk_inst[blk]];
+    if (cv < 0) return false;
+    if (MODE == PROJ_PRIMAL && cv == a.ctrl->iter) {
+        const int it = a.ctrl->iter;
+        const double* cur = (it & 1) ? a.xk[1] : a.xk[0];
+        double* nxt = (it & 1) ? a.xk[0] : a.xk[1];
+        const int len = s * (s + 1) / 2;
+        for (int q = threadIdx.x; q < len; q += blockDim.x) nxt[off + q] = cur[off + q];
+    }
+    return true;
+}
+
 template <typename T, int MODE, class SH>
 __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     constexpr int KA = SH::KA, KV = SH::KV;
@@ -203,6 +223,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
     const int s = a.size[blk];
     const long long off = a.off[blk];
+    if (block_stopped<MODE>(a, blk, s, off)) return;
     const int N = s + (s & 1);
     const int H = N / 2;
     const int LD = N + 1;
@@ -510,6 +531,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
     const int s = a.size[blk];
     const long long off = a.off[blk];
+    if (block_stopped<MODE>(a, blk, s, off)) return;
     const int N = s + (s & 1);
     const int r0 = w * kOSRows;
     // Warm start whenever eigenvectors are kept (they are the identity right after a reset); the
@@ -820,18 +842,23 @@ cudaError_t prepare_mode() {
 }
 
 template <typename T, int MODE>
-cudaError_t launch_mode(const ProjArgs& a, int smax, cudaStream_t st) {
+cudaError_t launch_mode(const ProjArgs& a, int variant, int smax, cudaStream_t st) {
     const size_t smem = project_smem_bytes(smax, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
     const double rinv = 1.0 / a.rho;
-    const int N = smax + (smax & 1);
-    if (sizeof(T) == 4 && N <= 32)
-        return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
-    if (sizeof(T) == 4 && N <= 64)
-        return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
-    if (N <= 16) return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
-    if (N <= 32) return launch_pdl(k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st, a, rinv);
-    if (N <= 64) return launch_pdl(k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st, a, rinv);
-    return launch_pdl(k_project<T, MODE, ShapeS96>, dim3(a.count), dim3(ShapeS96::NT), smem, st, a, rinv);
+    switch (variant) {
+        case PV_OS1:
+            return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
+        case PV_OS2:
+            return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
+        case PV_TS16:
+            return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
+        case PV_TS32:
+            return launch_pdl(k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st, a, rinv);
+        case PV_TS64:
+            return launch_pdl(k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st, a, rinv);
+        default:
+            return launch_pdl(k_project<T, MODE, ShapeS96>, dim3(a.count), dim3(ShapeS96::NT), smem, st, a, rinv);
+    }
 }
 
 }  // namespace
@@ -866,16 +893,76 @@ cudaError_t project_prepare() {
     return prepare_mode<double, PROJ_DUAL>();
 }
 
-cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cudaStream_t st) {
-    if (a.count <= 0) return cudaSuccess;
-    if (prec == SDP_PROJ_FP32) {
-        if (mode == PROJ_PLAIN) return launch_mode<float, PROJ_PLAIN>(a, smax, st);
-        if (mode == PROJ_PRIMAL) return launch_mode<float, PROJ_PRIMAL>(a, smax, st);
-        return launch_mode<float, PROJ_DUAL>(a, smax, st);
+int project_default_variant(int s, int prec) {
+    const int N = s + (s & 1);
+    if (prec == SDP_PROJ_FP32 && N <= 32) return PV_OS1;
+    if (prec == SDP_PROJ_FP32 && N <= 64) return PV_OS2;
+    if (N <= 16) return PV_TS16;
+    if (N <= 32) return PV_TS32;
+    if (N <= 64) return PV_TS64;
+    return PV_TS96;
+}
+
+bool project_variant_valid(int variant, int s, int prec) {
+    const int N = s + (s & 1);
+    switch (variant) {
+        case PV_OS1: return prec == SDP_PROJ_FP32 && N <= 32;
+        case PV_OS2: return prec == SDP_PROJ_FP32 && N <= 64;
+        case PV_TS16: return N <= 16;
+        case PV_TS32: return N <= 32;
+        case PV_TS64: return N <= 64;
+        case PV_TS96: return N <= 96;
+        default: return false;
     }
-    if (mode == PROJ_PLAIN) return launch_mode<double, PROJ_PLAIN>(a, smax, st);
-    if (mode == PROJ_PRIMAL) return launch_mode<double, PROJ_PRIMAL>(a, smax, st);
-    return launch_mode<double, PROJ_DUAL>(a, smax, st);
+}
+
+ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec, const int* table) {
+    ProjPlan pl{};
+    pl.runs = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+        const int s = size[order[i]];
+        const int N = s + (s & 1);
+        int v = project_default_variant(s, prec);
+        if (table != nullptr && project_variant_valid(table[N], s, prec)) v = table[N];
+        if (pl.runs > 0 && pl.variant[pl.runs - 1] == v) {
+            ++pl.count[pl.runs - 1];
+            pl.smax[pl.runs - 1] = std::max(pl.smax[pl.runs - 1], s);
+            continue;
+        }
+        if (pl.runs == kMaxProjRuns) {
+            // Out of runs (only with an unusual table): the last run takes the rest with a variant
+            // that fits its largest block.
+            const int r = pl.runs - 1;
+            ++pl.count[r];
+            pl.smax[r] = std::max(pl.smax[r], s);
+            if (!project_variant_valid(pl.variant[r], pl.smax[r], prec))
+                pl.variant[r] = project_default_variant(pl.smax[r], prec);
+            continue;
+        }
+        pl.start[pl.runs] = (int)i;
+        pl.count[pl.runs] = 1;
+        pl.variant[pl.runs] = v;
+        pl.smax[pl.runs] = s;
+        ++pl.runs;
+    }
+    return pl;
+}
+
+cudaError_t launch_project_variant(const ProjArgs& a, int mode, int prec, int variant, int smax, cudaStream_t st) {
+    if (a.count <= 0) return cudaSuccess;
+    if (!project_variant_valid(variant, smax, prec)) return cudaErrorInvalidValue;
+    if (prec == SDP_PROJ_FP32) {
+        if (mode == PROJ_PLAIN) return launch_mode<float, PROJ_PLAIN>(a, variant, smax, st);
+        if (mode == PROJ_PRIMAL) return launch_mode<float, PROJ_PRIMAL>(a, variant, smax, st);
+        return launch_mode<float, PROJ_DUAL>(a, variant, smax, st);
+    }
+    if (mode == PROJ_PLAIN) return launch_mode<double, PROJ_PLAIN>(a, variant, smax, st);
+    if (mode == PROJ_PRIMAL) return launch_mode<double, PROJ_PRIMAL>(a, variant, smax, st);
+    return launch_mode<double, PROJ_DUAL>(a, variant, smax, st);
+}
+
+cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cudaStream_t st) {
+    return launch_project_variant(a, mode, prec, project_default_variant(smax, prec), smax, st);
 }
 
 }  // namespace cadmm

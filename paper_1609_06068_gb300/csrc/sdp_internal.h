@@ -45,8 +45,17 @@ struct HostProblem {
     std::vector<int> c_colptr;                  // CSC of A (columns = E_L entries)
     std::vector<unsigned short> c_row;
     std::vector<double> c_val;
-    std::vector<double> Linv, LinvT;            // m x m row-major
+    std::vector<double> Linv, LinvT;            // per instance an m_q x m_q row-major block
+    // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
+    int ninst = 1;
+    std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row;   // vertices, cliques, E_L
+                                                                      // entries, positions, rows
+    std::vector<long long> mblk_off;                        // offsets of the L^-1 blocks
 };
+
+// Builds one HostProblem for a batch of independent problems (a block-diagonal problem). On
+// failure fills err (prefixed with the failing instance) and returns the SDP_* status.
+int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& hp, std::string& err);
 
 // Builds HostProblem from the ABI inputs. Returns an SDP_* status and fills err on failure.
 int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
@@ -78,34 +87,72 @@ struct ProjArgs {
     void* vstore;           // per-clique eigenvectors kept for warm starts (NULL: always cold)
     const long long* voff;  // [*] element offset of each clique's N x N block in vstore
     const Ctrl* ctrl;       // NULL for the standalone entry
+    // Batches: a clique whose problem has stopped (inst_conv >= 0) is skipped. In the primal form
+    // its current blocks are first copied to the other ping-pong buffer, once, so that both hold
+    // them whatever the parity of later iterations. NULL for a single problem.
+    const int* blk_inst;
+    const int* inst_conv;
 };
 
 // Entries covered by more cliques than this are scattered by a whole warp (in ascending clique
 // order, so the sum is the same as the sequential one).
 constexpr int kHeavyCount = 16;
 
+// One CTA's share of a launch: problem q of the batch, element range [lo, hi). aux is the
+// constraint (row) of a CSR chunk and unused elsewhere. No CTA spans two problems, so every
+// partial sum belongs to one problem.
+struct Sched {
+    int q, lo, hi, aux;
+};
+
+// Projection launches: the cliques in processing order (largest first) split into runs that use
+// the same kernel variant. A run [start, start + count) of `order` goes to one launch.
+enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_COUNT };
+constexpr int kMaxProjRuns = 64;
+struct ProjPlan {
+    int runs;
+    int start[kMaxProjRuns], count[kMaxProjRuns], variant[kMaxProjRuns], smax[kMaxProjRuns];
+};
+
 struct IterPtrs {
-    // problem
-    int n, m, p, nEL, SL, smax, R;      // R = CTAs per CSR row
+    // problem (a batch is the block-diagonal union of its problems)
+    int n, m, p, nEL, SL, smax;
+    int ninst;                      // problems in the batch (1 after sdp_setup)
+    int mmax;                       // largest number of constraints of one problem
+    const int* inst_cl;             // [ninst+1] first clique of each problem
+    const int* inst_row;            // [ninst+1] first constraint of each problem
+    const long long* mblk_off;      // [ninst+1] offset of each problem's block of L^-1 and L^-T
+    const int* blk_inst;            // [p] problem of each clique
+    // CTA schedules
+    const Sched* row_sched; int row_ctas; const int* row_cta;   // CSR chunks; row_cta[m+1]
+    const Sched* tri_sched; int tri_ctas;                        // <= 8 rows of L^-1 per CTA
+    const Sched* col_sched; int col_ctas;                        // CSC entry ranges
+    const Sched* pos_sched; int pos_ctas;                        // packed positions
+    const Sched* ent_sched; int ent_ctas;                        // light entries, one per thread
+    const Sched* heavy_sched; int heavy_ctas;                    // heavy-list ranges, one per warp
+    // per problem: its first CTA in each schedule that produces residual partials ([ninst+1])
+    const int* inst_col_cta; const int* inst_pos_cta; const int* inst_ent_cta; const int* inst_heavy_cta;
+    double* inst_res;     // [ninst * 4]: eps_p, eps_d, obj_p, obj_d of its last iteration
+    int* inst_conv;       // [ninst]: iteration at which it stopped (converged or NaN), or -1
+    int* inst_stat;       // [ninst]: SDP_OK, SDP_MAX_ITER or SDP_ERR_NAN
     const int* blk_off; const long long* blk_off64; const int* blk_size; const int* order;
     const int* gather_idx; const unsigned char* pos_w;
     const int* sc_ptr; const int* sc_pos;
-    const int* heavy; int n_heavy, heavy_ctas;     // warp-per-entry scatter of heavily shared entries
+    const int* heavy; int n_heavy;                 // warp-per-entry scatter of heavily shared entries
     const double* D; const double* dinv; const double* wdinv; const double* c; const double* b;
     const unsigned char* ew;
     const int* a_rowptr; const int* a_col; const double* a_val;
-    const int* c_colptr; const unsigned short* c_row; const double* c_val;
+    const int* c_colptr; const unsigned short* c_row; const double* c_val;   // c_row: row within its problem
     const double* Linv; const double* LinvT;
     // state
     double* x; double* y; double* r; double* rsw; double* z1;
     double* xk[2]; double* lam; double* vk;
     void* vstore;         // eigenvector blocks for warm starts (projection precision)
     const long long* voff;
-    double* tpart;        // [m * R]
+    double* tpart;        // [row_ctas]
     double* part_blk;     // [p * 4]
-    double* part_ent;     // [(max(ent_ctas + heavy_ctas, pos_ctas)) * 8]
+    double* part_ent;     // [max(ent_ctas + heavy_ctas, pos_ctas) * 8]
     double* part_obj;     // [col_ctas]
-    int ent_ctas, col_ctas, pos_ctas;
     Ctrl* ctrl;
 };
 
@@ -142,22 +189,32 @@ __device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCom
 
 // Kernel launchers (kernels.cu / project.cu). All return cudaError_t of the launch.
 cudaError_t launch_project(const ProjArgs& a, int mode, int prec, int smax, cudaStream_t st);
+// One launch of a given variant over a.count blocks (a.order may point into a longer order array).
+cudaError_t launch_project_variant(const ProjArgs& a, int mode, int prec, int variant, int smax, cudaStream_t st);
+int project_default_variant(int s, int prec);   // the variant launch_project picks for max size s
+bool project_variant_valid(int variant, int s, int prec);
+// Runs of `order` (sizes non-increasing) that share a variant; table[N] (N = 1..SDP_MAX_CLIQUE+1,
+// padded even order) overrides the default choice when non-NULL and valid.
+ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec,
+                        const int* table);
 cudaError_t project_prepare();   // raises the dynamic shared-memory limit of every variant
 size_t project_smem_bytes(int smax, int prec, int mode);
 int project_threads(int smax);
 size_t project_vstore_elems(int s);   // N*N with N = s rounded up to even
 cudaError_t launch_vstore_identity(const IterPtrs& P, int prec, cudaStream_t st);
 
-cudaError_t launch_iteration(const IterPtrs& P, int form, int prec, double rho, cudaStream_t st,
-                             cudaEvent_t* ev = nullptr);
-const char* phase_name(int form, int i);
+cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,
+                             cudaStream_t st, cudaEvent_t* ev = nullptr);
+int phase_count(const IterPtrs& P, int form);
+const char* phase_name(int form, bool batch, int i);
 cudaError_t launch_primal_rebuild_r(const IterPtrs& P, double rho, cudaStream_t st);
 cudaError_t launch_gather(const IterPtrs& P, const double* x, double* blocks, cudaStream_t st);
 cudaError_t launch_scatter(const IterPtrs& P, const double* blocks, double* out, cudaStream_t st);
 cudaError_t launch_ctrl_arm(Ctrl* ctrl, int n_iters, double tol, cudaStream_t st);
 cudaError_t launch_ctrl_reset(Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_ctrl_clear(Ctrl* ctrl, cudaStream_t st);
-int iteration_kernel_count(int form);
+int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form);
+cudaError_t launch_inst_reset(const IterPtrs& P, cudaStream_t st);   // every problem active again
 int record_error(int code, const std::string& msg);   // sets the message sdp_last_error() returns
 cudaError_t iteration_prepare();  // raises the dynamic shared-memory limit of the m-sized kernels
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <numeric>
 #include <thread>
 
@@ -26,10 +27,15 @@ inline long long find_entry(const std::vector<long long>& keys, long long k) {
     return (long long)(it - keys.begin());
 }
 
+// Set on the worker threads of a batch build: each problem is then built on one thread.
+thread_local bool t_serial = false;
+
+int worker_count() { return t_serial ? 1 : (int)std::max(1u, std::thread::hardware_concurrency()); }
+
 // Runs f(i) for i in [0, n) on up to hardware_concurrency threads (contiguous slices).
 template <typename F>
 void parallel_for(int n, F f) {
-    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int hw = worker_count();
     const int nt = std::max(1, std::min(hw, n));
     if (nt == 1) {
         for (int i = 0; i < n; ++i) f(i);
@@ -278,7 +284,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                 }
             }
         };
-        const unsigned hw = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)chunks));
+        const unsigned hw = (unsigned)std::max(1, std::min(worker_count(), chunks));
         for (int base = 0; base < chunks; base += (int)hw) {
             std::vector<std::thread> th;
             for (int ch = base; ch < std::min(chunks, base + (int)hw); ++ch) th.emplace_back(work, ch);
@@ -323,6 +329,131 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     hp.LinvT.assign(mm, 0.0);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j <= i; ++j) hp.LinvT[(size_t)j * m + i] = hp.Linv[(size_t)i * m + j];
+
+    hp.ninst = 1;
+    hp.inst_vtx = {0, n};
+    hp.inst_cl = {0, p};
+    hp.inst_e = {0, nEL};
+    hp.inst_pos = {0, hp.SL};
+    hp.inst_row = {0, m};
+    hp.mblk_off = {0, (long long)mm};
+    return SDP_OK;
+}
+
+int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out, std::string& err) {
+    if (count < 1 || !in) return fail(err, SDP_ERR_ARG, "count must be >= 1 and problems non-NULL");
+    // Each problem is built on one thread; problems are spread over the hardware threads.
+    std::vector<HostProblem> parts(count);
+    std::vector<int> rcs(count, SDP_OK);
+    std::vector<std::string> errs(count);
+    {
+        const int nt = std::max(1, std::min(worker_count(), count));
+        std::vector<std::thread> th;
+        std::atomic<int> next{0};
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&]() {
+                t_serial = true;
+                for (int q = next++; q < count; q = next++) {
+                    const sdp_problem& pr = in[q];
+                    rcs[q] = build_host_problem(pr.n, pr.m, pr.A_ptr, pr.A_row, pr.A_col, pr.A_val, pr.b,
+                                                pr.C_nnz, pr.C_row, pr.C_col, pr.C_val, pr.pat_nnz,
+                                                pr.pat_row, pr.pat_col, pr.p, pr.clique_ptr, pr.clique_vtx,
+                                                parts[q], errs[q]);
+                }
+            });
+        for (auto& x : th) x.join();
+    }
+    for (int q = 0; q < count; ++q)
+        if (rcs[q] != SDP_OK) return fail(err, rcs[q], "problem " + std::to_string(q) + ": " + errs[q]);
+
+    // Totals and limits of the union.
+    long long n = 0, m = 0, p = 0, nEL = 0, SL = 0, nnz = 0, mm = 0;
+    for (const HostProblem& h : parts) {
+        n += h.n; m += h.m; p += h.p; nEL += h.nEL; SL += h.SL; nnz += h.nnz;
+        mm += (long long)h.m * h.m;
+    }
+    if (n >= (1LL << 31) || m >= (1LL << 31) || p >= (1LL << 31))
+        return fail(err, SDP_ERR_UNSUPPORTED, "batch: n, m or p >= 2^31");
+    if (nEL >= (1LL << 31) || SL >= (1LL << 31) || nnz >= (1LL << 31))
+        return fail(err, SDP_ERR_UNSUPPORTED, "batch: |E_L|, S_L or nnz(A) >= 2^31");
+
+    HostProblem& hp = out;
+    hp = HostProblem();
+    hp.n = (int)n; hp.m = (int)m; hp.p = (int)p; hp.nEL = (int)nEL; hp.SL = (int)SL; hp.nnz = nnz;
+    hp.ninst = count;
+    for (auto* v : {&hp.inst_vtx, &hp.inst_cl, &hp.inst_e, &hp.inst_pos, &hp.inst_row}) v->assign(count + 1, 0);
+    hp.mblk_off.assign(count + 1, 0);
+    for (int q = 0; q < count; ++q) {
+        const HostProblem& h = parts[q];
+        hp.inst_vtx[q + 1] = hp.inst_vtx[q] + h.n;
+        hp.inst_cl[q + 1] = hp.inst_cl[q] + h.p;
+        hp.inst_e[q + 1] = hp.inst_e[q] + h.nEL;
+        hp.inst_pos[q + 1] = hp.inst_pos[q] + h.SL;
+        hp.inst_row[q + 1] = hp.inst_row[q] + h.m;
+        hp.mblk_off[q + 1] = hp.mblk_off[q] + (long long)h.m * h.m;
+        hp.smax = std::max(hp.smax, h.smax);
+    }
+    auto reserve_all = [&]() {
+        hp.pat_row.reserve(nEL); hp.pat_col.reserve(nEL); hp.ew.reserve(nEL);
+        hp.D.reserve(nEL); hp.dinv.reserve(nEL); hp.wdinv.reserve(nEL); hp.c.reserve(nEL);
+        hp.sc_ptr.reserve(nEL + 1); hp.c_colptr.reserve(nEL + 1);
+        hp.blk_off.reserve(p + 1); hp.blk_size.reserve(p);
+        hp.gather_idx.reserve(SL); hp.pos_w.reserve(SL); hp.sc_pos.reserve(SL);
+        hp.b.reserve(m); hp.a_rowptr.reserve(m + 1);
+        hp.a_col.reserve(nnz); hp.a_val.reserve(nnz); hp.c_row.reserve(nnz); hp.c_val.reserve(nnz);
+        hp.Linv.reserve(mm); hp.LinvT.reserve(mm);
+    };
+    reserve_all();
+    hp.sc_ptr.push_back(0);
+    hp.c_colptr.push_back(0);
+    hp.a_rowptr.push_back(0);
+    // Concatenate: indices into E_L, positions, vertices and nonzeros are shifted by the totals of
+    // the problems before; the CSC keeps rows within the problem (its y block is staged alone).
+    for (int q = 0; q < count; ++q) {
+        HostProblem& h = parts[q];
+        const int v0 = hp.inst_vtx[q], e0 = hp.inst_e[q], s0 = hp.inst_pos[q];
+        const int a0 = hp.a_rowptr.back();
+        for (int e = 0; e < h.nEL; ++e) {
+            hp.pat_row.push_back(h.pat_row[e] + v0);
+            hp.pat_col.push_back(h.pat_col[e] + v0);
+            hp.sc_ptr.push_back(h.sc_ptr[e + 1] + s0);
+            hp.c_colptr.push_back(h.c_colptr[e + 1] + a0);
+        }
+        hp.ew.insert(hp.ew.end(), h.ew.begin(), h.ew.end());
+        hp.D.insert(hp.D.end(), h.D.begin(), h.D.end());
+        hp.dinv.insert(hp.dinv.end(), h.dinv.begin(), h.dinv.end());
+        hp.wdinv.insert(hp.wdinv.end(), h.wdinv.begin(), h.wdinv.end());
+        hp.c.insert(hp.c.end(), h.c.begin(), h.c.end());
+        for (int k = 0; k < h.p; ++k) {
+            hp.blk_off.push_back(h.blk_off[k] + s0);
+            hp.blk_size.push_back(h.blk_size[k]);
+        }
+        for (int t = 0; t < h.SL; ++t) {
+            hp.gather_idx.push_back(h.gather_idx[t] + e0);
+            hp.sc_pos.push_back(h.sc_pos[t] + s0);
+        }
+        hp.pos_w.insert(hp.pos_w.end(), h.pos_w.begin(), h.pos_w.end());
+        for (int e : h.heavy) hp.heavy.push_back(e + e0);
+        hp.b.insert(hp.b.end(), h.b.begin(), h.b.end());
+        for (int i = 0; i < h.m; ++i) hp.a_rowptr.push_back(h.a_rowptr[i + 1] + a0);
+        for (int c : h.a_col) hp.a_col.push_back(c + e0);
+        hp.a_val.insert(hp.a_val.end(), h.a_val.begin(), h.a_val.end());
+        hp.c_row.insert(hp.c_row.end(), h.c_row.begin(), h.c_row.end());
+        hp.c_val.insert(hp.c_val.end(), h.c_val.begin(), h.c_val.end());
+        hp.Linv.insert(hp.Linv.end(), h.Linv.begin(), h.Linv.end());
+        hp.LinvT.insert(hp.LinvT.end(), h.LinvT.begin(), h.LinvT.end());
+        h = HostProblem();   // release the part as soon as it is copied
+    }
+    hp.blk_off.push_back((int)SL);
+    hp.voff.assign(p + 1, 0);
+    for (long long k = 0; k < p; ++k) {
+        const long long Nk = hp.blk_size[k] + (hp.blk_size[k] & 1);
+        hp.voff[k + 1] = hp.voff[k] + Nk * Nk;
+    }
+    hp.order.resize(p);
+    std::iota(hp.order.begin(), hp.order.end(), 0);
+    std::stable_sort(hp.order.begin(), hp.order.end(),
+                     [&](int x, int y) { return hp.blk_size[x] > hp.blk_size[y]; });
     return SDP_OK;
 }
 
