@@ -9,6 +9,11 @@ are reported beside it, and so is the CPU oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config C]
 
+--config 2 runs the batched workload instead: 512 independent block-arrow SDPs of uneven size in
+one handle (FP32 eigensolves with the projection variants tuned on the handle, FP64 affine step);
+a step is one cold-start batched solve until every problem has met the tolerance, and value counts
+the iterations of every problem (problem-iterations per second).
+
 For N > 1 the launcher starts one process per GPU; every rank solves its own replica (the
 single-instance path does not shard) and value = all ranks' iterations / slowest rank's time.
 """
@@ -37,6 +42,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
+FP32_MEASURED_TFLOPS = 73.3      # FMA-chain probe on this GB300 pool (8 independent chains/thread)
 
 
 def parse_args():
@@ -57,34 +63,57 @@ def parse_args():
 
 # ----------------------------------------------------------------------------- workload
 
+def _arrays(inst):
+    return dict(n=inst.n, cliques=inst.cliques, A_ptr=inst.A_ptr, A_row=inst.A_row, A_col=inst.A_col,
+                A_val=inst.A_val, b=inst.b, C_row=inst.C_row, C_col=inst.C_col, C_val=inst.C_val)
+
+
 def workload(config: int):
+    """(cfg, instances, arrays): one instance and its arrays, or lists of them for a batch."""
     from sdp_inputs import CONFIGS, config_instance
     cfg = dict(CONFIGS[config])
+    if cfg["count"] > 1:
+        insts = [config_instance(config, i) for i in range(cfg["count"])]
+        return cfg, insts, [_arrays(x) for x in insts]
     inst = config_instance(config)
-    arrs = dict(n=inst.n, cliques=inst.cliques, A_ptr=inst.A_ptr, A_row=inst.A_row, A_col=inst.A_col,
-                A_val=inst.A_val, b=inst.b, C_row=inst.C_row, C_col=inst.C_col, C_val=inst.C_val)
-    return cfg, inst, arrs
+    return cfg, inst, _arrays(inst)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_worker(args):
-    """Runs in a child process with one BLAS thread: times oracle iterations on the workload."""
+    """Runs in a child process with one BLAS thread: times oracle iterations on the workload (for a
+    batch, iterations of its problems one after another, each from a cold start, 50 per problem)."""
     from oracle import chordal_admm as orc
-    cfg, inst, arrs = workload(args.config)
-    t0 = time.perf_counter()
-    sdp = orc.ChordalSDP(inst.n, inst.cliques, inst.A_ptr, inst.A_row, inst.A_col, inst.A_val,
-                         inst.b, inst.C_row, inst.C_col, inst.C_val)
-    setup_s = time.perf_counter() - t0
+    from sdp_inputs import CONFIGS, config_instance
+    cfg = dict(CONFIGS[args.config])
+    batch = cfg["count"] > 1
     step = orc.primal_iteration if cfg["form"] == "primal" else orc.dual_iteration
-    st = orc.admm_init(sdp, cfg["form"])
-    iters, t0 = 0, time.perf_counter()
     limit = args.oracle_iters if args.oracle_iters > 0 else 10 ** 9
-    while iters < limit and (args.oracle_iters > 0 or time.perf_counter() - t0 < args.cpu_seconds):
-        st = step(sdp, st, cfg["rho"])
-        iters += 1
-    dt = time.perf_counter() - t0
-    print(json.dumps(dict(iters=iters, seconds=dt, setup_seconds=setup_s)))
+    iters, setup_s, run_s, problems, q = 0, 0.0, 0.0, 0, 0
+    t_all = time.perf_counter()
+    while iters < limit and (args.oracle_iters > 0 or run_s < args.cpu_seconds):
+        inst = config_instance(args.config, q % cfg["count"])
+        t0 = time.perf_counter()
+        sdp = orc.ChordalSDP(inst.n, inst.cliques, inst.A_ptr, inst.A_row, inst.A_col, inst.A_val,
+                             inst.b, inst.C_row, inst.C_col, inst.C_val)
+        setup_s += time.perf_counter() - t0
+        st = orc.admm_init(sdp, cfg["form"])
+        t0 = time.perf_counter()
+        k = 0
+        while iters < limit and (not batch or k < 50) and (args.oracle_iters > 0 or
+                                                           time.perf_counter() - t0 + run_s < args.cpu_seconds):
+            st = step(sdp, st, cfg["rho"])
+            iters += 1
+            k += 1
+        run_s += time.perf_counter() - t0
+        problems += 1
+        q += 1
+        if not batch:
+            break
+        if time.perf_counter() - t_all > 4 * max(args.cpu_seconds, 1.0) + 60:
+            break
+    print(json.dumps(dict(iters=iters, seconds=run_s, setup_seconds=setup_s, problems=problems)))
 
 
 def run_oracle(args, iters=0, seconds=None):
@@ -98,11 +127,16 @@ def run_oracle(args, iters=0, seconds=None):
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_entry(args, cfg):
+def cpu_baseline_entry(args, cfg, unit=UNIT):
     r = run_oracle(args)
-    return dict(value=r["iters"] / r["seconds"], unit=UNIT, cores=1, kind="oracle",
-                sample=f"{r['iters']} oracle {cfg['form']}-form iterations from a cold start on "
-                       f"{cfg['name']} (setup {r['setup_seconds']:.2f} s excluded), one BLAS thread")
+    if cfg["count"] > 1:
+        sample = (f"{r['iters']} oracle {cfg['form']}-form iterations over the first {r['problems']} problems "
+                  f"of {cfg['name']} (50 from a cold start each; setup {r['setup_seconds']:.2f} s excluded), "
+                  f"one BLAS thread")
+    else:
+        sample = (f"{r['iters']} oracle {cfg['form']}-form iterations from a cold start on "
+                  f"{cfg['name']} (setup {r['setup_seconds']:.2f} s excluded), one BLAS thread")
+    return dict(value=r["iters"] / r["seconds"], unit=unit, cores=1, kind="oracle", sample=sample)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -202,7 +236,8 @@ def roofline(phases, inst_sizes, cfg, prec, peaks, clocks):
         mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
         if prec == "fp32":
             peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-            peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+            peak_src = (f"derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock (an FMA-chain probe "
+                        f"measured {FP32_MEASURED_TFLOPS} TFLOP/s)")
         else:
             peak = FP64_NOMINAL_TFLOPS
             peak_src = "nominal FP64 1.25 TFLOP/s"
@@ -263,20 +298,22 @@ def run_reference(args):
     world, rank, local = dist_init(args)
     if rank != 0:
         return
-    cfg, inst, arrs = workload(args.config)
+    from sdp_inputs import CONFIGS
+    cfg = dict(CONFIGS[args.config])
+    unit = "problem-iter/s" if cfg["count"] > 1 else UNIT
     per_step = max(1, int(os.environ.get("BENCH_REF_ITERS", "10")))
     if args.warmup > 0:
         run_oracle(args, iters=min(per_step, 3))
     r = run_oracle(args, iters=per_step * max(1, args.steps))
     value = r["iters"] / r["seconds"]
-    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+    line = dict(impl="reference", metric=METRIC, value=value, unit=unit, n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * r["seconds"] / max(1, args.steps),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", config=dict(workload=cfg["name"], form=cfg["form"], rho=cfg["rho"],
                                               step=f"{per_step} oracle iterations"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                cpu_baseline=dict(value=value, unit=unit, cores=1, kind="oracle",
                                   sample=f"{r['iters']} {cfg['form']}-form oracle iterations, one BLAS thread"),
-                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                e2e=dict(value=value, unit=unit, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
 
@@ -292,16 +329,21 @@ def run_ours(args):
     torch.cuda.set_device(local)
     cadmm.load_library()
     cfg, inst, arrs = workload(args.config)
+    batch = cfg["count"] > 1
+    unit = "problem-iter/s" if batch else UNIT
     opts = cadmm.make_opts(rho=cfg["rho"], tol=cfg["tol"] if cfg["tol"] > 0 else 1e-4,
                            max_iter=cfg["max_iter"], check_every=16, form=cfg["form"], prec="fp32")
     solver = cadmm.ChordalADMM(arrs, opts)
     sz = solver.sizes
-    inst_sizes = dict(s_list=[len(c) for c in inst.cliques], p=sz["p"], nEL=sz["nE_lower"],
-                      SL=sz["S_lower"], m=sz["m"], nnz=sz["nnz_A"])
+    insts = inst if batch else [inst]
+    s_list = [len(c) for x in insts for c in x.cliques]
+    inst_sizes = dict(s_list=s_list, p=sz["p"], nEL=sz["nE_lower"], SL=sz["S_lower"], m=sz["m"],
+                      nnz=sz["nnz_A"])
     stream = torch.cuda.current_stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def timed_solves(k):
+        """k cold-start solves; iterations counted per problem (a batch sums its problems')."""
         iters, ms, launches, res = 0, [], 0, None
         for _ in range(k):
             flush.zero_()
@@ -313,10 +355,19 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-            iters += res["iters"]
-            launches += res["kernel_launches"] + 2      # + ctrl reset and the r rebuild
+            iters += int(solver.batch_results()["iters"].sum()) if batch else res["iters"]
+            launches += res["kernel_launches"] + (4 if batch else 2)   # + resets and the r rebuild
         return iters, ms, launches, res
 
+    tuned = None
+    if batch:
+        # projection kernel variant per clique order, tuned on this handle's own iterations
+        from paper_1609_06068_gb300 import autotune
+        solver.reset(stream)
+        solver.iterate(20, stream)
+        tr = autotune.tune_handle(solver.h, "fp32", reps=3)
+        names = cadmm.project_variants()
+        tuned = {str(n): names[v] for n, v in sorted(tr["table"].items())}
     for _ in range(args.warmup):
         solver.reset(stream)
         solver.solve(stream)
@@ -341,15 +392,22 @@ def run_ours(args):
 
     # FP64 eigensolves on the same instance (the plain baseline of the metric)
     fp64, phases64 = None, None
-    if args.fp64_steps > 0:
+    fp64_steps = min(args.fp64_steps, 1) if batch else args.fp64_steps
+    if fp64_steps > 0:
         solver.set_opts(prec="fp64")
-        it64, ms64, _, last64 = timed_solves(args.fp64_steps)
-        fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=UNIT, time_to_tol_ms=sum(ms64) / args.fp64_steps,
-                    iters_per_solve=it64 / args.fp64_steps, obj_dual=last64["obj_dual"],
+        it64, ms64, _, last64 = timed_solves(fp64_steps)
+        fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=unit, time_to_tol_ms=sum(ms64) / fp64_steps,
+                    iters_per_solve=it64 / fp64_steps, obj_dual=last64["obj_dual"],
                     obj_primal=last64["obj_primal"], status=last64["status"])
+        if batch:
+            fp64["batch_iters_per_solve"] = last64["iters"]
+        solver.reset(stream)
+        solver.iterate(20, stream)          # warm-started eigensolves, every problem still active
         phases64 = cadmm.sdp_time_phases(solver.h, reps=5, stream=stream)
         solver.set_opts(prec="fp32")
-    phases = cadmm.sdp_time_phases(solver.h, reps=50, stream=stream)
+    solver.reset(stream)
+    solver.iterate(20, stream)
+    phases = cadmm.sdp_time_phases(solver.h, reps=50 if not batch else 10, stream=stream)
 
     peaks = {}
     try:
@@ -360,50 +418,62 @@ def run_ours(args):
     roof = roofline(phases, inst_sizes, cfg, "fp32", peaks, clocks)
 
     # end to end through the C ABI from pinned host arrays: setup, solve, read the solution
-    pinned = {}
     h2d = 0
-    for k in ("A_ptr", "A_row", "A_col", "A_val", "b", "C_row", "C_col", "C_val"):
-        a = np.ascontiguousarray(arrs[k])
-        t = torch.from_numpy(a).pin_memory()
-        pinned[k] = t.numpy()
-        h2d += a.nbytes
-    cl = [np.asarray(c, np.int32) for c in arrs["cliques"]]
-    h2d += sum(c.nbytes for c in cl) + 4 * (len(cl) + 1)
-    e2e_arrs = dict(pinned, n=arrs["n"], cliques=cl)
+    e2e_list = []
+    for a_ in (arrs if batch else [arrs]):
+        pinned = {}
+        for k in ("A_ptr", "A_row", "A_col", "A_val", "b", "C_row", "C_col", "C_val"):
+            a = np.ascontiguousarray(a_[k])
+            t = torch.from_numpy(a).pin_memory()
+            pinned[k] = t.numpy()
+            h2d += a.nbytes
+        cl = [np.asarray(c, np.int32) for c in a_["cliques"]]
+        h2d += sum(c.nbytes for c in cl) + 4 * (len(cl) + 1)
+        e2e_list.append(dict(pinned, n=a_["n"], cliques=cl))
+    e2e_arrs = e2e_list if batch else e2e_list[0]
     e2e_iters, e2e_s, d2h = 0, 0.0, 0
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = cadmm.ChordalADMM(e2e_arrs, opts)
+        if tuned is not None:
+            cadmm.sdp_set_proj_table(s2.h, "fp32", {int(n): cadmm.project_variants().index(v)
+                                                    for n, v in tuned.items()})
         r2 = s2.solve(stream)
         X, y, Z = s2.solution()
+        per = s2.batch_results()["iters"] if batch else None
         s2.close()
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
-        e2e_iters += r2["iters"]
-        d2h = X.nbytes + y.nbytes + Z.nbytes + 64
+        e2e_iters += int(per.sum()) if batch else r2["iters"]
+        d2h = X.nbytes + y.nbytes + Z.nbytes + 64 + (per.nbytes * 6 if batch else 0)
     e2e = None
     if args.e2e_steps > 0:
         e2e_iters_all = reduce(world, e2e_iters, "sum")
         e2e_s_max = reduce(world, e2e_s, "max")
-        e2e = dict(value=e2e_iters_all / e2e_s_max, unit=UNIT, h2d_bytes_per_step=h2d,
+        e2e = dict(value=e2e_iters_all / e2e_s_max, unit=unit, h2d_bytes_per_step=h2d,
                    d2h_bytes_per_step=d2h, ms_per_step=1e3 * e2e_s_max / args.e2e_steps,
                    includes="sdp_setup (host maps, A D^-1 A^T, Cholesky, upload) + admm_solve + "
                             "sdp_get_solution")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_entry(args, cfg)
+        cpu = cpu_baseline_entry(args, cfg, unit)
 
     if rank == 0:
+        conf = dict(workload=cfg["name"], n=sz["n"], m=sz["m"], p=sz["p"], clique=sz["max_clique"],
+                    form=cfg["form"], rho=cfg["rho"], tol=opts.tol, max_iter=opts.max_iter,
+                    step="one cold-start solve to max(eps_p, eps_d) < tol",
+                    l2="256 MiB buffer written before every timed solve", parallelism=f"replicas x{world}")
+        if batch:
+            conf.update(problems=sz["batch"], clique_min=min(s_list), nnz_A=sz["nnz_A"],
+                        step="one cold-start batched solve until every problem has max(eps_p, eps_d) < tol",
+                        projection_variants=tuned)
         line = dict(
-            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            metric=METRIC, value=value, unit=unit, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f32 eigensolves + f64 affine/reductions", data="synthetic",
-            config=dict(workload=cfg["name"], n=sz["n"], m=sz["m"], p=sz["p"], clique=sz["max_clique"],
-                        form=cfg["form"], rho=cfg["rho"], tol=opts.tol, max_iter=opts.max_iter,
-                        step="one cold-start solve to max(eps_p, eps_d) < tol",
-                        l2="256 MiB buffer written before every timed solve", parallelism=f"replicas x{world}"),
+            config=conf,
             time_to_tol_ms=ms_per_step, iters_per_solve=fp32_iters_per_solve,
             obj_dual=last["obj_dual"], obj_primal=last["obj_primal"], status=last["status"],
             fp64_plain=fp64,
@@ -411,6 +481,8 @@ def run_ours(args):
             phases_ms_fp32=phases, phases_ms_fp64=phases64,
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks,
             gpu=torch.cuda.get_device_name(local))
+        if batch:
+            line["batch_iters_per_solve"] = last["iters"]
         print(json.dumps(line))
     solver.close()
     if world > 1:

@@ -225,6 +225,29 @@ int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stre
 int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
                         int count, int prec, void* cuda_stream);
 
+/* ---- kernel variants of the batched projection (no counterpart in the paper: implementation
+ * choices, exposed so that they can be tuned). Variant v in 0 .. project_variant_count()-1 is one
+ * eigensolver kernel shape (one-sided Jacobi with a warp segment or a CTA per block, two-sided
+ * Jacobi with a CTA per block) with a largest padded order (s rounded up to even) and a
+ * precision it accepts; project_variant_name(v) names it ("ow16": one-sided, a 16-lane warp
+ * segment per block, FP32, order <= 16). project_variant_fits(v, s, prec) says whether it takes
+ * blocks of order s in precision prec (1) or not (0). */
+int project_variant_count(void);
+const char* project_variant_name(int v);
+int project_variant_fits(int v, int s, int prec);
+
+/* project_psd_batched with every block on one given variant (device pointers as there).
+ * SDP_ERR_UNSUPPORTED when the variant does not fit some block or the precision. */
+int project_psd_batched_variant(const double* in, double* out, const int* sizes,
+                                const long long* offsets, int count, int prec, int variant,
+                                void* cuda_stream);
+
+/* Per handle: which variant projects the cliques of padded order N in precision prec.
+ * table[N] for N = 0 .. len-1 (host array; -1 or a variant that does not fit = the default for
+ * that order); len <= SDP_MAX_CLIQUE + 1. NULL restores the defaults. The iteration graphs are
+ * rebuilt at the next admm_iterate; iterates are unchanged. */
+int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len);
+
 /* Profiling: run `reps` iterations kernel by kernel (no graph) on cuda_stream with CUDA events
  * between the phases, and write the average device milliseconds of each phase of one iteration
  * to ms_out[0 .. count-1] in launch order (count = 6 primal, 7 dual, one more for the per-problem
@@ -236,7 +259,8 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
 const char* sdp_phase_name(sdp_handle h, int i);
 
 /* Batched PSD projection that allocates nothing (no counterpart in the paper: it exists for
- * callers, not for the method). Same arguments, kernels and results as project_psd_batched, for
+ * callers, not for the method). Same arguments and results (to rounding: every block goes to the
+ * kernel variant that fits the largest one) as project_psd_batched, for
  * callers that may not allocate device memory: code embedded in a host framework that owns all
  * device memory through a pool sized up front, and latency-bound loops where a cudaMalloc (which
  * may synchronize the device) is not acceptable. The per-call block schedule goes into a fixed

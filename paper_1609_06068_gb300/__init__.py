@@ -41,7 +41,9 @@ EXPORTS = [
     "sdp_setup", "sdp_setup_batch", "sdp_batch_layout", "sdp_batch_results", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
-    "project_psd_batched_noalloc", "sdp_free", "sdp_status_string", "sdp_last_error",
+    "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
+    "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_free",
+    "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
 
@@ -116,6 +118,11 @@ def load_library(path: str = LIB_PATH):
         "sdp_time_phases": (_I, [_P, _I, _P, _P, _I]),
         "sdp_phase_name": (ctypes.c_char_p, [_P, _I]),
         "project_psd_batched_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
+        "project_variant_count": (_I, []),
+        "project_variant_name": (ctypes.c_char_p, [_I]),
+        "project_variant_fits": (_I, [_I, _I, _I]),
+        "project_psd_batched_variant": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
+        "sdp_set_proj_table": (_I, [_P, _I, _P, _I]),
         "sdp_free": (None, [_P]),
         "sdp_status_string": (ctypes.c_char_p, [_I]),
         "sdp_last_error": (ctypes.c_char_p, []),
@@ -361,6 +368,42 @@ def project_psd_batched_noalloc(inp, out, sizes, offsets, prec="fp64", stream=No
     _check(load_library().project_psd_batched_noalloc(
         _dev_ptr(inp, need, "inp"), _dev_ptr(out, need, "out"), _ptr(sizes), _ptr(offsets), len(sizes),
         PRECS.get(prec, prec), _stream(stream)), "project_psd_batched_noalloc")
+
+
+def project_variants() -> list:
+    """Names of the projection kernel variants, by variant index."""
+    lib = load_library()
+    return [lib.project_variant_name(v).decode() for v in range(lib.project_variant_count())]
+
+
+def project_variant_fits(variant: int, s: int, prec="fp32") -> bool:
+    return bool(load_library().project_variant_fits(int(variant), int(s), PRECS.get(prec, prec)))
+
+
+def project_psd_batched_variant(inp, out, sizes, offsets, variant: int, prec="fp32", stream=None):
+    """project_psd_batched with every block on one kernel variant."""
+    sizes = _arr(sizes, np.int32)
+    offsets = _arr(offsets, np.int64)
+    need = int(np.max(offsets + sizes.astype(np.int64) * (sizes + 1) // 2)) if len(sizes) else 0
+    _check(load_library().project_psd_batched_variant(
+        _dev_ptr(inp, need, "inp"), _dev_ptr(out, need, "out"), _ptr(sizes), _ptr(offsets), len(sizes),
+        PRECS.get(prec, prec), int(variant), _stream(stream)), "project_psd_batched_variant")
+
+
+def sdp_set_proj_table(h, prec, table=None):
+    """Projection variant per padded block order for a handle (a dict {N: variant} or a sequence
+    indexed by N; None restores the defaults)."""
+    p = PRECS.get(prec, prec)
+    if table is None:
+        _check(load_library().sdp_set_proj_table(h, p, None, 0), "sdp_set_proj_table")
+        return
+    if isinstance(table, dict):
+        t = np.full(SDP_MAX_CLIQUE + 1, -1, np.int32)
+        for n, v in table.items():
+            t[int(n)] = int(v)
+    else:
+        t = _arr(table, np.int32)
+    _check(load_library().sdp_set_proj_table(h, p, _ptr(t), len(t)), "sdp_set_proj_table")
 
 
 def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:

@@ -33,7 +33,6 @@ int set_err(int code, const std::string& msg) {
     } while (0)
 
 constexpr double kWaitTimeoutSeconds = 600.0;
-constexpr int kColCtasPerSm = 4;
 
 double now_s() {
     using namespace std::chrono;
@@ -77,6 +76,8 @@ struct sdp_ctx {
     // host copies needed after setup
     std::vector<int> pat_row, pat_col, blk_off, gather_idx;
     std::vector<int> inst_vtx, inst_row, inst_cl, inst_e, inst_pos;
+    std::vector<int> order_h, blk_size_h;   // for rebuilding the projection plans
+    int ow_min_blocks = 0;
     cadmm::ProjPlan plan[2]{};    // projection launches per precision (SDP_PROJ_FP64, SDP_PROJ_FP32)
     std::vector<void*> allocs;
     IterPtrs P{};
@@ -234,55 +235,66 @@ int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// CTA schedules. No CTA spans two problems; within a problem the ranges follow the element order,
-// so a single problem gets the same split as an unscheduled grid would.
+// Work schedules. No CTA (or, for the passes over A, no warp chunk) spans two problems; within a
+// problem the ranges follow the element order.
 struct Schedules {
     std::vector<cadmm::Sched> row, tri, col, pos, ent, heavy;
-    std::vector<int> row_cta, inst_col_cta, inst_pos_cta, inst_ent_cta, inst_heavy_cta;
+    std::vector<int> row_chunk, inst_col_chunk, inst_pos_cta, inst_ent_cta, inst_heavy_cta;
 };
+
+constexpr int kChunksPerSm = 64;      // warp chunks per SM for the passes over A (8 CTAs of 8 warps)
 
 Schedules build_schedules(const HostProblem& hp, int num_sms) {
     Schedules S;
     const int Q = hp.ninst;
-    // CSR chunks: about two waves of CTAs over all of A, at least 2048 nonzeros each, <= 64 per row.
-    const long long target = std::max<long long>(2048, (hp.nnz + 2LL * num_sms - 1) / (2LL * num_sms));
-    S.row_cta.assign(hp.m + 1, 0);
+    const long long nchunk = (long long)kChunksPerSm * num_sms;
+    // CSR: each row split into chunks of about nnz / nchunk nonzeros (at least 1024, at most 256
+    // chunks per row); one warp per chunk.
+    const long long rt = std::max<long long>(1024, (hp.nnz + nchunk - 1) / nchunk);
+    S.row_chunk.assign(hp.m + 1, 0);
     for (int q = 0; q < Q; ++q)
         for (int i = hp.inst_row[q]; i < hp.inst_row[q + 1]; ++i) {
             const int lo0 = hp.a_rowptr[i], hi0 = hp.a_rowptr[i + 1];
             const long long len = hi0 - lo0;
-            const int R = (int)std::max<long long>(1, std::min<long long>(64, (len + target - 1) / target));
+            const int R = (int)std::max<long long>(1, std::min<long long>(256, (len + rt - 1) / rt));
             for (int ch = 0; ch < R; ++ch)
                 S.row.push_back({q, lo0 + (int)(len * ch / R), lo0 + (int)(len * (ch + 1) / R), i});
-            S.row_cta[i + 1] = (int)S.row.size();
+            S.row_chunk[i + 1] = (int)S.row.size();
         }
     // L^-1 / L^-T products: 8 rows (one per warp) per CTA.
     for (int q = 0; q < Q; ++q)
         for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1]; r += 8)
             S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
-    // CSC: about four CTAs per SM over all of A; each CTA a whole number of 32-column rounds.
-    S.inst_col_cta.assign(Q + 1, 0);
-    const long long col_target = std::max<long long>(1, (hp.nnz + 4LL * num_sms - 1) / (4LL * num_sms));
+    // A^T: chunks of whole slices with about nnz / nchunk stored elements (at least 256); one warp
+    // per chunk, one lane per column.
+    const long long ct = std::max<long long>(256, (hp.nnz + nchunk - 1) / nchunk);
+    S.inst_col_chunk.assign(Q + 1, 0);
     for (int q = 0; q < Q; ++q) {
-        const int e0 = hp.inst_e[q], e1 = hp.inst_e[q + 1];
-        const long long nq = e1 - e0;
-        const long long nnzq = (long long)hp.c_colptr[e1] - hp.c_colptr[e0];
-        long long k = std::max<long long>(1, (nnzq + col_target / 2) / col_target);
-        k = std::min<long long>(k, std::max<long long>(1, (nq + 31) / 32));
-        long long chunk = (nq + k - 1) / k;
-        chunk = std::max<long long>(32, (chunk + 31) / 32 * 32);
-        for (long long lo = e0; lo < e1; lo += chunk)
-            S.col.push_back({q, (int)lo, (int)std::min<long long>(lo + chunk, e1), 0});
-        S.inst_col_cta[q + 1] = (int)S.col.size();
+        int sl = hp.inst_sl[q];
+        const int s1 = hp.inst_sl[q + 1];
+        while (sl < s1) {
+            const int lo = sl;
+            long long acc = 0;
+            while (sl < s1 && (sl == lo || acc + 32LL * hp.sell_len[sl] <= ct)) {
+                acc += 32LL * hp.sell_len[sl];
+                ++sl;
+            }
+            S.col.push_back({q, lo, sl, 0});
+        }
+        S.inst_col_chunk[q + 1] = (int)S.col.size();
     }
-    // Packed positions and light entries: 256 per CTA; heavy entries: 8 (one per warp) per CTA.
+    // Light entries: 256 per CTA; heavy entries: 8 (one per warp) per CTA.
+    // Packed positions per CTA of the dual update: enough CTAs for 8 per SM, 256..2048 (1..8 per
+    // thread) each.
+    const int pos_per = (int)std::max<long long>(
+        256, std::min<long long>(2048, ((long long)hp.SL / (8LL * num_sms) + 255) / 256 * 256));
     S.inst_pos_cta.assign(Q + 1, 0);
     S.inst_ent_cta.assign(Q + 1, 0);
     S.inst_heavy_cta.assign(Q + 1, 0);
     size_t h = 0;
     for (int q = 0; q < Q; ++q) {
-        for (int lo = hp.inst_pos[q]; lo < hp.inst_pos[q + 1]; lo += 256)
-            S.pos.push_back({q, lo, std::min(lo + 256, hp.inst_pos[q + 1]), 0});
+        for (int lo = hp.inst_pos[q]; lo < hp.inst_pos[q + 1]; lo += pos_per)
+            S.pos.push_back({q, lo, std::min(lo + pos_per, hp.inst_pos[q + 1]), 0});
         S.inst_pos_cta[q + 1] = (int)S.pos.size();
         for (int lo = hp.inst_e[q]; lo < hp.inst_e[q + 1]; lo += 256)
             S.ent.push_back({q, lo, std::min(lo + 256, hp.inst_e[q + 1]), 0});
@@ -296,6 +308,77 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
     return S;
 }
 
+// The batched projection on caller buffers: blocks largest first, one launch per run of blocks
+// that share a kernel variant (variant < 0: the default for each size; else that variant for all).
+int run_project_batched(const double* in, double* out, const int* sizes, const long long* offsets, int count,
+                        int prec, int variant, void* cuda_stream) {
+    if (count < 0) return set_err(SDP_ERR_ARG, "count must be >= 0");
+    if (count == 0) return SDP_OK;
+    if (!in || !out || !sizes || !offsets) return set_err(SDP_ERR_ARG, "NULL argument");
+    if (prec != SDP_PROJ_FP64 && prec != SDP_PROJ_FP32) return set_err(SDP_ERR_ARG, "bad prec");
+    int smax = 0;
+    for (int k = 0; k < count; ++k) {
+        if (sizes[k] < 1) return set_err(SDP_ERR_ARG, "block sizes must be >= 1");
+        if (sizes[k] > SDP_MAX_CLIQUE) return set_err(SDP_ERR_UNSUPPORTED, "block larger than SDP_MAX_CLIQUE");
+        if (offsets[k] < 0) return set_err(SDP_ERR_ARG, "offsets must be >= 0");
+        smax = std::max(smax, sizes[k]);
+    }
+    if (variant >= 0 && !cadmm::project_variant_valid(variant, smax, prec))
+        return set_err(SDP_ERR_UNSUPPORTED, "the variant does not take these blocks");
+    std::vector<int> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
+    cudaStream_t st = as_stream(cuda_stream);
+    CK(cadmm::project_prepare());
+    // One stream-ordered device buffer holds offsets, sizes and order.
+    const size_t bytes = (size_t)count * (2 * sizeof(int) + sizeof(long long));
+    std::vector<unsigned char> host(bytes);
+    std::memcpy(host.data(), offsets, (size_t)count * sizeof(long long));
+    std::memcpy(host.data() + (size_t)count * sizeof(long long), sizes, (size_t)count * sizeof(int));
+    std::memcpy(host.data() + (size_t)count * (sizeof(long long) + sizeof(int)), order.data(),
+                (size_t)count * sizeof(int));
+    void* d = nullptr;
+    CK(cudaMallocAsync(&d, bytes, st));
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        cadmm::ProjArgs a{};
+        a.off = static_cast<const long long*>(d);
+        a.size = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) + (size_t)count * sizeof(long long));
+        const int* d_order = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) +
+                                                          (size_t)count * (sizeof(long long) + sizeof(int)));
+        a.rho = 1.0;
+        a.in = in;
+        a.out = out;
+        a.ctrl = nullptr;
+        const std::vector<int> sz(sizes, sizes + count);
+        cadmm::ProjPlan plan{};
+        if (variant >= 0) {
+            plan.runs = 1;
+            plan.start[0] = 0;
+            plan.count[0] = count;
+            plan.variant[0] = variant;
+            plan.smax[0] = smax;
+        } else {
+            int dev = 0, num_sms = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+                plan = cadmm::make_proj_plan(order, sz, prec, nullptr, cadmm::proj_ow_min_blocks(num_sms));
+            else
+                plan = cadmm::make_proj_plan(order, sz, prec, nullptr, 0);
+        }
+        for (int r = 0; r < plan.runs && e == cudaSuccess; ++r) {
+            a.order = d_order + plan.start[r];
+            a.count = plan.count[r];
+            e = cadmm::launch_project_variant(a, cadmm::PROJ_PLAIN, prec, plan.variant[r], plan.smax[r], st);
+        }
+    }
+    // The pageable host copy above returns once the data is staged, so `host` may go away.
+    const cudaError_t fe = cudaFreeAsync(d, st);
+    if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("project_psd_batched: ") + cudaGetErrorString(e));
+    if (fe != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(fe));
+    return SDP_OK;
+}
+
 int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     sdp_ctx* h = new sdp_ctx();
     std::unique_ptr<sdp_ctx> guard(h);
@@ -307,22 +390,25 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     h->blk_off = hp.blk_off; h->gather_idx = hp.gather_idx;
     h->inst_vtx = hp.inst_vtx; h->inst_row = hp.inst_row; h->inst_cl = hp.inst_cl;
     h->inst_e = hp.inst_e; h->inst_pos = hp.inst_pos;
-    h->plan[SDP_PROJ_FP64] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP64, nullptr);
-    h->plan[SDP_PROJ_FP32] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP32, nullptr);
+    h->order_h = hp.order;
+    h->blk_size_h = hp.blk_size;
     CK(cadmm::project_prepare());
     CK(cadmm::iteration_prepare());
 
     int num_sms = 0;
     CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->ow_min_blocks = cadmm::proj_ow_min_blocks(num_sms);
+    h->plan[SDP_PROJ_FP64] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP64, nullptr, h->ow_min_blocks);
+    h->plan[SDP_PROJ_FP32] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP32, nullptr, h->ow_min_blocks);
     const Schedules S = build_schedules(hp, num_sms);
     IterPtrs& P = h->P;
     P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
     P.ninst = hp.ninst;
     P.mmax = 0;
     for (int q = 0; q < hp.ninst; ++q) P.mmax = std::max(P.mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
-    P.row_ctas = (int)S.row.size();
+    P.row_chunks = (int)S.row.size();
     P.tri_ctas = (int)S.tri.size();
-    P.col_ctas = (int)S.col.size();
+    P.col_chunks = (int)S.col.size();
     P.pos_ctas = (int)S.pos.size();
     P.ent_ctas = (int)S.ent.size();
     P.heavy_ctas = (int)S.heavy.size();
@@ -345,13 +431,13 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(mblk_off, hp.mblk_off);
     UP(blk_inst, blk_inst);
     UP(row_sched, S.row);
-    UP(row_cta, S.row_cta);
+    UP(row_chunk, S.row_chunk);
     UP(tri_sched, S.tri);
     UP(col_sched, S.col);
     UP(pos_sched, S.pos);
     UP(ent_sched, S.ent);
     UP(heavy_sched, S.heavy);
-    UP(inst_col_cta, S.inst_col_cta);
+    UP(inst_col_chunk, S.inst_col_chunk);
     UP(inst_pos_cta, S.inst_pos_cta);
     UP(inst_ent_cta, S.inst_ent_cta);
     UP(inst_heavy_cta, S.inst_heavy_cta);
@@ -374,9 +460,11 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(a_rowptr, hp.a_rowptr);
     UP(a_col, hp.a_col);
     UP(a_val, hp.a_val);
-    UP(c_colptr, hp.c_colptr);
-    UP(c_row, hp.c_row);
-    UP(c_val, hp.c_val);
+    UP(sell_col, hp.sell_col);
+    UP(sell_len, hp.sell_len);
+    UP(sell_off, hp.sell_off);
+    UP(sell_row, hp.sell_row);
+    UP(sell_val, hp.sell_val);
     UP(Linv, hp.Linv);
     UP(LinvT, hp.LinvT);
 #undef UP
@@ -392,10 +480,10 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
     if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
     if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
-    if ((rc = h->dalloc(&P.tpart, (size_t)P.row_ctas))) return rc;
+    if ((rc = h->dalloc(&P.tpart, (size_t)P.row_chunks))) return rc;
     if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
     if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas + P.heavy_ctas, P.pos_ctas) * 8))) return rc;
-    if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_ctas))) return rc;
+    if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_chunks))) return rc;
     if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
     {
         double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
@@ -660,57 +748,39 @@ int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stre
 
 int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
                         int count, int prec, void* cuda_stream) {
-    if (count < 0) return set_err(SDP_ERR_ARG, "count must be >= 0");
-    if (count == 0) return SDP_OK;
-    if (!in || !out || !sizes || !offsets) return set_err(SDP_ERR_ARG, "NULL argument");
+    return run_project_batched(in, out, sizes, offsets, count, prec, -1, cuda_stream);
+}
+
+int project_psd_batched_variant(const double* in, double* out, const int* sizes, const long long* offsets,
+                                int count, int prec, int variant, void* cuda_stream) {
+    if (variant < 0 || variant >= cadmm::PV_COUNT) return set_err(SDP_ERR_ARG, "no such variant");
+    return run_project_batched(in, out, sizes, offsets, count, prec, variant, cuda_stream);
+}
+
+int project_variant_count(void) { return cadmm::PV_COUNT; }
+
+const char* project_variant_name(int v) {
+    static const char* names[cadmm::PV_COUNT] = {"os32", "os64", "ts16", "ts32", "ts64", "ts96",
+                                                 "ow8", "ow16", "ow32"};
+    return (v >= 0 && v < cadmm::PV_COUNT) ? names[v] : nullptr;
+}
+
+int project_variant_fits(int v, int s, int prec) {
+    if (s < 1 || s > SDP_MAX_CLIQUE) return 0;
+    return cadmm::project_variant_valid(v, s, prec) ? 1 : 0;
+}
+
+int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
     if (prec != SDP_PROJ_FP64 && prec != SDP_PROJ_FP32) return set_err(SDP_ERR_ARG, "bad prec");
-    int smax = 0;
-    for (int k = 0; k < count; ++k) {
-        if (sizes[k] < 1) return set_err(SDP_ERR_ARG, "block sizes must be >= 1");
-        if (sizes[k] > SDP_MAX_CLIQUE) return set_err(SDP_ERR_UNSUPPORTED, "block larger than SDP_MAX_CLIQUE");
-        if (offsets[k] < 0) return set_err(SDP_ERR_ARG, "offsets must be >= 0");
-        smax = std::max(smax, sizes[k]);
-    }
-    // schedule: largest blocks first
-    std::vector<int> order(count);
-    for (int k = 0; k < count; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
-    cudaStream_t st = as_stream(cuda_stream);
-    CK(cadmm::project_prepare());
-    // One stream-ordered device buffer holds order, sizes and offsets.
-    const size_t bytes = (size_t)count * (2 * sizeof(int) + sizeof(long long));
-    std::vector<unsigned char> host(bytes);
-    std::memcpy(host.data(), offsets, (size_t)count * sizeof(long long));
-    std::memcpy(host.data() + (size_t)count * sizeof(long long), sizes, (size_t)count * sizeof(int));
-    std::memcpy(host.data() + (size_t)count * (sizeof(long long) + sizeof(int)), order.data(),
-                (size_t)count * sizeof(int));
-    void* d = nullptr;
-    CK(cudaMallocAsync(&d, bytes, st));
-    cudaError_t e = cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
-        cadmm::ProjArgs a{};
-        a.off = static_cast<const long long*>(d);
-        a.size = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) + (size_t)count * sizeof(long long));
-        a.order = reinterpret_cast<const int*>(static_cast<unsigned char*>(d) +
-                                               (size_t)count * (sizeof(long long) + sizeof(int)));
-        a.rho = 1.0;
-        a.in = in;
-        a.out = out;
-        a.ctrl = nullptr;
-        // One launch per run of blocks that share a kernel variant, largest blocks first.
-        const std::vector<int> sz(sizes, sizes + count);
-        const cadmm::ProjPlan plan = cadmm::make_proj_plan(order, sz, prec, nullptr);
-        const int* d_order = a.order;
-        for (int r = 0; r < plan.runs && e == cudaSuccess; ++r) {
-            a.order = d_order + plan.start[r];
-            a.count = plan.count[r];
-            e = cadmm::launch_project_variant(a, cadmm::PROJ_PLAIN, prec, plan.variant[r], plan.smax[r], st);
-        }
-    }
-    // The pageable host copy above returns once the data is staged, so `host` may go away.
-    const cudaError_t fe = cudaFreeAsync(d, st);
-    if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("project_psd_batched: ") + cudaGetErrorString(e));
-    if (fe != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(fe));
+    if (table && (len < 0 || len > SDP_MAX_CLIQUE + 1)) return set_err(SDP_ERR_ARG, "len out of range");
+    CK(cudaSetDevice(h->device));
+    std::vector<int> t(SDP_MAX_CLIQUE + 2, -1);
+    if (table)
+        for (int i = 0; i < len; ++i) t[i] = table[i];
+    h->plan[prec] = cadmm::make_proj_plan(h->order_h, h->blk_size_h, prec, table ? t.data() : nullptr,
+                                          h->ow_min_blocks);
+    h->destroy_graphs();
     return SDP_OK;
 }
 

@@ -24,7 +24,6 @@ constexpr int kEntThreads = 256;  // entry-wise kernels
 constexpr int kRowThreads = 256;  // CSR row chunks
 constexpr int kTriThreads = 256;  // triangular products (8 warps, one row per warp)
 constexpr int kColThreads = 256;  // CSC columns
-constexpr int kColGroup = 8;      // lanes per CSC column
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -77,7 +76,7 @@ __device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int 
         for (int q = threadIdx.x; q < n_part; q += blockDim.x)
             for (int k = 0; k < 5; ++k) v[k] += P.part_ent[q * 8 + k];
     }
-    for (int q = threadIdx.x; q < P.col_ctas; q += blockDim.x) v[5] += P.part_obj[q];
+    for (int q = threadIdx.x; q < P.col_chunks; q += blockDim.x) v[5] += P.part_obj[q];
     for (int i = threadIdx.x; i < P.m; i += blockDim.x) v[6] = fma(P.b[i], P.y[i], v[6]);
     block_sum<7>(v, red);
     if (threadIdx.x != 0) return;
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(256) k_finalize_batch(IterPtrs P, int form, do
             for (int c = P.inst_pos_cta[q] + lane; c < P.inst_pos_cta[q + 1]; c += 32)
                 for (int k = 0; k < 5; ++k) v[k] += P.part_ent[c * 8 + k];
         }
-        for (int c = P.inst_col_cta[q] + lane; c < P.inst_col_cta[q + 1]; c += 32) v[5] += P.part_obj[c];
+        for (int c = P.inst_col_chunk[q] + lane; c < P.inst_col_chunk[q + 1]; c += 32) v[5] += P.part_obj[c];
         for (int i = P.inst_row[q] + lane; i < P.inst_row[q + 1]; i += 32) v[6] = fma(P.b[i], P.y[i], v[6]);
 #pragma unroll
         for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
@@ -385,28 +384,30 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
 }
 
 // ---------------------------------------------------------------- t = A (w r / D), CSR chunks
-// Four independent accumulators per thread keep several gathers in flight.
+// One warp per chunk of a row (no block-wide reduction); four loads in flight per lane.
 __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
-    __shared__ double red[33];
     pdl_wait();
     if (P.ctrl->done) return;
-    const Sched sc = P.row_sched[blockIdx.x];
+    const int lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5);
+    if (ch >= P.row_chunks) return;
+    const Sched sc = P.row_sched[ch];
     if (stopped(P, sc.q)) return;
-    const int lo = sc.lo, hi = sc.hi;
-    const int bd = blockDim.x;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int j = lo + threadIdx.x;
-    for (; j + 3 * bd < hi; j += 4 * bd) {
-        a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
-        a1 = fma(P.a_val[j + bd], P.rsw[P.a_col[j + bd]], a1);
-        a2 = fma(P.a_val[j + 2 * bd], P.rsw[P.a_col[j + 2 * bd]], a2);
-        a3 = fma(P.a_val[j + 3 * bd], P.rsw[P.a_col[j + 3 * bd]], a3);
+    const int hi = sc.hi;
+    double a0 = 0.0, a1 = 0.0;
+    int j = sc.lo + lane;
+    for (; j + 96 < hi; j += 128) {
+        const double v0 = P.a_val[j], v1 = P.a_val[j + 32], v2 = P.a_val[j + 64], v3 = P.a_val[j + 96];
+        const int c0 = P.a_col[j], c1 = P.a_col[j + 32], c2 = P.a_col[j + 64], c3 = P.a_col[j + 96];
+        a0 = fma(v0, P.rsw[c0], a0);
+        a1 = fma(v1, P.rsw[c1], a1);
+        a0 = fma(v2, P.rsw[c2], a0);
+        a1 = fma(v3, P.rsw[c3], a1);
     }
-    for (; j < hi; j += bd) a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
+    for (; j < hi; j += 32) a0 = fma(P.a_val[j], P.rsw[P.a_col[j]], a0);
     pdl_trigger();
-    double v[1] = {(a0 + a1) + (a2 + a3)};
-    block_sum<1>(v, red);
-    if (threadIdx.x == 0) P.tpart[blockIdx.x] = v[0];
+    const double t = warp_sum(a0 + a1);
+    if (lane == 0) P.tpart[ch] = t;
 }
 
 // ---------------------------------------------------------------- z = L^-1 (t - rhs2)
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
     const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double t = 0.0;
-        for (int c = P.row_cta[r0 + i]; c < P.row_cta[r0 + i + 1]; ++c) t += P.tpart[c];
+        for (int c = P.row_chunk[r0 + i]; c < P.row_chunk[r0 + i + 1]; ++c) t += P.tpart[c];
         const double bi = P.b[r0 + i];
         const double rhs2 = form == SDP_PRIMAL ? bi : -__dmul_rn(rinv, bi);
         u[i] = t - rhs2;
@@ -470,48 +471,46 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
     }
 }
 
-// ---------------------------------------------------------------- x = (r - A^T y) / D, CSC
-// kColGroup lanes per column; y is staged in shared memory. Also the partial objective sums
-// sum_e w_e c_e x_e of this CTA.
+// ---------------------------------------------------------------- x = (r - A^T y) / D
+// A^T in sliced ELL form (columns ordered by length within windows of 256, so slices pad
+// little): one warp per chunk of slices of one problem, one lane per column, so
+// every load of the slice is coalesced and no lane-to-lane reduction is needed. y is read through
+// the read-only cache (a problem's y is small and hot). Also the partial objective
+// sum_e w_e c_e x_e of the chunk.
 __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
-    extern __shared__ double ys[];
-    __shared__ double red[33];
     pdl_wait();
     if (P.ctrl->done) return;
-    const Sched sc = P.col_sched[blockIdx.x];
+    const int lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * (kColThreads / 32) + (threadIdx.x >> 5);
+    if (ch >= P.col_chunks) return;
+    const Sched sc = P.col_sched[ch];
     if (stopped(P, sc.q)) return;
-    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = P.y[r0 + i];
-    __syncthreads();
-    const int gid = threadIdx.x / kColGroup, gl = threadIdx.x % kColGroup;
-    const int ngroups = blockDim.x / kColGroup;
+    const double* __restrict__ y = P.y + P.inst_row[sc.q];
     double obj = 0.0;
-    for (int e0 = sc.lo; e0 < sc.hi; e0 += ngroups) {
-        const int e = e0 + gid;
-        const bool valid = e < sc.hi;
+    for (int sl = sc.lo; sl < sc.hi; ++sl) {
+        const int e = P.sell_col[32 * sl + lane], len = P.sell_len[sl];
+        const double* __restrict__ val = P.sell_val + P.sell_off[sl] + lane;
+        const unsigned short* __restrict__ row = P.sell_row + P.sell_off[sl] + lane;
         double s0 = 0.0, s1 = 0.0;
-        if (valid) {
-            const int lo = P.c_colptr[e], hi = P.c_colptr[e + 1];
-            int j = lo + gl;
-            for (; j + kColGroup < hi; j += 2 * kColGroup) {
-                s0 = fma(P.c_val[j], ys[P.c_row[j]], s0);
-                s1 = fma(P.c_val[j + kColGroup], ys[P.c_row[j + kColGroup]], s1);
-            }
-            if (j < hi) s0 = fma(P.c_val[j], ys[P.c_row[j]], s0);
+        int k = 0;
+        for (; k + 3 < len; k += 4) {
+            const double v0 = val[32 * k], v1 = val[32 * (k + 1)], v2 = val[32 * (k + 2)], v3 = val[32 * (k + 3)];
+            const int r0 = row[32 * k], r1 = row[32 * (k + 1)], r2 = row[32 * (k + 2)], r3 = row[32 * (k + 3)];
+            s0 = fma(v0, __ldg(y + r0), s0);
+            s1 = fma(v1, __ldg(y + r1), s1);
+            s0 = fma(v2, __ldg(y + r2), s0);
+            s1 = fma(v3, __ldg(y + r3), s1);
         }
-        double s = s0 + s1;
-#pragma unroll
-        for (int o = kColGroup / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (valid && gl == 0) {
-            const double xe = (P.r[e] - s) * P.dinv[e];
+        for (; k < len; ++k) s0 = fma(val[32 * k], __ldg(y + row[32 * k]), s0);
+        if (e >= 0) {
+            const double xe = (P.r[e] - (s0 + s1)) * P.dinv[e];
             P.x[e] = xe;
             obj = fma((double)P.ew[e] * P.c[e], xe, obj);
         }
     }
     pdl_trigger();
-    double v[1] = {obj};
-    block_sum<1>(v, red);
-    if (threadIdx.x == 0) P.part_obj[blockIdx.x] = v[0];
+    obj = warp_sum(obj);
+    if (lane == 0) P.part_obj[ch] = obj;
 }
 
 // ---------------------------------------------------------------- dual-form multiplier update
@@ -653,14 +652,18 @@ struct Marks {
 cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, cudaStream_t st, Marks& mk) {
     cudaError_t e;
     mk.mark();
-    if ((e = launch_pdl(k_spmv_rows, dim3(P.row_ctas), dim3(kRowThreads), 0, st, P)) != cudaSuccess) return e;
+    const int warps = kRowThreads / 32;
+    if ((e = launch_pdl(k_spmv_rows, dim3(cdiv(P.row_chunks, warps)), dim3(kRowThreads), 0, st, P)) != cudaSuccess)
+        return e;
     const size_t mbytes = (size_t)P.mmax * sizeof(double);   // the largest problem's y, staged
     mk.mark();
     if ((e = launch_pdl(k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) return e;
     mk.mark();
     if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
     mk.mark();
-    if ((e = launch_pdl(k_spmv_cols, dim3(P.col_ctas), dim3(kColThreads), mbytes, st, P)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_spmv_cols, dim3(cdiv(P.col_chunks, kColThreads / 32)), dim3(kColThreads), 0, st, P)) !=
+        cudaSuccess)
+        return e;
     if (form == SDP_DUAL) {
         mk.mark();
         return launch_pdl(k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);
@@ -681,8 +684,7 @@ cudaError_t iteration_prepare() {
     const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,

@@ -194,8 +194,9 @@ __device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int p
 // Batches: true when clique blk belongs to a problem that has stopped, so the CTA must return.
 // In the primal form the iteration right after the stop copies the block's current x_k to the
 // other ping-pong buffer first, so both hold it for every later parity.
+// The threads t0, t0 + stride, ... share the copy.
 template <int MODE>
-__device__ __forceinline__ bool block_stopped(const ProjArgs& a, int blk, int s, long long off) {
+__device__ __forceinline__ bool block_stopped(const ProjArgs& a, int blk, int s, long long off, int t0, int stride) {
     if (a.inst_conv == nullptr) return false;
     const int cv = a.inst_conv[a.blk_inst[blk]];
     if (cv < 0) return false;
@@ -204,9 +205,13 @@ __device__ __forceinline__ bool block_stopped(const ProjArgs& a, int blk, int s,
         const double* cur = (it & 1) ? a.xk[1] : a.xk[0];
         double* nxt = (it & 1) ? a.xk[0] : a.xk[1];
         const int len = s * (s + 1) / 2;
-        for (int q = threadIdx.x; q < len; q += blockDim.x) nxt[off + q] = cur[off + q];
+        for (int q = t0; q < len; q += stride) nxt[off + q] = cur[off + q];
     }
     return true;
+}
+template <int MODE>
+__device__ __forceinline__ bool block_stopped(const ProjArgs& a, int blk, int s, long long off) {
+    return block_stopped<MODE>(a, blk, s, off, threadIdx.x, blockDim.x);
 }
 
 template <typename T, int MODE, class SH>
@@ -816,6 +821,226 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     if (a.part != nullptr && tid == 0) a.part[blk * 4 + 3] = (double)sweeps;
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32, padded order N <= NR (NR = 8, 16, 32): one warp segment of NR lanes per clique (32 / NR
+// cliques per warp, 4 warps per CTA), lane c holding column c of G = B V in registers, so a round
+// of the one-sided Jacobi iteration needs no barrier and no shared memory: the partner column
+// arrives by shuffles and both ends compute the rotation from the same Gram entries. The shift is
+// sigma = 2 ||W||_F, so every column of G keeps a norm mu_j = lambda_j + sigma >= ||W||_F; V is
+// not tracked: G's columns converge to mu_j v_j (B = W + sigma I is positive definite and
+// G = B V), so v_j = g_j / mu_j and lambda_j = mu_j - sigma. The normalized columns are kept as
+// the next call's warm start (G = B V_prev). Segments of one warp stop independently; a stopped
+// segment's columns are left as they are while the others finish.
+template <int NR>
+struct OWLayout {
+    static constexpr int SEG = 32 / NR;            // cliques per warp
+    static constexpr int WARPS = 4;
+    static constexpr int BPC = SEG * WARPS;        // cliques per CTA
+    static constexpr int LD = NR + 1;
+    static constexpr size_t kBytes = (size_t)BPC * NR * LD * sizeof(float);
+};
+
+template <int NR>
+__device__ __forceinline__ float seg_sum(float v) {
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int NR>
+__device__ __forceinline__ float seg_maxf(float v) {
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <int NR>
+__device__ __forceinline__ double seg_maxd(double v) {
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <int NR>
+__device__ __forceinline__ double seg_sumd(double v) {
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MODE, int NR>
+__global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a, double rinv) {
+    using L = OWLayout<NR>;
+    constexpr int LD = L::LD;
+    extern __shared__ __align__(16) unsigned char smem_ow[];
+    pdl_wait();
+    if (a.ctrl != nullptr && a.ctrl->done) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = lane / NR, c = lane % NR, base = seg * NR;
+    const int slot = warp * L::SEG + seg;
+    const int idx = blockIdx.x * L::BPC + slot;
+    float* Ws = reinterpret_cast<float*>(smem_ow) + (size_t)slot * NR * LD;
+    int blk = -1, s = 0;
+    long long off = 0;
+    if (idx < a.count) {
+        blk = a.order ? a.order[idx] : idx;
+        s = a.size[blk];
+        off = a.off[blk];
+        if (block_stopped<MODE>(a, blk, s, off, c, NR)) {
+            blk = -1;
+            s = 0;
+        }
+    }
+    const bool act = blk >= 0;
+    const int N = s + (s & 1);
+    const bool warm = act && a.vstore != nullptr && a.ctrl != nullptr;
+    float* vglob = (act && a.vstore != nullptr) ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+
+    // ---- W scaled by 2^-e2 (exact) into the segment's tile, both triangles, zero padding
+    double wmax = 0.0;
+    if (c < s)
+        for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
+    wmax = seg_maxd<NR>(wmax);
+    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) Ws[r * LD + c] = 0.f;
+    __syncwarp();
+    if (c < s)
+        for (int r = c; r < s; ++r) {
+            const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
+            Ws[r * LD + c] = wt;
+            Ws[c * LD + r] = wt;
+        }
+    __syncwarp();
+
+    // ---- sigma = 2 ||W||_F and the initial columns: G = B (cold) or B V_prev (warm)
+    float sq = 0.f;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sq = fmaf(Ws[r * LD + c], Ws[r * LD + c], sq);
+    const float sigma = 2.f * sqrtf(seg_sum<NR>(sq));
+    float g[NR];
+    if (warm) {
+        float vr[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) vr[r] = (r < N && c < N) ? vglob[r * N + c] : (r == c ? 1.f : 0.f);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float acc = sigma * vr[r];
+#pragma unroll
+            for (int m = 0; m < NR; ++m) acc = fmaf(Ws[r * LD + m], vr[m], acc);
+            g[r] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) g[r] = Ws[r * LD + c] + ((r == c && c < N) ? sigma : 0.f);
+    }
+    if (c >= N) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) g[r] = 0.f;
+    }
+
+    // ---- sweeps over the round-robin schedule of N players
+    int sweeps = 0;
+    bool done = !act;
+    for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
+        if (__all_sync(0xffffffffu, done)) break;
+        float alpha = 0.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) alpha = fmaf(g[r], g[r], alpha);
+        const int rounds = __reduce_max_sync(0xffffffffu, done ? 0 : N - 1);
+        float worst = 0.f;
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int p = (!done && c < N && rd < N - 1) ? rr_partner(c, rd, N) : c;
+            float gp[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) gp[r] = __shfl_sync(0xffffffffu, g[r], base + p);
+            float gam = 0.f;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) gam = fmaf(g[r], gp[r], gam);
+            const float beta = __shfl_sync(0xffffffffu, alpha, base + p);
+            if (p != c && fabsf(gam) > 1.0e-30f) {
+                const bool first = c < p;
+                const float ai = first ? alpha : beta, aj = first ? beta : alpha;
+                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
+                const float zeta = __fdividef(aj - ai, 2.f * gam);
+                const float az = fabsf(zeta);
+                float den;
+                if (az > 1.0e15f) {
+                    den = 2.f * az;
+                } else {
+                    const float x = fmaf(zeta, zeta, 1.f);
+                    den = az + x * rsqrtf(x);
+                }
+                const float t = copysignf(__fdividef(1.f, den), zeta);
+                const float cc = __frsqrt_rn(fmaf(t, t, 1.f));
+                const float sn = t * cc;
+                const float sg = first ? -sn : sn;      // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) g[r] = fmaf(sg, gp[r], cc * g[r]);
+                alpha = first ? ai - t * gam : aj + t * gam;
+            }
+        }
+        if (!done) ++sweeps;
+        worst = seg_maxf<NR>(worst);
+        if (worst < kOneSidedStop * kOneSidedStop) done = true;
+    }
+
+    // ---- lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into the tile
+    float mu2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) mu2 = fmaf(g[r], g[r], mu2);
+    const float mu = sqrtf(mu2);
+    const float inv = mu > 0.f ? 1.f / mu : 0.f;
+    const float lam = mu - sigma;
+    const float qs = (act && c < N && lam > 0.f) ? sqrtf(lam) * inv : 0.f;
+    if (vglob != nullptr && c < N) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r < N) vglob[r * N + c] = mu > 0.f ? g[r] * inv : (r == c ? 1.f : 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) Ws[r * LD + c] = g[r] * qs;
+    __syncwarp();
+
+    // ---- rebuild the lower triangle of Q Q^T, column by column, and apply the epilogue
+    pdl_trigger();
+    double pv[3] = {0.0, 0.0, 0.0};
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL && act) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
+    for (int cb = 0; cb < s; ++cb) {
+        const float* Qb = Ws + cb * LD;
+        for (int ra = cb + c; ra < s; ra += NR) {
+            const float* Qa = Ws + ra * LD;
+            float acc = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
+            const double xv = (double)acc * up;
+            const int pos = packed_pos(ra, cb, s);
+            if (MODE == PROJ_PRIMAL) {
+                const double u = a.x[a.gather_idx[off + pos]];
+                const double l = a.lam[off + pos];
+                const double d = xv - u;
+                xk_new[off + pos] = xv;
+                a.lam[off + pos] = l + a.rho * d;                  // Eq. LambdakUpdate
+                const double wgt = (ra == cb) ? 1.0 : 2.0;
+                pv[0] += wgt * d * d;
+                pv[1] += wgt * xv * xv;
+                pv[2] += wgt * u * u;
+            } else {
+                a.out[off + pos] = xv;
+            }
+        }
+    }
+    if (MODE == PROJ_PRIMAL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pv[k] = seg_sumd<NR>(pv[k]);
+        if (act && c == 0) {
+            a.part[blk * 4 + 0] = pv[0];
+            a.part[blk * 4 + 1] = pv[1];
+            a.part[blk * 4 + 2] = pv[2];
+        }
+    }
+    if (act && a.part != nullptr && c == 0) a.part[blk * 4 + 3] = (double)sweeps;
+}
+
 template <typename T, int MODE, class SH>
 cudaError_t prepare_one() {
     const size_t smem = project_smem_bytes(SDP_MAX_CLIQUE, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
@@ -828,12 +1053,21 @@ cudaError_t prepare_os() {
                                 (int)OSLayout<CPL>::kBytes);
 }
 
+template <int MODE, int NR>
+cudaError_t prepare_ow() {
+    return cudaFuncSetAttribute(k_project_ow<MODE, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)OWLayout<NR>::kBytes);
+}
+
 template <typename T, int MODE>
 cudaError_t prepare_mode() {
     cudaError_t e;
     if (sizeof(T) == 4) {
         if ((e = prepare_os<MODE, 1>()) != cudaSuccess) return e;
         if ((e = prepare_os<MODE, 2>()) != cudaSuccess) return e;
+        if ((e = prepare_ow<MODE, 8>()) != cudaSuccess) return e;
+        if ((e = prepare_ow<MODE, 16>()) != cudaSuccess) return e;
+        if ((e = prepare_ow<MODE, 32>()) != cudaSuccess) return e;
     }
     if ((e = prepare_one<T, MODE, ShapeS16>()) != cudaSuccess) return e;
     if ((e = prepare_one<T, MODE, ShapeS32>()) != cudaSuccess) return e;
@@ -850,6 +1084,15 @@ cudaError_t launch_mode(const ProjArgs& a, int variant, int smax, cudaStream_t s
             return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
         case PV_OS2:
             return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
+        case PV_OW8:
+            return launch_pdl(k_project_ow<MODE, 8>, dim3((a.count + OWLayout<8>::BPC - 1) / OWLayout<8>::BPC),
+                              dim3(128), OWLayout<8>::kBytes, st, a, rinv);
+        case PV_OW16:
+            return launch_pdl(k_project_ow<MODE, 16>, dim3((a.count + OWLayout<16>::BPC - 1) / OWLayout<16>::BPC),
+                              dim3(128), OWLayout<16>::kBytes, st, a, rinv);
+        case PV_OW32:
+            return launch_pdl(k_project_ow<MODE, 32>, dim3((a.count + OWLayout<32>::BPC - 1) / OWLayout<32>::BPC),
+                              dim3(128), OWLayout<32>::kBytes, st, a, rinv);
         case PV_TS16:
             return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
         case PV_TS32:
@@ -895,7 +1138,9 @@ cudaError_t project_prepare() {
 
 int project_default_variant(int s, int prec) {
     const int N = s + (s & 1);
-    if (prec == SDP_PROJ_FP32 && N <= 32) return PV_OS1;
+    if (prec == SDP_PROJ_FP32 && N <= 8) return PV_OW8;
+    if (prec == SDP_PROJ_FP32 && N <= 16) return PV_OW16;
+    if (prec == SDP_PROJ_FP32 && N <= 32) return PV_OW32;
     if (prec == SDP_PROJ_FP32 && N <= 64) return PV_OS2;
     if (N <= 16) return PV_TS16;
     if (N <= 32) return PV_TS32;
@@ -907,6 +1152,9 @@ bool project_variant_valid(int variant, int s, int prec) {
     const int N = s + (s & 1);
     switch (variant) {
         case PV_OS1: return prec == SDP_PROJ_FP32 && N <= 32;
+        case PV_OW8: return prec == SDP_PROJ_FP32 && N <= 8;
+        case PV_OW16: return prec == SDP_PROJ_FP32 && N <= 16;
+        case PV_OW32: return prec == SDP_PROJ_FP32 && N <= 32;
         case PV_OS2: return prec == SDP_PROJ_FP32 && N <= 64;
         case PV_TS16: return N <= 16;
         case PV_TS32: return N <= 32;
@@ -916,13 +1164,20 @@ bool project_variant_valid(int variant, int s, int prec) {
     }
 }
 
-ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec, const int* table) {
+ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec, const int* table,
+                        int ow_min_blocks) {
+    // A warp segment per block pays off when there are enough blocks to fill the GPU with warps;
+    // with fewer, a CTA per block finishes each block sooner.
+    long long small = 0;
+    for (int k : order) small += (size[k] + (size[k] & 1)) <= 32;
+    const bool use_ow = small >= ow_min_blocks;
     ProjPlan pl{};
     pl.runs = 0;
     for (size_t i = 0; i < order.size(); ++i) {
         const int s = size[order[i]];
         const int N = s + (s & 1);
         int v = project_default_variant(s, prec);
+        if (!use_ow && (v == PV_OW8 || v == PV_OW16 || v == PV_OW32)) v = PV_OS1;
         if (table != nullptr && project_variant_valid(table[N], s, prec)) v = table[N];
         if (pl.runs > 0 && pl.variant[pl.runs - 1] == v) {
             ++pl.count[pl.runs - 1];
@@ -947,6 +1202,8 @@ ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& s
     }
     return pl;
 }
+
+int proj_ow_min_blocks(int num_sms) { return 4 * num_sms; }
 
 cudaError_t launch_project_variant(const ProjArgs& a, int mode, int prec, int variant, int smax, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;

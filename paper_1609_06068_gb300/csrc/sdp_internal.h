@@ -42,14 +42,22 @@ struct HostProblem {
     std::vector<unsigned char> ew;              // [nEL] weight 1 (diagonal) or 2
     std::vector<int> a_rowptr, a_col;           // CSR of A (rows = constraints)
     std::vector<double> a_val;
-    std::vector<int> c_colptr;                  // CSC of A (columns = E_L entries)
+    std::vector<int> c_colptr;                  // CSC of A (columns = E_L entries); host only
     std::vector<unsigned short> c_row;
     std::vector<double> c_val;
+    // A^T in sliced ELL form for the device: slot t of slice s holds column sell_col[32 s + t]
+    // (-1: empty; a slice never spans two problems), padded to the slice's longest column;
+    // element k of that column sits at sell_off[s] + 32 k + t (padding: value 0, row 0). Rows
+    // are numbered within the problem.
+    std::vector<int> sell_col, sell_len;        // [32 nslices], [nslices]
+    std::vector<long long> sell_off;            // [nslices+1]
+    std::vector<unsigned short> sell_row;
+    std::vector<double> sell_val;
     std::vector<double> Linv, LinvT;            // per instance an m_q x m_q row-major block
     // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
     int ninst = 1;
-    std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row;   // vertices, cliques, E_L
-                                                                      // entries, positions, rows
+    std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
+                                                                      // E_L entries, positions, rows, slices
     std::vector<long long> mblk_off;                        // offsets of the L^-1 blocks
 };
 
@@ -107,7 +115,7 @@ struct Sched {
 
 // Projection launches: the cliques in processing order (largest first) split into runs that use
 // the same kernel variant. A run [start, start + count) of `order` goes to one launch.
-enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_COUNT };
+enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_OW8, PV_OW16, PV_OW32, PV_COUNT };
 constexpr int kMaxProjRuns = 64;
 struct ProjPlan {
     int runs;
@@ -123,15 +131,16 @@ struct IterPtrs {
     const int* inst_row;            // [ninst+1] first constraint of each problem
     const long long* mblk_off;      // [ninst+1] offset of each problem's block of L^-1 and L^-T
     const int* blk_inst;            // [p] problem of each clique
-    // CTA schedules
-    const Sched* row_sched; int row_ctas; const int* row_cta;   // CSR chunks; row_cta[m+1]
-    const Sched* tri_sched; int tri_ctas;                        // <= 8 rows of L^-1 per CTA
-    const Sched* col_sched; int col_ctas;                        // CSC entry ranges
-    const Sched* pos_sched; int pos_ctas;                        // packed positions
-    const Sched* ent_sched; int ent_ctas;                        // light entries, one per thread
-    const Sched* heavy_sched; int heavy_ctas;                    // heavy-list ranges, one per warp
-    // per problem: its first CTA in each schedule that produces residual partials ([ninst+1])
-    const int* inst_col_cta; const int* inst_pos_cta; const int* inst_ent_cta; const int* inst_heavy_cta;
+    // Work schedules. The two passes over A are split into warp-sized chunks (8 per CTA); the
+    // other kernels give one Sched per CTA.
+    const Sched* row_sched; int row_chunks; const int* row_chunk;  // CSR chunks; row_chunk[m+1]
+    const Sched* tri_sched; int tri_ctas;                          // <= 8 rows of L^-1 per CTA
+    const Sched* col_sched; int col_chunks;                        // slice ranges of A^T
+    const Sched* pos_sched; int pos_ctas;                          // packed positions
+    const Sched* ent_sched; int ent_ctas;                          // light entries, one per thread
+    const Sched* heavy_sched; int heavy_ctas;                      // heavy-list ranges, one per warp
+    // per problem: its first entry in each schedule that produces residual partials ([ninst+1])
+    const int* inst_col_chunk; const int* inst_pos_cta; const int* inst_ent_cta; const int* inst_heavy_cta;
     double* inst_res;     // [ninst * 4]: eps_p, eps_d, obj_p, obj_d of its last iteration
     int* inst_conv;       // [ninst]: iteration at which it stopped (converged or NaN), or -1
     int* inst_stat;       // [ninst]: SDP_OK, SDP_MAX_ITER or SDP_ERR_NAN
@@ -142,17 +151,18 @@ struct IterPtrs {
     const double* D; const double* dinv; const double* wdinv; const double* c; const double* b;
     const unsigned char* ew;
     const int* a_rowptr; const int* a_col; const double* a_val;
-    const int* c_colptr; const unsigned short* c_row; const double* c_val;   // c_row: row within its problem
+    const int* sell_col; const int* sell_len; const long long* sell_off;    // A^T, sliced ELL
+    const unsigned short* sell_row; const double* sell_val;                  // rows within the problem
     const double* Linv; const double* LinvT;
     // state
     double* x; double* y; double* r; double* rsw; double* z1;
     double* xk[2]; double* lam; double* vk;
     void* vstore;         // eigenvector blocks for warm starts (projection precision)
     const long long* voff;
-    double* tpart;        // [row_ctas]
+    double* tpart;        // [row_chunks]
     double* part_blk;     // [p * 4]
     double* part_ent;     // [max(ent_ctas + heavy_ctas, pos_ctas) * 8]
-    double* part_obj;     // [col_ctas]
+    double* part_obj;     // [col_chunks]
     Ctrl* ctrl;
 };
 
@@ -196,7 +206,8 @@ bool project_variant_valid(int variant, int s, int prec);
 // Runs of `order` (sizes non-increasing) that share a variant; table[N] (N = 1..SDP_MAX_CLIQUE+1,
 // padded even order) overrides the default choice when non-NULL and valid.
 ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec,
-                        const int* table);
+                        const int* table, int ow_min_blocks);
+int proj_ow_min_blocks(int num_sms);   // blocks of order <= 32 below which a CTA per block is used
 cudaError_t project_prepare();   // raises the dynamic shared-memory limit of every variant
 size_t project_smem_bytes(int smax, int prec, int mode);
 int project_threads(int smax);

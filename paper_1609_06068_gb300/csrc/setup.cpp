@@ -330,7 +330,58 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     for (int i = 0; i < m; ++i)
         for (int j = 0; j <= i; ++j) hp.LinvT[(size_t)j * m + i] = hp.Linv[(size_t)i * m + j];
 
+    // ---- A^T as sliced ELL (32 columns per slice, one lane per column on the device). Within
+    // each window of 256 consecutive columns the columns are ordered by length (longest first,
+    // stable), so a slice pads to a length close to its columns' own; the window keeps the
+    // per-column reads and writes of a slice within 256 consecutive entries.
+    {
+        constexpr int kWindow = 256;
+        const int ns = (nEL + 31) / 32;
+        std::vector<int> slot_col(32LL * ns, -1);
+        std::vector<int> cols;
+        for (int w0 = 0; w0 < nEL; w0 += kWindow) {
+            const int w1 = std::min(w0 + kWindow, nEL);
+            cols.resize(w1 - w0);
+            std::iota(cols.begin(), cols.end(), w0);
+            std::stable_sort(cols.begin(), cols.end(), [&](int x, int y) {
+                return hp.c_colptr[x + 1] - hp.c_colptr[x] > hp.c_colptr[y + 1] - hp.c_colptr[y];
+            });
+            for (int t = 0; t < w1 - w0; ++t) slot_col[w0 + t] = cols[t];
+        }
+        hp.sell_col.assign(slot_col.begin(), slot_col.end());
+        hp.sell_len.resize(ns);
+        hp.sell_off.resize(ns + 1);
+        long long off = 0;
+        for (int sl = 0; sl < ns; ++sl) {
+            int len = 0;
+            for (int t = 0; t < 32; ++t) {
+                const int c = slot_col[32LL * sl + t];
+                if (c >= 0) len = std::max(len, hp.c_colptr[c + 1] - hp.c_colptr[c]);
+            }
+            hp.sell_len[sl] = len;
+            hp.sell_off[sl] = off;
+            off += 32LL * len;
+        }
+        hp.sell_off[ns] = off;
+        if (off >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "padded nnz(A) >= 2^31");
+        hp.sell_val.assign(off, 0.0);
+        hp.sell_row.assign(off, 0);
+        for (int sl = 0; sl < ns; ++sl)
+            for (int t = 0; t < 32; ++t) {
+                const int c = slot_col[32LL * sl + t];
+                if (c < 0) continue;
+                for (int j = hp.c_colptr[c]; j < hp.c_colptr[c + 1]; ++j) {
+                    const long long q = hp.sell_off[sl] + 32LL * (j - hp.c_colptr[c]) + t;
+                    hp.sell_val[q] = hp.c_val[j];
+                    hp.sell_row[q] = hp.c_row[j];
+                }
+            }
+        std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
+        std::vector<unsigned short>().swap(hp.c_row);
+    }
+
     hp.ninst = 1;
+    hp.inst_sl = {0, (int)hp.sell_len.size()};
     hp.inst_vtx = {0, n};
     hp.inst_cl = {0, p};
     hp.inst_e = {0, nEL};
@@ -381,7 +432,11 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
     hp = HostProblem();
     hp.n = (int)n; hp.m = (int)m; hp.p = (int)p; hp.nEL = (int)nEL; hp.SL = (int)SL; hp.nnz = nnz;
     hp.ninst = count;
-    for (auto* v : {&hp.inst_vtx, &hp.inst_cl, &hp.inst_e, &hp.inst_pos, &hp.inst_row}) v->assign(count + 1, 0);
+    for (auto* v : {&hp.inst_vtx, &hp.inst_cl, &hp.inst_e, &hp.inst_pos, &hp.inst_row, &hp.inst_sl})
+        v->assign(count + 1, 0);
+    long long sell_total = 0;
+    for (const HostProblem& h : parts) sell_total += h.sell_off.back();
+    if (sell_total >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "batch: padded nnz(A) >= 2^31");
     hp.mblk_off.assign(count + 1, 0);
     for (int q = 0; q < count; ++q) {
         const HostProblem& h = parts[q];
@@ -390,25 +445,28 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         hp.inst_e[q + 1] = hp.inst_e[q] + h.nEL;
         hp.inst_pos[q + 1] = hp.inst_pos[q] + h.SL;
         hp.inst_row[q + 1] = hp.inst_row[q] + h.m;
+        hp.inst_sl[q + 1] = hp.inst_sl[q] + (int)h.sell_len.size();
         hp.mblk_off[q + 1] = hp.mblk_off[q] + (long long)h.m * h.m;
         hp.smax = std::max(hp.smax, h.smax);
     }
     auto reserve_all = [&]() {
         hp.pat_row.reserve(nEL); hp.pat_col.reserve(nEL); hp.ew.reserve(nEL);
         hp.D.reserve(nEL); hp.dinv.reserve(nEL); hp.wdinv.reserve(nEL); hp.c.reserve(nEL);
-        hp.sc_ptr.reserve(nEL + 1); hp.c_colptr.reserve(nEL + 1);
+        hp.sc_ptr.reserve(nEL + 1);
+        hp.sell_col.reserve(32LL * hp.inst_sl[count]); hp.sell_len.reserve(hp.inst_sl[count]);
+        hp.sell_off.reserve(hp.inst_sl[count] + 1);
+        hp.sell_val.reserve(sell_total); hp.sell_row.reserve(sell_total);
         hp.blk_off.reserve(p + 1); hp.blk_size.reserve(p);
         hp.gather_idx.reserve(SL); hp.pos_w.reserve(SL); hp.sc_pos.reserve(SL);
         hp.b.reserve(m); hp.a_rowptr.reserve(m + 1);
-        hp.a_col.reserve(nnz); hp.a_val.reserve(nnz); hp.c_row.reserve(nnz); hp.c_val.reserve(nnz);
+        hp.a_col.reserve(nnz); hp.a_val.reserve(nnz);
         hp.Linv.reserve(mm); hp.LinvT.reserve(mm);
     };
     reserve_all();
     hp.sc_ptr.push_back(0);
-    hp.c_colptr.push_back(0);
     hp.a_rowptr.push_back(0);
     // Concatenate: indices into E_L, positions, vertices and nonzeros are shifted by the totals of
-    // the problems before; the CSC keeps rows within the problem (its y block is staged alone).
+    // the problems before; A^T keeps rows within the problem (each chunk reads its problem's y).
     for (int q = 0; q < count; ++q) {
         HostProblem& h = parts[q];
         const int v0 = hp.inst_vtx[q], e0 = hp.inst_e[q], s0 = hp.inst_pos[q];
@@ -417,8 +475,15 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
             hp.pat_row.push_back(h.pat_row[e] + v0);
             hp.pat_col.push_back(h.pat_col[e] + v0);
             hp.sc_ptr.push_back(h.sc_ptr[e + 1] + s0);
-            hp.c_colptr.push_back(h.c_colptr[e + 1] + a0);
         }
+        const long long so = hp.sell_val.size();
+        for (size_t sl = 0; sl < h.sell_len.size(); ++sl) {
+            hp.sell_len.push_back(h.sell_len[sl]);
+            hp.sell_off.push_back(h.sell_off[sl] + so);
+        }
+        for (int c : h.sell_col) hp.sell_col.push_back(c >= 0 ? c + e0 : -1);
+        hp.sell_val.insert(hp.sell_val.end(), h.sell_val.begin(), h.sell_val.end());
+        hp.sell_row.insert(hp.sell_row.end(), h.sell_row.begin(), h.sell_row.end());
         hp.ew.insert(hp.ew.end(), h.ew.begin(), h.ew.end());
         hp.D.insert(hp.D.end(), h.D.begin(), h.D.end());
         hp.dinv.insert(hp.dinv.end(), h.dinv.begin(), h.dinv.end());
@@ -438,13 +503,12 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         for (int i = 0; i < h.m; ++i) hp.a_rowptr.push_back(h.a_rowptr[i + 1] + a0);
         for (int c : h.a_col) hp.a_col.push_back(c + e0);
         hp.a_val.insert(hp.a_val.end(), h.a_val.begin(), h.a_val.end());
-        hp.c_row.insert(hp.c_row.end(), h.c_row.begin(), h.c_row.end());
-        hp.c_val.insert(hp.c_val.end(), h.c_val.begin(), h.c_val.end());
         hp.Linv.insert(hp.Linv.end(), h.Linv.begin(), h.Linv.end());
         hp.LinvT.insert(hp.LinvT.end(), h.LinvT.begin(), h.LinvT.end());
         h = HostProblem();   // release the part as soon as it is copied
     }
     hp.blk_off.push_back((int)SL);
+    hp.sell_off.push_back((long long)hp.sell_val.size());
     hp.voff.assign(p + 1, 0);
     for (long long k = 0; k < p; ++k) {
         const long long Nk = hp.blk_size[k] + (hp.blk_size[k] & 1);
