@@ -225,6 +225,33 @@ int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stre
 int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
                         int count, int prec, void* cuda_stream);
 
+/* ---- new data for an existing handle ---------------------------------------------------------
+ * Replace the cost (c_lower: device array of nE_lower values, C on E_L in the handle's order, as
+ * sdp_get_maps lists it) or the right-hand side (b: device array of m values). The KKT factor does
+ * not depend on either, so nothing is refactored; iterates are kept. Stream-ordered. */
+int sdp_set_cost(sdp_handle h, const double* c_lower, void* cuda_stream);
+int sdp_set_rhs(sdp_handle h, const double* b, void* cuda_stream);
+
+/* ---- differentiation of unrolled iterations (not in the paper) ----------------------------------
+ * sdp_unrolled_forward resets the handle and runs exactly T iterations of Algorithm 1 (form must
+ * be SDP_PRIMAL and prec SDP_PROJ_FP64; cliques of order <= 32), keeping the iterates
+ * (x_k, lambda_k) every ckpt_every iterations in device memory owned by the handle. X_T is the
+ * affine iterate x of iteration T; it is copied to x_out (device, nE_lower values; may be NULL)
+ * and left in the handle (sdp_get_state).
+ *
+ * sdp_unrolled_backward is reverse mode through those iterations. xbar (device, nE_lower) is
+ * dL/dtheta for the lower-triangle values theta of X_T (an off-diagonal theta moves X_ij and X_ji
+ * together). It writes cbar (device, nE_lower): dL/dtheta_C through the iterations, where theta_C
+ * are the lower-triangle values of C (a loss that uses C directly adds that term itself), and
+ * bbar (device, m): dL/db. Each segment of ckpt_every iterations is recomputed from its checkpoint
+ * to recover the eigenvectors of every projection; the derivative of the projection is the
+ * Daleckii-Krein formula (f'(0) = 0, f' of the mean for eigenvalues closer than 1e-12 max|lambda|),
+ * the KKT step is self-adjoint. Stream-ordered, returns after the stream finished. It fails with
+ * SDP_ERR_ARG if the data or options changed after the forward call; it leaves the handle's
+ * iterates at some recomputed step (call admm_reset before solving again). */
+int sdp_unrolled_forward(sdp_handle h, int T, int ckpt_every, double* x_out, void* cuda_stream);
+int sdp_unrolled_backward(sdp_handle h, const double* xbar, double* cbar, double* bbar, void* cuda_stream);
+
 /* ---- kernel variants of the batched projection (no counterpart in the paper: implementation
  * choices, exposed so that they can be tuned). Variant v in 0 .. project_variant_count()-1 is one
  * eigensolver kernel shape (one-sided Jacobi with a warp segment or a CTA per block, two-sided

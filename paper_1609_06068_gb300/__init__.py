@@ -42,7 +42,8 @@ EXPORTS = [
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
-    "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_free",
+    "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_set_cost",
+    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_free",
     "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
@@ -123,6 +124,10 @@ def load_library(path: str = LIB_PATH):
         "project_variant_fits": (_I, [_I, _I, _I]),
         "project_psd_batched_variant": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
         "sdp_set_proj_table": (_I, [_P, _I, _P, _I]),
+        "sdp_set_cost": (_I, [_P, _P, _P]),
+        "sdp_set_rhs": (_I, [_P, _P, _P]),
+        "sdp_unrolled_forward": (_I, [_P, _I, _I, _P, _P]),
+        "sdp_unrolled_backward": (_I, [_P, _P, _P, _P, _P]),
         "sdp_free": (None, [_P]),
         "sdp_status_string": (ctypes.c_char_p, [_I]),
         "sdp_last_error": (ctypes.c_char_p, []),
@@ -404,6 +409,34 @@ def sdp_set_proj_table(h, prec, table=None):
     else:
         t = _arr(table, np.int32)
     _check(load_library().sdp_set_proj_table(h, p, _ptr(t), len(t)), "sdp_set_proj_table")
+
+
+def sdp_set_cost(h, c_lower, stream=None):
+    """New cost C for the handle: a float64 CUDA tensor of its lower-pattern values (E_L order)."""
+    n = sdp_get_sizes(h)["nE_lower"]
+    _check(load_library().sdp_set_cost(h, _dev_ptr(c_lower, n, "c_lower"), _stream(stream)), "sdp_set_cost")
+
+
+def sdp_set_rhs(h, b, stream=None):
+    """New right-hand side b for the handle: a float64 CUDA tensor of m values."""
+    m = sdp_get_sizes(h)["m"]
+    _check(load_library().sdp_set_rhs(h, _dev_ptr(b, m, "b"), _stream(stream)), "sdp_set_rhs")
+
+
+def sdp_unrolled_forward(h, T: int, ckpt_every: int = 20, x_out=None, stream=None):
+    """T primal-form FP64 iterations from a reset, with checkpoints; X_T into x_out (CUDA tensor)."""
+    n = sdp_get_sizes(h)["nE_lower"]
+    ptr = None if x_out is None else _dev_ptr(x_out, n, "x_out")
+    _check(load_library().sdp_unrolled_forward(h, int(T), int(ckpt_every), ptr, _stream(stream)),
+           "sdp_unrolled_forward")
+
+
+def sdp_unrolled_backward(h, xbar, cbar, bbar, stream=None):
+    """Reverse mode of the last sdp_unrolled_forward: dL/dtheta_C into cbar and dL/db into bbar."""
+    sz = sdp_get_sizes(h)
+    _check(load_library().sdp_unrolled_backward(
+        h, _dev_ptr(xbar, sz["nE_lower"], "xbar"), _dev_ptr(cbar, sz["nE_lower"], "cbar"),
+        _dev_ptr(bbar, sz["m"], "bbar"), _stream(stream)), "sdp_unrolled_backward")
 
 
 def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:

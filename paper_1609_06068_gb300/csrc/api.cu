@@ -72,12 +72,26 @@ struct sdp_ctx {
     int device = 0;
     admm_opts opts{};
     int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0, ninst = 1;
+    long long vstore_elems = 0;   // sum over cliques of N_k^2
     long long nnz = 0;
     // host copies needed after setup
     std::vector<int> pat_row, pat_col, blk_off, gather_idx;
     std::vector<int> inst_vtx, inst_row, inst_cl, inst_e, inst_pos;
     std::vector<int> order_h, blk_size_h;   // for rebuilding the projection plans
     int ow_min_blocks = 0;
+    // Unrolled iterations kept for reverse mode (sdp_unrolled_forward / _backward).
+    struct Adjoint {
+        int T = 0, K = 0, nseg = 0, n_large = 0;
+        bool valid = false;
+        size_t cap_ckpt = 0, cap_seg = 0;   // doubles held by ckpt, and by Wseg + Vseg
+        double* ckpt = nullptr;             // nseg x [x_k (S_L), lambda_k (S_L)]
+        double* Wseg = nullptr;             // K x S_L: W_k of each iteration of a segment
+        double* Vseg = nullptr;             // K x (sum N_k^2): their eigenvectors
+        double *lam_prev = nullptr, *Xb = nullptr, *Lb = nullptr, *ub = nullptr;
+        double *cbar = nullptr, *bbar = nullptr;
+        cadmm::IterPtrs AP{};               // the forward's pointers with adjoint vectors swapped in
+        std::vector<void*> seg_allocs;
+    } adj;
     cadmm::ProjPlan plan[2]{};    // projection launches per precision (SDP_PROJ_FP64, SDP_PROJ_FP32)
     std::vector<void*> allocs;
     IterPtrs P{};
@@ -117,6 +131,7 @@ struct sdp_ctx {
     ~sdp_ctx() {
         cudaSetDevice(device);
         destroy_graphs();
+        for (void* a : adj.seg_allocs) cudaFree(a);
         for (void* a : allocs) cudaFree(a);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto& e : ev)
@@ -394,6 +409,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     h->blk_size_h = hp.blk_size;
     CK(cadmm::project_prepare());
     CK(cadmm::iteration_prepare());
+    CK(cadmm::adjoint_prepare());
 
     int num_sms = 0;
     CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -489,6 +505,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
         double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
         if ((rc = h->dalloc(&vs, (size_t)hp.voff[hp.p]))) return rc;
         P.vstore = vs;
+        h->vstore_elems = hp.voff[hp.p];
     }
     CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -781,6 +798,178 @@ int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len) {
     h->plan[prec] = cadmm::make_proj_plan(h->order_h, h->blk_size_h, prec, table ? t.data() : nullptr,
                                           h->ow_min_blocks);
     h->destroy_graphs();
+    return SDP_OK;
+}
+
+int sdp_set_cost(sdp_handle h, const double* c_lower, void* cuda_stream) {
+    if (!h || !c_lower) return set_err(SDP_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = as_stream(cuda_stream);
+    CK(cudaMemcpyAsync(const_cast<double*>(h->P.c), c_lower, sizeof(double) * h->nEL, cudaMemcpyDeviceToDevice, st));
+    h->adj.valid = false;
+    return rebuild_r_if_primal(h, st);      // the primal right-hand side holds -c/rho
+}
+
+int sdp_set_rhs(sdp_handle h, const double* b, void* cuda_stream) {
+    if (!h || !b) return set_err(SDP_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(const_cast<double*>(h->P.b), b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice,
+                       as_stream(cuda_stream)));
+    h->adj.valid = false;
+    return SDP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device memory for T unrolled iterations with checkpoints every K (reused when large enough).
+int ensure_adjoint(sdp_ctx* h, int T, int K) {
+    auto& A = h->adj;
+    const size_t SL = (size_t)std::max(1, h->SL), VS = (size_t)std::max<long long>(1, h->vstore_elems);
+    const int nseg = (T + K - 1) / K;
+    const size_t need_ckpt = (size_t)nseg * 2 * SL, need_seg = (size_t)K * (SL + VS);
+    if (A.Xb == nullptr) {
+        int rc;
+        auto& P = h->P;
+        A.AP = P;
+        double *xbar, *rsw, *rbar, *ybar, *z1, *tpart, *pobj;
+        int* conv;
+        cadmm::Ctrl* ctrl;
+        if ((rc = h->dalloc(&A.lam_prev, SL)) || (rc = h->dalloc(&A.Xb, SL)) || (rc = h->dalloc(&A.Lb, SL)) ||
+            (rc = h->dalloc(&A.ub, SL)) || (rc = h->dalloc(&A.cbar, h->nEL)) || (rc = h->dalloc(&A.bbar, h->m)) ||
+            (rc = h->dalloc(&xbar, h->nEL)) || (rc = h->dalloc(&rsw, h->nEL)) || (rc = h->dalloc(&rbar, h->nEL)) ||
+            (rc = h->dalloc(&ybar, h->m)) || (rc = h->dalloc(&z1, h->m)) ||
+            (rc = h->dalloc(&tpart, (size_t)P.row_chunks)) || (rc = h->dalloc(&pobj, (size_t)P.col_chunks)) ||
+            (rc = h->dalloc(&conv, (size_t)h->ninst)) || (rc = h->dalloc(&ctrl, 1)))
+            return rc;
+        CK(cudaMemset(conv, 0xff, sizeof(int) * h->ninst));        // -1: no problem stopped
+        CK(cudaMemset(ctrl, 0, sizeof(cadmm::Ctrl)));             // done = 0 for good
+        A.AP.r = xbar;
+        A.AP.rsw = rsw;
+        A.AP.x = rbar;
+        A.AP.y = ybar;
+        A.AP.z1 = z1;
+        A.AP.tpart = tpart;
+        A.AP.part_obj = pobj;
+        A.AP.inst_conv = conv;
+        A.AP.ctrl = ctrl;
+        A.n_large = 0;
+        for (int s : h->blk_size_h) A.n_large += (s + (s & 1)) > 16;
+    }
+    if (need_ckpt > A.cap_ckpt || need_seg > A.cap_seg) {
+        for (void* a : A.seg_allocs) cudaFree(a);
+        A.seg_allocs.clear();
+        A.ckpt = A.Wseg = A.Vseg = nullptr;
+        A.cap_ckpt = A.cap_seg = 0;
+        void* p1 = nullptr;
+        void* p2 = nullptr;
+        CK(cudaMalloc(&p1, need_ckpt * sizeof(double)));
+        A.seg_allocs.push_back(p1);
+        CK(cudaMalloc(&p2, need_seg * sizeof(double)));
+        A.seg_allocs.push_back(p2);
+        A.ckpt = static_cast<double*>(p1);
+        A.Wseg = static_cast<double*>(p2);
+        A.Vseg = A.Wseg + (size_t)K * SL;
+        A.cap_ckpt = need_ckpt;
+        A.cap_seg = need_seg;
+    }
+    A.Vseg = A.Wseg + (size_t)K * SL;
+    A.T = T;
+    A.K = K;
+    A.nseg = nseg;
+    return SDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdp_unrolled_forward(sdp_handle h, int T, int ckpt_every, double* x_out, void* cuda_stream) {
+    if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
+    if (T < 1 || ckpt_every < 1) return set_err(SDP_ERR_ARG, "T and ckpt_every must be >= 1");
+    if (h->opts.form != SDP_PRIMAL || h->opts.prec != SDP_PROJ_FP64)
+        return set_err(SDP_ERR_ARG, "unrolled differentiation needs form SDP_PRIMAL and prec SDP_PROJ_FP64");
+    if (h->smax > 32) return set_err(SDP_ERR_UNSUPPORTED, "unrolled differentiation takes cliques of order <= 32");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = as_stream(cuda_stream);
+    try {
+        int rc = ensure_adjoint(h, T, ckpt_every);
+        if (rc) return rc;
+        auto& A = h->adj;
+        A.valid = false;
+        if ((rc = admm_reset(h, st))) return rc;
+        const double tol = h->opts.tol;
+        h->opts.tol = 0.0;                       // run exactly T iterations
+        const size_t SL = h->SL;
+        for (int seg = 0; seg < A.nseg && rc == SDP_OK; ++seg) {
+            const int t0 = seg * A.K, n = std::min(A.K, T - t0);
+            double* ck = A.ckpt + (size_t)seg * 2 * SL;
+            cudaError_t e = cudaMemcpyAsync(ck, h->P.xk[t0 & 1], sizeof(double) * SL, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ck + SL, h->P.lam, sizeof(double) * SL, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) {
+                h->opts.tol = tol;
+                return set_err(SDP_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
+            }
+            admm_result res{};
+            rc = run_iterations(h, n, st, &res);
+            if (rc == SDP_MAX_ITER) rc = SDP_OK;
+        }
+        h->opts.tol = tol;
+        if (rc) return rc;
+        if (x_out) CK(cudaMemcpyAsync(x_out, h->P.x, sizeof(double) * h->nEL, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        A.valid = true;
+        return SDP_OK;
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_unrolled_forward");
+    }
+}
+
+int sdp_unrolled_backward(sdp_handle h, const double* xbar, double* cbar, double* bbar, void* cuda_stream) {
+    if (!h || !xbar || !cbar || !bbar) return set_err(SDP_ERR_ARG, "NULL argument");
+    auto& A = h->adj;
+    if (!A.valid) return set_err(SDP_ERR_ARG, "no sdp_unrolled_forward to differentiate (or data changed since)");
+    if (h->opts.form != SDP_PRIMAL || h->opts.prec != SDP_PROJ_FP64)
+        return set_err(SDP_ERR_ARG, "options changed since sdp_unrolled_forward");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = as_stream(cuda_stream);
+    const cadmm::IterPtrs& P = h->P;
+    const double rho = h->opts.rho, rinv = 1.0 / rho;
+    const size_t SL = h->SL, VS = (size_t)h->vstore_elems;
+    CK(cudaMemsetAsync(A.Xb, 0, sizeof(double) * std::max<size_t>(1, SL), st));
+    CK(cudaMemsetAsync(A.Lb, 0, sizeof(double) * std::max<size_t>(1, SL), st));
+    CK(cudaMemsetAsync(A.cbar, 0, sizeof(double) * h->nEL, st));
+    CK(cudaMemsetAsync(A.bbar, 0, sizeof(double) * h->m, st));
+    for (int seg = A.nseg - 1; seg >= 0; --seg) {
+        const int t0 = seg * A.K, n = std::min(A.K, A.T - t0);
+        // recompute the segment from its checkpoint, keeping W_k and the eigenvectors of each step
+        const double* ck = A.ckpt + (size_t)seg * 2 * SL;
+        CK(cadmm::launch_ctrl_set_iter(P.ctrl, t0, st));
+        CK(cadmm::launch_ctrl_arm(P.ctrl, n, 0.0, st));
+        CK(cudaMemcpyAsync(P.xk[t0 & 1], ck, sizeof(double) * SL, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(P.lam, ck + SL, sizeof(double) * SL, cudaMemcpyDeviceToDevice, st));
+        CK(cadmm::launch_vstore_identity(P, SDP_PROJ_FP64, st));
+        CK(cadmm::launch_inst_reset(P, st));
+        CK(cadmm::launch_primal_rebuild_r(P, rho, st));
+        for (int j = 0; j < n; ++j) {
+            CK(cadmm::launch_copy(P.lam, A.lam_prev, (long long)SL, st));
+            CK(cadmm::launch_iteration(P, h->plan[SDP_PROJ_FP64], SDP_PRIMAL, SDP_PROJ_FP64, rho, st));
+            CK(cadmm::launch_form_w(P, A.lam_prev, rinv, A.Wseg + (size_t)j * SL, st));
+            CK(cadmm::launch_copy(static_cast<const double*>(P.vstore), A.Vseg + (size_t)j * VS, (long long)VS, st));
+        }
+        // reverse through the segment
+        for (int j = n - 1; j >= 0; --j) {
+            const int t = t0 + j + 1;
+            CK(cadmm::launch_dk_vjp(P, A.n_large, A.Wseg + (size_t)j * SL, A.Vseg + (size_t)j * VS, A.Xb, A.Lb,
+                                    A.ub, rho, st));
+            CK(cadmm::launch_adj_scatter(P, A.ub, t == A.T ? xbar : nullptr, A.AP.r, A.AP.rsw, st));
+            CK(cadmm::launch_kkt_adjoint(A.AP, st));
+            CK(cadmm::launch_adj_accum(P, A.AP.x, A.AP.y, A.cbar, A.bbar, A.Xb, A.Lb, rinv, st));
+        }
+    }
+    CK(cadmm::launch_adj_finish(P, A.cbar, A.bbar, cbar, bbar, st));
+    CK(cudaStreamSynchronize(st));
     return SDP_OK;
 }
 

@@ -411,7 +411,8 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
 }
 
 // ---------------------------------------------------------------- z = L^-1 (t - rhs2)
-// rhs2 = b (primal) or -rho^-1 b (dual). One warp per row of L^-1.
+// rhs2 = b (primal), -rho^-1 b (dual) or 0 (kKktZeroRhs: the adjoint solve). One warp per row of
+// L^-1.
 __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double rinv, int form) {
     extern __shared__ double u[];
     pdl_wait();
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
         double t = 0.0;
         for (int c = P.row_chunk[r0 + i]; c < P.row_chunk[r0 + i + 1]; ++c) t += P.tpart[c];
         const double bi = P.b[r0 + i];
-        const double rhs2 = form == SDP_PRIMAL ? bi : -__dmul_rn(rinv, bi);
+        const double rhs2 = form == SDP_PRIMAL ? bi : (form == SDP_DUAL ? -__dmul_rn(rinv, bi) : 0.0);
         u[i] = t - rhs2;
     }
     __syncthreads();
@@ -733,6 +734,18 @@ const char* phase_name(int form, bool batch, int i) {
     if (i < 0 || i >= n) return nullptr;
     if (form == SDP_PRIMAL) return batch ? primal_b[i] : primal[i];
     return batch ? dual_b[i] : dual[i];
+}
+
+cudaError_t launch_kkt_adjoint(const IterPtrs& P, cudaStream_t st) {
+    Marks mk{nullptr, st, 0};
+    return launch_affine(P, kKktZeroRhs, 1.0, 1.0, st, mk);
+}
+
+__global__ void k_ctrl_set_iter(Ctrl* C, int it) { C->iter = it; }
+
+cudaError_t launch_ctrl_set_iter(Ctrl* ctrl, int it, cudaStream_t st) {
+    k_ctrl_set_iter<<<1, 1, 0, st>>>(ctrl, it);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_inst_reset(const IterPtrs& P, cudaStream_t st) {

@@ -226,6 +226,24 @@ cudaError_t launch_ctrl_reset(Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_ctrl_clear(Ctrl* ctrl, cudaStream_t st);
 int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form);
 cudaError_t launch_inst_reset(const IterPtrs& P, cudaStream_t st);   // every problem active again
+// The block-elimination solve alone with right-hand side [r; 0] (r in P.r, r w/D in P.rsw):
+// y = (A D^-1 A^T)^-1 A D^-1 r into P.y and x = D^-1 (r - A^T y) into P.x (form kKktZeroRhs).
+constexpr int kKktZeroRhs = 2;
+cudaError_t launch_kkt_adjoint(const IterPtrs& P, cudaStream_t st);
+cudaError_t launch_ctrl_set_iter(Ctrl* ctrl, int it, cudaStream_t st);
+
+// Reverse mode of unrolled primal iterations (adjoint.cu).
+cudaError_t adjoint_prepare();
+cudaError_t launch_form_w(const IterPtrs& P, const double* lam_prev, double rinv, double* W, cudaStream_t st);
+cudaError_t launch_dk_vjp(const IterPtrs& P, int n_large, const double* W, const double* V, double* Xb,
+                          double* Lb, double* ub, double rho, cudaStream_t st);
+cudaError_t launch_adj_scatter(const IterPtrs& P, const double* ub, const double* xbar_T, double* xbar,
+                               double* rsw, cudaStream_t st);
+cudaError_t launch_adj_accum(const IterPtrs& P, const double* rbar, const double* ybar, double* cbar,
+                             double* bbar, double* Xb, double* Lb, double rinv, cudaStream_t st);
+cudaError_t launch_adj_finish(const IterPtrs& P, const double* cbar, const double* bbar, double* cout,
+                              double* bout, cudaStream_t st);
+cudaError_t launch_copy(const double* src, double* dst, long long n, cudaStream_t st);
 int record_error(int code, const std::string& msg);   // sets the message sdp_last_error() returns
 cudaError_t iteration_prepare();  // raises the dynamic shared-memory limit of the m-sized kernels
 
