@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="for profilers: set up, run this many iterations from a reset, exit (no JSON)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-iters", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -359,6 +361,13 @@ def run_ours(args):
             launches += res["kernel_launches"] + (4 if batch else 2)   # + resets and the r rebuild
         return iters, ms, launches, res
 
+    if args.profile_iters > 0:
+        # a short, fixed sequence of launches for a profiler: reset, then K iterations
+        solver.reset(stream)
+        solver.iterate(args.profile_iters, stream)
+        torch.cuda.synchronize()
+        solver.close()
+        return
     tuned = None
     if batch:
         # projection kernel variant per clique order, tuned on this handle's own iterations

@@ -255,6 +255,7 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 struct Schedules {
     std::vector<cadmm::Sched> row, tri, col, pos, ent, heavy;
     std::vector<int> row_chunk, inst_col_chunk, inst_pos_cta, inst_ent_cta, inst_heavy_cta;
+    bool col_split = false;
 };
 
 constexpr int kChunksPerSm = 64;      // warp chunks per SM for the passes over A (8 CTAs of 8 warps)
@@ -281,10 +282,16 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
         for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1]; r += 8)
             S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
     // A^T: chunks of whole slices with about nnz / nchunk stored elements (at least 256); one warp
-    // per chunk, one lane per column.
+    // per chunk, one lane per column. With fewer than 16 slices per SM in all, every slice gets a
+    // CTA of its own instead, whose warps split the slice's length.
     const long long ct = std::max<long long>(256, (hp.nnz + nchunk - 1) / nchunk);
+    S.col_split = hp.inst_sl[Q] < 16LL * num_sms;
     S.inst_col_chunk.assign(Q + 1, 0);
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < Q && S.col_split; ++q) {
+        for (int sl = hp.inst_sl[q]; sl < hp.inst_sl[q + 1]; ++sl) S.col.push_back({q, sl, sl + 1, 0});
+        S.inst_col_chunk[q + 1] = (int)S.col.size();
+    }
+    for (int q = 0; q < Q && !S.col_split; ++q) {
         int sl = hp.inst_sl[q];
         const int s1 = hp.inst_sl[q + 1];
         while (sl < s1) {
@@ -425,6 +432,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     P.row_chunks = (int)S.row.size();
     P.tri_ctas = (int)S.tri.size();
     P.col_chunks = (int)S.col.size();
+    P.col_split = S.col_split ? 1 : 0;
     P.pos_ctas = (int)S.pos.size();
     P.ent_ctas = (int)S.ent.size();
     P.heavy_ctas = (int)S.heavy.size();
@@ -778,7 +786,7 @@ int project_variant_count(void) { return cadmm::PV_COUNT; }
 
 const char* project_variant_name(int v) {
     static const char* names[cadmm::PV_COUNT] = {"os32", "os64", "ts16", "ts32", "ts64", "ts96",
-                                                 "ow8", "ow16", "ow32"};
+                                                 "ow8", "ow16", "ow32", "ow64"};
     return (v >= 0 && v < cadmm::PV_COUNT) ? names[v] : nullptr;
 }
 

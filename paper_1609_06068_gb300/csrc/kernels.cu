@@ -514,6 +514,50 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
     if (lane == 0) P.part_obj[ch] = obj;
 }
 
+// The same product for problems with few slices: one CTA per slice, its 8 warps splitting the
+// slice's length and their partial sums added in warp order by warp 0.
+__global__ void __launch_bounds__(kColThreads) k_spmv_cols_split(IterPtrs P) {
+    constexpr int NW = kColThreads / 32;
+    __shared__ double part[NW][32];
+    pdl_wait();
+    if (P.ctrl->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Sched sc = P.col_sched[blockIdx.x];
+    if (stopped(P, sc.q)) return;
+    const int sl = sc.lo, len = P.sell_len[sl];
+    const int k0 = (int)((long long)len * w / NW), k1 = (int)((long long)len * (w + 1) / NW);
+    const double* __restrict__ y = P.y + P.inst_row[sc.q];
+    const double* __restrict__ val = P.sell_val + P.sell_off[sl] + lane;
+    const unsigned short* __restrict__ row = P.sell_row + P.sell_off[sl] + lane;
+    double s0 = 0.0, s1 = 0.0;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+        const double v0 = val[32 * k], v1 = val[32 * (k + 1)], v2 = val[32 * (k + 2)], v3 = val[32 * (k + 3)];
+        const int r0 = row[32 * k], r1 = row[32 * (k + 1)], r2 = row[32 * (k + 2)], r3 = row[32 * (k + 3)];
+        s0 = fma(v0, __ldg(y + r0), s0);
+        s1 = fma(v1, __ldg(y + r1), s1);
+        s0 = fma(v2, __ldg(y + r2), s0);
+        s1 = fma(v3, __ldg(y + r3), s1);
+    }
+    for (; k < k1; ++k) s0 = fma(val[32 * k], __ldg(y + row[32 * k]), s0);
+    part[w][lane] = s0 + s1;
+    __syncthreads();
+    if (w != 0) return;
+    double s = part[0][lane];
+#pragma unroll
+    for (int ww = 1; ww < NW; ++ww) s += part[ww][lane];
+    const int e = P.sell_col[32 * sl + lane];
+    double obj = 0.0;
+    if (e >= 0) {
+        const double xe = (P.r[e] - s) * P.dinv[e];
+        P.x[e] = xe;
+        obj = (double)P.ew[e] * P.c[e] * xe;
+    }
+    pdl_trigger();
+    obj = warp_sum(obj);
+    if (lane == 0) P.part_obj[blockIdx.x] = obj;
+}
+
 // ---------------------------------------------------------------- dual-form multiplier update
 // v_k = z_k + rho^-1 lambda_k + H_k x (Eq. vkEqn), lambda_k = -rho H_k x (Eq. DualMultUpdate with
 // the sign Eq. MultUpdateDualSDP implies), and the residual sums; the last CTA finalizes.
@@ -662,9 +706,11 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
     mk.mark();
     if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
     mk.mark();
-    if ((e = launch_pdl(k_spmv_cols, dim3(cdiv(P.col_chunks, kColThreads / 32)), dim3(kColThreads), 0, st, P)) !=
-        cudaSuccess)
-        return e;
+    if (P.col_split)
+        e = launch_pdl(k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
+    else
+        e = launch_pdl(k_spmv_cols, dim3(cdiv(P.col_chunks, kColThreads / 32)), dim3(kColThreads), 0, st, P);
+    if (e != cudaSuccess) return e;
     if (form == SDP_DUAL) {
         mk.mark();
         return launch_pdl(k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);

@@ -1041,6 +1041,206 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
     if (act && a.part != nullptr && c == 0) a.part[blk * 4 + 3] = (double)sweeps;
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32, padded order 32 < N <= 64: the same method as k_project_ow with one column per lane, but a
+// block spans two warps (64 lanes), so the partner column crosses warps: every round each lane
+// stores its column in the block's shared tile, the two warps meet at a named barrier, and each
+// lane reads its partner's column from the tile (twice, for the Gram entry and for the update,
+// which keeps register use near 64 floats). Two blocks per CTA of four warps.
+constexpr int kOW64LD = 65;
+constexpr size_t kOW64BlockFloats = 2 * 64 * kOW64LD + 2 * 64;   // tile, V (warm start), alpha, scratch
+constexpr size_t kOW64Bytes = 2 * kOW64BlockFloats * sizeof(float);
+
+__device__ __forceinline__ void pair_sync(int pair) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + pair), "r"(64) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
+    constexpr int LD = kOW64LD;
+    extern __shared__ __align__(16) unsigned char smem_ow64[];
+    pdl_wait();
+    if (a.ctrl != nullptr && a.ctrl->done) return;
+    const int pair = threadIdx.x >> 6, c = threadIdx.x & 63;
+    const int idx = blockIdx.x * 2 + pair;
+    float* Ts = reinterpret_cast<float*>(smem_ow64) + (size_t)pair * kOW64BlockFloats;   // 64 x LD
+    float* Vs = Ts + 64 * LD;                                                           // 64 x LD
+    float* als = Vs + 64 * LD;                                                          // 64
+    float* red = als + 64;                                                              // 64
+    if (idx >= a.count) return;                     // both warps of the pair leave together
+    const int blk = a.order ? a.order[idx] : idx;
+    const int s = a.size[blk];
+    const long long off = a.off[blk];
+    if (block_stopped<MODE>(a, blk, s, off, c, 64)) return;
+    const int N = s + (s & 1);
+    const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
+    float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+
+    // ---- W scaled by 2^-e2 (exact) into the tile, both triangles, zero padding
+    double wmax = 0.0;
+    if (c < s)
+        for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
+    red[c] = (float)0;
+    double wm = wmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    double* redd = reinterpret_cast<double*>(Vs);     // Vs is free until the warm start fills it
+    if ((c & 31) == 0) redd[c >> 5] = wm;
+    for (int r = 0; r < 64; ++r) Ts[r * LD + c] = 0.f;
+    pair_sync(pair);
+    wmax = fmax(redd[0], redd[1]);
+    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
+    pair_sync(pair);
+    if (c < s)
+        for (int r = c; r < s; ++r) {
+            const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
+            Ts[r * LD + c] = wt;
+            Ts[c * LD + r] = wt;
+        }
+    if (warm)
+        for (int r = 0; r < 64; ++r) Vs[r * LD + c] = (r < N && c < N) ? vglob[r * N + c] : (r == c ? 1.f : 0.f);
+    pair_sync(pair);
+
+    // ---- sigma = 2 ||W||_F and G = B (cold) or B V_prev (warm), column c in registers
+    float sq = 0.f;
+    for (int r = 0; r < 64; ++r) sq = fmaf(Ts[r * LD + c], Ts[r * LD + c], sq);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((c & 31) == 0) red[c >> 5] = sq;
+    pair_sync(pair);
+    const float sigma = 2.f * sqrtf(red[0] + red[1]);
+    float g[64];
+    if (warm) {
+#pragma unroll
+        for (int r = 0; r < 64; ++r) g[r] = sigma * Vs[r * LD + c];
+        for (int m = 0; m < 64; ++m) {
+            const float vm = Vs[m * LD + c];
+#pragma unroll
+            for (int r = 0; r < 64; ++r) g[r] = fmaf(Ts[r * LD + m], vm, g[r]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 64; ++r) g[r] = Ts[r * LD + c] + ((r == c && c < N) ? sigma : 0.f);
+    }
+    if (c >= N) {
+#pragma unroll
+        for (int r = 0; r < 64; ++r) g[r] = 0.f;
+    }
+
+    // ---- sweeps: columns meet through the tile
+    int sweeps = 0;
+    for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
+        float alpha = 0.f;
+#pragma unroll
+        for (int r = 0; r < 64; ++r) alpha = fmaf(g[r], g[r], alpha);
+        float worst = 0.f;
+        for (int rd = 0; rd < N - 1; ++rd) {
+            const int p = c < N ? rr_partner(c, rd, N) : c;
+            pair_sync(pair);                                  // the previous round's reads are done
+#pragma unroll
+            for (int r = 0; r < 64; ++r) Ts[c * LD + r] = g[r];
+            als[c] = alpha;
+            pair_sync(pair);
+            const float* gp = Ts + p * LD;
+            float gam = 0.f;
+#pragma unroll
+            for (int r = 0; r < 64; ++r) gam = fmaf(g[r], gp[r], gam);
+            const float beta = als[p];
+            if (p != c && fabsf(gam) > 1.0e-30f) {
+                const bool first = c < p;
+                const float ai = first ? alpha : beta, aj = first ? beta : alpha;
+                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
+                const float zeta = __fdividef(aj - ai, 2.f * gam);
+                const float az = fabsf(zeta);
+                float den;
+                if (az > 1.0e15f) {
+                    den = 2.f * az;
+                } else {
+                    const float x = fmaf(zeta, zeta, 1.f);
+                    den = az + x * rsqrtf(x);
+                }
+                const float t = copysignf(__fdividef(1.f, den), zeta);
+                const float cc = __frsqrt_rn(fmaf(t, t, 1.f));
+                const float sn = t * cc;
+                const float sg = first ? -sn : sn;
+#pragma unroll
+                for (int r = 0; r < 64; ++r) g[r] = fmaf(sg, gp[r], cc * g[r]);
+                alpha = first ? ai - t * gam : aj + t * gam;
+            }
+        }
+        ++sweeps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+        pair_sync(pair);
+        if ((c & 31) == 0) red[c >> 5] = worst;
+        pair_sync(pair);
+        if (fmaxf(red[0], red[1]) < kOneSidedStop * kOneSidedStop) break;
+    }
+
+    // ---- lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into the tile
+    float mu2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 64; ++r) mu2 = fmaf(g[r], g[r], mu2);
+    const float mu = sqrtf(mu2);
+    const float inv = mu > 0.f ? 1.f / mu : 0.f;
+    const float lam = mu - sigma;
+    const float qs = (c < N && lam > 0.f) ? sqrtf(lam) * inv : 0.f;
+    if (vglob != nullptr && c < N)
+        for (int r = 0; r < N; ++r) vglob[r * N + c] = mu > 0.f ? g[r] * inv : (r == c ? 1.f : 0.f);
+    pair_sync(pair);
+#pragma unroll
+    for (int r = 0; r < 64; ++r) Ts[r * LD + c] = g[r] * qs;
+    pair_sync(pair);
+
+    // ---- rebuild the lower triangle of Q Q^T and apply the epilogue
+    pdl_trigger();
+    double pv[3] = {0.0, 0.0, 0.0};
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
+    for (int cb = 0; cb < s; ++cb) {
+        const float* Qb = Ts + cb * LD;
+        for (int ra = cb + c; ra < s; ra += 64) {
+            const float* Qa = Ts + ra * LD;
+            float acc = 0.f;
+            for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
+            const double xv = (double)acc * up;
+            const int pos = packed_pos(ra, cb, s);
+            if (MODE == PROJ_PRIMAL) {
+                const double u = a.x[a.gather_idx[off + pos]];
+                const double l = a.lam[off + pos];
+                const double d = xv - u;
+                xk_new[off + pos] = xv;
+                a.lam[off + pos] = l + a.rho * d;                  // Eq. LambdakUpdate
+                const double wgt = (ra == cb) ? 1.0 : 2.0;
+                pv[0] += wgt * d * d;
+                pv[1] += wgt * xv * xv;
+                pv[2] += wgt * u * u;
+            } else {
+                a.out[off + pos] = xv;
+            }
+        }
+    }
+    if (MODE == PROJ_PRIMAL) {
+        double* rd = reinterpret_cast<double*>(Vs);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pv[k] += __shfl_xor_sync(0xffffffffu, pv[k], o);
+        }
+        pair_sync(pair);
+        if ((c & 31) == 0)
+            for (int k = 0; k < 3; ++k) rd[(c >> 5) * 3 + k] = pv[k];
+        pair_sync(pair);
+        if (c == 0) {
+            a.part[blk * 4 + 0] = rd[0] + rd[3];
+            a.part[blk * 4 + 1] = rd[1] + rd[4];
+            a.part[blk * 4 + 2] = rd[2] + rd[5];
+        }
+    }
+    if (a.part != nullptr && c == 0) a.part[blk * 4 + 3] = (double)sweeps;
+}
+
 template <typename T, int MODE, class SH>
 cudaError_t prepare_one() {
     const size_t smem = project_smem_bytes(SDP_MAX_CLIQUE, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
@@ -1068,6 +1268,9 @@ cudaError_t prepare_mode() {
         if ((e = prepare_ow<MODE, 8>()) != cudaSuccess) return e;
         if ((e = prepare_ow<MODE, 16>()) != cudaSuccess) return e;
         if ((e = prepare_ow<MODE, 32>()) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_project_ow64<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kOW64Bytes)) != cudaSuccess)
+            return e;
     }
     if ((e = prepare_one<T, MODE, ShapeS16>()) != cudaSuccess) return e;
     if ((e = prepare_one<T, MODE, ShapeS32>()) != cudaSuccess) return e;
@@ -1090,6 +1293,8 @@ cudaError_t launch_mode(const ProjArgs& a, int variant, int smax, cudaStream_t s
         case PV_OW16:
             return launch_pdl(k_project_ow<MODE, 16>, dim3((a.count + OWLayout<16>::BPC - 1) / OWLayout<16>::BPC),
                               dim3(128), OWLayout<16>::kBytes, st, a, rinv);
+        case PV_OW64:
+            return launch_pdl(k_project_ow64<MODE>, dim3((a.count + 1) / 2), dim3(128), kOW64Bytes, st, a, rinv);
         case PV_OW32:
             return launch_pdl(k_project_ow<MODE, 32>, dim3((a.count + OWLayout<32>::BPC - 1) / OWLayout<32>::BPC),
                               dim3(128), OWLayout<32>::kBytes, st, a, rinv);
@@ -1141,7 +1346,7 @@ int project_default_variant(int s, int prec) {
     if (prec == SDP_PROJ_FP32 && N <= 8) return PV_OW8;
     if (prec == SDP_PROJ_FP32 && N <= 16) return PV_OW16;
     if (prec == SDP_PROJ_FP32 && N <= 32) return PV_OW32;
-    if (prec == SDP_PROJ_FP32 && N <= 64) return PV_OS2;
+    if (prec == SDP_PROJ_FP32 && N <= 64) return PV_OW64;
     if (N <= 16) return PV_TS16;
     if (N <= 32) return PV_TS32;
     if (N <= 64) return PV_TS64;
@@ -1155,6 +1360,7 @@ bool project_variant_valid(int variant, int s, int prec) {
         case PV_OW8: return prec == SDP_PROJ_FP32 && N <= 8;
         case PV_OW16: return prec == SDP_PROJ_FP32 && N <= 16;
         case PV_OW32: return prec == SDP_PROJ_FP32 && N <= 32;
+        case PV_OW64: return prec == SDP_PROJ_FP32 && N <= 64;
         case PV_OS2: return prec == SDP_PROJ_FP32 && N <= 64;
         case PV_TS16: return N <= 16;
         case PV_TS32: return N <= 32;
@@ -1169,7 +1375,7 @@ ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& s
     // A warp segment per block pays off when there are enough blocks to fill the GPU with warps;
     // with fewer, a CTA per block finishes each block sooner.
     long long small = 0;
-    for (int k : order) small += (size[k] + (size[k] & 1)) <= 32;
+    for (int k : order) small += (size[k] + (size[k] & 1)) <= 64;
     const bool use_ow = small >= ow_min_blocks;
     ProjPlan pl{};
     pl.runs = 0;
@@ -1178,6 +1384,7 @@ ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& s
         const int N = s + (s & 1);
         int v = project_default_variant(s, prec);
         if (!use_ow && (v == PV_OW8 || v == PV_OW16 || v == PV_OW32)) v = PV_OS1;
+        if (!use_ow && v == PV_OW64) v = PV_OS2;
         if (table != nullptr && project_variant_valid(table[N], s, prec)) v = table[N];
         if (pl.runs > 0 && pl.variant[pl.runs - 1] == v) {
             ++pl.count[pl.runs - 1];

@@ -115,7 +115,8 @@ struct Sched {
 
 // Projection launches: the cliques in processing order (largest first) split into runs that use
 // the same kernel variant. A run [start, start + count) of `order` goes to one launch.
-enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_OW8, PV_OW16, PV_OW32, PV_COUNT };
+enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_OW8, PV_OW16, PV_OW32, PV_OW64,
+                   PV_COUNT };
 constexpr int kMaxProjRuns = 64;
 struct ProjPlan {
     int runs;
@@ -136,6 +137,7 @@ struct IterPtrs {
     const Sched* row_sched; int row_chunks; const int* row_chunk;  // CSR chunks; row_chunk[m+1]
     const Sched* tri_sched; int tri_ctas;                          // <= 8 rows of L^-1 per CTA
     const Sched* col_sched; int col_chunks;                        // slice ranges of A^T
+    int col_split;                                                 // 1: one slice per CTA, warps split it
     const Sched* pos_sched; int pos_ctas;                          // packed positions
     const Sched* ent_sched; int ent_ctas;                          // light entries, one per thread
     const Sched* heavy_sched; int heavy_ctas;                      // heavy-list ranges, one per warp
