@@ -145,7 +145,7 @@ __global__ void k_adj_scatter(IterPtrs P, const double* __restrict__ ub, const d
         const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
         double acc = 0.0;
         for (int j = j0; j < j1; ++j) acc = (j == j0) ? ub[P.sc_pos[j]] : acc + ub[P.sc_pos[j]];
-        if (xbar_T != nullptr) acc += xbar_T[e] / (double)P.ew[e];
+        if (xbar_T != nullptr) acc += xbar_T[e] * (P.ew[e] == 1 ? 1.0 : 0.5);
         xbar[e] = acc;
         rsw[e] = acc * P.wdinv[e];
     }
@@ -169,7 +169,7 @@ __global__ void k_adj_accum(IterPtrs P, const double* __restrict__ rbar, const d
 __global__ void k_adj_finish(IterPtrs P, const double* __restrict__ cbar, const double* __restrict__ bbar,
                              double* __restrict__ cout, double* __restrict__ bout) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    for (int e = tid; e < P.nEL; e += nt) cout[e] = (double)P.ew[e] * cbar[e];
+    for (int e = tid; e < P.nEL; e += nt) cout[e] = (P.ew[e] == 1 ? 1.0 : 2.0) * cbar[e];
     for (int i = tid; i < P.m; i += nt) bout[i] = bbar[i];
 }
 

@@ -258,12 +258,17 @@ struct Schedules {
     bool col_split = false;
 };
 
-constexpr int kChunksPerSm = 64;      // warp chunks per SM for the passes over A (8 CTAs of 8 warps)
 
 Schedules build_schedules(const HostProblem& hp, int num_sms) {
     Schedules S;
     const int Q = hp.ninst;
-    const long long nchunk = (long long)kChunksPerSm * num_sms;
+    int mmax = 1;
+    for (int q = 0; q < Q; ++q) mmax = std::max(mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
+    // grids of whole waves: the CTAs each kernel can keep resident on an SM
+    const long long rows_res = cadmm::resident_ctas(0, 0);
+    const long long cols_res = cadmm::resident_ctas(1, (size_t)mmax * sizeof(double));
+    const long long upd_res = cadmm::resident_ctas(2, 0);
+    const long long nchunk = 8LL * rows_res * num_sms;
     // CSR: each row split into chunks of about nnz / nchunk nonzeros (at least 1024, at most 256
     // chunks per row); one warp per chunk.
     const long long rt = std::max<long long>(1024, (hp.nnz + nchunk - 1) / nchunk);
@@ -281,10 +286,10 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
     for (int q = 0; q < Q; ++q)
         for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1]; r += 8)
             S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
-    // A^T: chunks of whole slices with about nnz / nchunk stored elements (at least 256); one warp
-    // per chunk, one lane per column. With fewer than 16 slices per SM in all, every slice gets a
-    // CTA of its own instead, whose warps split the slice's length.
-    const long long ct = std::max<long long>(256, (hp.nnz + nchunk - 1) / nchunk);
+    // A^T: CTA chunks of whole slices with about nnz / (8 SMs) stored elements (at least 2048);
+    // the warps of a CTA take its slices in turn, one lane per column. With fewer than 16 slices
+    // per SM in all, every slice gets a CTA of its own instead, whose warps split the slice's length.
+    const long long ct = std::max<long long>(2048, (hp.nnz + cols_res * num_sms - 1) / (cols_res * num_sms));
     S.col_split = hp.inst_sl[Q] < 16LL * num_sms;
     S.inst_col_chunk.assign(Q + 1, 0);
     for (int q = 0; q < Q && S.col_split; ++q) {
@@ -306,10 +311,10 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
         S.inst_col_chunk[q + 1] = (int)S.col.size();
     }
     // Light entries: 256 per CTA; heavy entries: 8 (one per warp) per CTA.
-    // Packed positions per CTA of the dual update: enough CTAs for 8 per SM, 256..2048 (1..8 per
-    // thread) each.
+    // Packed positions per CTA of the dual update: about one wave of resident CTAs, 256..2048
+    // (1..8 per thread) each.
     const int pos_per = (int)std::max<long long>(
-        256, std::min<long long>(2048, ((long long)hp.SL / (8LL * num_sms) + 255) / 256 * 256));
+        256, std::min<long long>(2048, ((long long)hp.SL / (upd_res * num_sms) + 255) / 256 * 256));
     S.inst_pos_cta.assign(Q + 1, 0);
     S.inst_ent_cta.assign(Q + 1, 0);
     S.inst_heavy_cta.assign(Q + 1, 0);

@@ -25,6 +25,10 @@ constexpr int kRowThreads = 256;  // CSR row chunks
 constexpr int kTriThreads = 256;  // triangular products (8 warps, one row per warp)
 constexpr int kColThreads = 256;  // CSC columns
 
+// Weight 1 (diagonal) or 2 (off-diagonal) as a double, by selection: an integer-to-double
+// conversion would run on GB300's narrow FP64 pipe, which already limits these kernels.
+__device__ __forceinline__ double wt(unsigned char w) { return w == 1 ? 1.0 : 2.0; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -247,9 +251,11 @@ __device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int
 // r = sum_k H_k^T(x_k + rho^-1 lambda_k) - rho^-1 c, summed in ascending k from the first term;
 // also the dual-residual pieces ||sum_k H_k^T(x_k+ - x_k)||^2 and ||sum_k H_k^T lambda_k||^2.
 // use_current = 1 rebuilds r from the current blocks (after a reset or a state upload) and skips
-// the residual work. CTAs [0, ent_ctas) take one entry per thread (heavily shared entries are left
-// to the others); CTAs [ent_ctas, ent_ctas + heavy_ctas) take one heavily shared entry per warp:
-// its lanes form 32 terms at a time and every lane adds them in ascending clique order.
+// the residual work. CTAs [0, ent_ctas) take one entry per thread, adding its terms in ascending
+// clique order (heavily shared entries are left to the others); CTAs [ent_ctas, ent_ctas +
+// heavy_ctas) take one heavily shared entry per warp: lane t adds terms t, t+32, ... and the
+// lanes' sums meet in a fixed shuffle tree (deterministic; equal to the ascending sum up to
+// rounding, where a sequential sum over thousands of cliques would serialize the whole warp).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, double rho, int use_current) {
     __shared__ double red[33 * 2];
     pdl_wait();
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
                 const double re = __dsub_rn(acc, __dmul_rn(rinv, P.c[e]));
                 P.r[e] = re;
                 P.rsw[e] = re * P.wdinv[e];
-                const double w = (double)P.ew[e];
+                const double w = wt(P.ew[e]);
                 v[0] = w * dsum * dsum;
                 v[1] = w * lsum * lsum;
             }
@@ -292,30 +298,22 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
             const int e = P.heavy[hw];
             const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
             double acc = 0.0, dsum = 0.0, lsum = 0.0;
-            for (int base = j0; base < j1; base += 32) {
-                const int j = base + lane;
-                double term = 0.0, dd = 0.0, l = 0.0;
-                if (j < j1) {
-                    const int pos = P.sc_pos[j];
-                    const double xn = xn_buf[pos], xo = xo_buf[pos];
-                    l = P.lam[pos];
-                    term = __dadd_rn(xn, __dmul_rn(rinv, l));
-                    dd = xn - xo;
-                }
-                const int cnt = min(32, j1 - base);
-                for (int t = 0; t < cnt; ++t) {
-                    const double tv = __shfl_sync(0xffffffffu, term, t);
-                    const double dv = __shfl_sync(0xffffffffu, dd, t);
-                    const double lv = __shfl_sync(0xffffffffu, l, t);
-                    if (base == j0 && t == 0) { acc = tv; dsum = dv; lsum = lv; }
-                    else { acc = __dadd_rn(acc, tv); dsum += dv; lsum += lv; }
-                }
+#pragma unroll 4
+            for (int j = j0 + lane; j < j1; j += 32) {
+                const int pos = P.sc_pos[j];
+                const double xn = xn_buf[pos], xo = xo_buf[pos], l = P.lam[pos];
+                acc = __dadd_rn(acc, __dadd_rn(xn, __dmul_rn(rinv, l)));
+                dsum += xn - xo;
+                lsum += l;
             }
+            acc = warp_sum(acc);
+            dsum = warp_sum(dsum);
+            lsum = warp_sum(lsum);
             if (lane == 0) {
                 const double re = __dsub_rn(acc, __dmul_rn(rinv, P.c[e]));
                 P.r[e] = re;
                 P.rsw[e] = re * P.wdinv[e];
-                const double w = (double)P.ew[e];
+                const double w = wt(P.ew[e]);
                 v[0] = w * dsum * dsum;
                 v[1] = w * lsum * lsum;
             }
@@ -332,8 +330,9 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
 }
 
 // ---------------------------------------------------------------- scatter (dual form)
-// r = c - sum_k H_k^T(z_k + rho^-1 lambda_k), ascending k from the first term; the same split
-// between light entries (one per thread) and heavily shared ones (one per warp).
+// r = c - sum_k H_k^T(z_k + rho^-1 lambda_k), ascending k from the first term for light entries;
+// the same split between light entries (one per thread) and heavily shared ones (one per warp,
+// lane-strided partial sums and a fixed shuffle tree).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double rinv) {
     pdl_wait();
     if (P.ctrl->done) return;
@@ -363,19 +362,12 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
     const int e = P.heavy[hw];
     const int j0 = P.sc_ptr[e], j1 = P.sc_ptr[e + 1];
     double acc = 0.0;
-    for (int base = j0; base < j1; base += 32) {
-        const int j = base + lane;
-        double term = 0.0;
-        if (j < j1) {
-            const int pos = P.sc_pos[j];
-            term = __dadd_rn(z[pos], __dmul_rn(rinv, P.lam[pos]));
-        }
-        const int cnt = min(32, j1 - base);
-        for (int t = 0; t < cnt; ++t) {
-            const double tv = __shfl_sync(0xffffffffu, term, t);
-            acc = (base == j0 && t == 0) ? tv : __dadd_rn(acc, tv);
-        }
+#pragma unroll 4
+    for (int j = j0 + lane; j < j1; j += 32) {
+        const int pos = P.sc_pos[j];
+        acc = __dadd_rn(acc, __dadd_rn(z[pos], __dmul_rn(rinv, P.lam[pos])));
     }
+    acc = warp_sum(acc);
     if (lane == 0) {
         const double re = __dsub_rn(P.c[e], acc);
         P.r[e] = re;
@@ -474,21 +466,30 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
 
 // ---------------------------------------------------------------- x = (r - A^T y) / D
 // A^T in sliced ELL form (columns ordered by length within windows of 256, so slices pad
-// little): one warp per chunk of slices of one problem, one lane per column, so
-// every load of the slice is coalesced and no lane-to-lane reduction is needed. y is read through
-// the read-only cache (a problem's y is small and hot). Also the partial objective
-// sum_e w_e c_e x_e of the chunk.
+// little): one CTA per chunk of slices of one problem, its warps taking the slices in turn, one
+// lane per column, so every load of a slice is coalesced and no lane-to-lane reduction is needed.
+// The problem's y is staged in shared memory: the lanes of a warp read 32 scattered rows of it per
+// step, which shared memory serves in a few cycles where the L1 cache needs one pass per line.
+// Also the partial objective sum_e w_e c_e x_e of the chunk.
 __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
+    constexpr int NW = kColThreads / 32;
+    extern __shared__ double ys[];
+    __shared__ double red[33];
     pdl_wait();
     if (P.ctrl->done) return;
-    const int lane = threadIdx.x & 31;
-    const int ch = blockIdx.x * (kColThreads / 32) + (threadIdx.x >> 5);
-    if (ch >= P.col_chunks) return;
-    const Sched sc = P.col_sched[ch];
+    const Sched sc = P.col_sched[blockIdx.x];
     if (stopped(P, sc.q)) return;
-    const double* __restrict__ y = P.y + P.inst_row[sc.q];
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = P.y[r0 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double obj = 0.0;
-    for (int sl = sc.lo; sl < sc.hi; ++sl) {
+    // Slices in rounds of NW, warp w taking slot w of even rounds and slot NW-1-w of odd ones:
+    // within a window the slices shorten (columns are sorted by length), so the snake order
+    // pairs long slices with short ones for every warp.
+    for (int base = sc.lo; base < sc.hi; base += NW) {
+        const int sl = base + (((base - sc.lo) / NW) & 1 ? NW - 1 - w : w);
+        if (sl >= sc.hi) continue;
         const int e = P.sell_col[32 * sl + lane], len = P.sell_len[sl];
         const double* __restrict__ val = P.sell_val + P.sell_off[sl] + lane;
         const unsigned short* __restrict__ row = P.sell_row + P.sell_off[sl] + lane;
@@ -496,22 +497,23 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
         int k = 0;
         for (; k + 3 < len; k += 4) {
             const double v0 = val[32 * k], v1 = val[32 * (k + 1)], v2 = val[32 * (k + 2)], v3 = val[32 * (k + 3)];
-            const int r0 = row[32 * k], r1 = row[32 * (k + 1)], r2 = row[32 * (k + 2)], r3 = row[32 * (k + 3)];
-            s0 = fma(v0, __ldg(y + r0), s0);
-            s1 = fma(v1, __ldg(y + r1), s1);
-            s0 = fma(v2, __ldg(y + r2), s0);
-            s1 = fma(v3, __ldg(y + r3), s1);
+            const int q0 = row[32 * k], q1 = row[32 * (k + 1)], q2 = row[32 * (k + 2)], q3 = row[32 * (k + 3)];
+            s0 = fma(v0, ys[q0], s0);
+            s1 = fma(v1, ys[q1], s1);
+            s0 = fma(v2, ys[q2], s0);
+            s1 = fma(v3, ys[q3], s1);
         }
-        for (; k < len; ++k) s0 = fma(val[32 * k], __ldg(y + row[32 * k]), s0);
+        for (; k < len; ++k) s0 = fma(val[32 * k], ys[row[32 * k]], s0);
         if (e >= 0) {
             const double xe = (P.r[e] - (s0 + s1)) * P.dinv[e];
             P.x[e] = xe;
-            obj = fma((double)P.ew[e] * P.c[e], xe, obj);
+            obj = fma(wt(P.ew[e]) * P.c[e], xe, obj);
         }
     }
     pdl_trigger();
-    obj = warp_sum(obj);
-    if (lane == 0) P.part_obj[ch] = obj;
+    double v[1] = {obj};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) P.part_obj[blockIdx.x] = v[0];
 }
 
 // The same product for problems with few slices: one CTA per slice, its 8 warps splitting the
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols_split(IterPtrs P) {
     if (e >= 0) {
         const double xe = (P.r[e] - s) * P.dinv[e];
         P.x[e] = xe;
-        obj = (double)P.ew[e] * P.c[e] * xe;
+        obj = wt(P.ew[e]) * P.c[e] * xe;
     }
     pdl_trigger();
     obj = warp_sum(obj);
@@ -568,20 +570,59 @@ __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double 
     const Sched sc = P.pos_sched[blockIdx.x];
     if (stopped(P, sc.q)) return;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int pos = sc.lo + threadIdx.x; pos < sc.hi; pos += blockDim.x) {
-        const double u = P.x[P.gather_idx[pos]];
-        const double z = P.xk[0][pos], l = P.lam[pos], vo = P.vk[pos];
-        const double vn = __dadd_rn(__dadd_rn(z, __dmul_rn(rinv, l)), u);
-        const double ln = __dmul_rn(-rho, u);
-        P.vk[pos] = vn;
-        P.lam[pos] = ln;
-        const double w = (double)P.pos_w[pos];
-        const double d1 = z - vn, d2 = vn - vo;
-        v[0] = fma(w * d1, d1, v[0]);
-        v[1] = fma(w * z, z, v[1]);
-        v[2] = fma(w * vn, vn, v[2]);
-        v[3] = fma(w * d2, d2, v[3]);
-        v[4] = fma(w * ln, ln, v[4]);
+    // Four positions per step, all of their loads issued before any arithmetic (one step when a
+    // CTA has at most one position per thread).
+    constexpr int U = 4;
+    const int bd = blockDim.x;
+    if (sc.hi - sc.lo <= bd) {
+        const int pos = sc.lo + threadIdx.x;
+        if (pos < sc.hi) {
+            const double u = P.x[P.gather_idx[pos]];
+            const double z = P.xk[0][pos], l = P.lam[pos], vo = P.vk[pos];
+            const double vn = __dadd_rn(__dadd_rn(z, __dmul_rn(rinv, l)), u);
+            const double ln = __dmul_rn(-rho, u);
+            P.vk[pos] = vn;
+            P.lam[pos] = ln;
+            const double w = wt(P.pos_w[pos]);
+            const double d1 = z - vn, d2 = vn - vo;
+            v[0] = w * d1 * d1;
+            v[1] = w * z * z;
+            v[2] = w * vn * vn;
+            v[3] = w * d2 * d2;
+            v[4] = w * ln * ln;
+        }
+    }
+    for (int base = sc.lo + threadIdx.x; base < sc.hi && sc.hi - sc.lo > bd; base += U * bd) {
+        int gi[U];
+        double z[U], l[U], vo[U], u[U], w[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            const int pos = base + t * bd;
+            const bool ok = pos < sc.hi;
+            gi[t] = ok ? P.gather_idx[pos] : 0;
+            z[t] = ok ? P.xk[0][pos] : 0.0;
+            l[t] = ok ? P.lam[pos] : 0.0;
+            vo[t] = ok ? P.vk[pos] : 0.0;
+            w[t] = ok ? wt(P.pos_w[pos]) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) u[t] = P.x[gi[t]];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            const int pos = base + t * bd;
+            const double vn = __dadd_rn(__dadd_rn(z[t], __dmul_rn(rinv, l[t])), u[t]);
+            const double ln = __dmul_rn(-rho, u[t]);
+            if (pos < sc.hi) {
+                P.vk[pos] = vn;
+                P.lam[pos] = ln;
+            }
+            const double d1 = z[t] - vn, d2 = vn - vo[t];
+            v[0] = fma(w[t] * d1, d1, v[0]);
+            v[1] = fma(w[t] * z[t], z[t], v[1]);
+            v[2] = fma(w[t] * vn, vn, v[2]);
+            v[3] = fma(w[t] * d2, d2, v[3]);
+            v[4] = fma(w[t] * ln, ln, v[4]);
+        }
     }
     pdl_trigger();
     block_sum<5>(v, red);
@@ -709,7 +750,7 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
     if (P.col_split)
         e = launch_pdl(k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
     else
-        e = launch_pdl(k_spmv_cols, dim3(cdiv(P.col_chunks, kColThreads / 32)), dim3(kColThreads), 0, st, P);
+        e = launch_pdl(k_spmv_cols, dim3(P.col_chunks), dim3(kColThreads), mbytes, st, P);
     if (e != cudaSuccess) return e;
     if (form == SDP_DUAL) {
         mk.mark();
@@ -731,7 +772,8 @@ cudaError_t iteration_prepare() {
     const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,
@@ -780,6 +822,15 @@ const char* phase_name(int form, bool batch, int i) {
     if (i < 0 || i >= n) return nullptr;
     if (form == SDP_PRIMAL) return batch ? primal_b[i] : primal[i];
     return batch ? dual_b[i] : dual[i];
+}
+
+int resident_ctas(int kernel, size_t smem) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (kernel == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmv_rows, kRowThreads, smem);
+    if (kernel == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmv_cols, kColThreads, smem);
+    if (kernel == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update_dual, kEntThreads, smem);
+    return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 cudaError_t launch_kkt_adjoint(const IterPtrs& P, cudaStream_t st) {

@@ -233,6 +233,9 @@ cudaError_t launch_inst_reset(const IterPtrs& P, cudaStream_t st);   // every pr
 constexpr int kKktZeroRhs = 2;
 cudaError_t launch_kkt_adjoint(const IterPtrs& P, cudaStream_t st);
 cudaError_t launch_ctrl_set_iter(Ctrl* ctrl, int it, cudaStream_t st);
+// CTAs of one SM that can be resident at once for kernel 0 (spmv_rows), 1 (spmv_cols) or 2
+// (update_dual) with `smem` bytes of dynamic shared memory; sizes the grids to whole waves.
+int resident_ctas(int kernel, size_t smem);
 
 // Reverse mode of unrolled primal iterations (adjoint.cu).
 cudaError_t adjoint_prepare();
