@@ -476,17 +476,18 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
 // FP32, padded order N <= 32 * CPL (CPL = 1, 2): one-sided (Hestenes) Jacobi, one CTA of 4 * CPL
 // warps per clique. Larger blocks and FP64 use the two-sided kernel above.
 //
-// Lane j holds columns j, j + 32, ... (CPL of them) of G = B V and of V, with B = W + sigma I and
-// sigma = ||W||_F, so B is positive semidefinite and its eigenvalues are lambda(W) + sigma (for an
-// indefinite W, one-sided Jacobi alone would confuse eigenvalues +mu and -mu). Warp w holds rows
-// 8w .. 8w+7 of every column, in registers. A rotation of columns (i, j) makes g_i and g_j
-// orthogonal (Golub & Van Loan's 2x2 formula on the Gram entries alpha = g_i.g_i, beta = g_j.g_j,
-// gamma = g_i.g_j): the partner column's rows arrive by warp shuffles, the warps' partial gammas
-// meet in shared memory (one barrier per round), and both ends of a pair compute the same rotation
-// from the same sums. Rounds follow the round-robin schedule, so a sweep of N-1 rounds meets every
-// pair once. After a sweep whose largest |gamma| / sqrt(alpha beta) was below kOneSidedStop when
-// it began, V holds the eigenvectors and lambda_j = v_j . g_j - sigma (a Rayleigh quotient, since
-// G = B V). Warm start: the stored eigenvectors, re-orthonormalized by one Newton-Schulz step.
+// Lane j holds columns j, j + 32, ... (CPL of them) of G = B V, with B = W + sigma I and
+// sigma = 2 ||W||_F, so B is positive definite and its eigenvalues are lambda(W) + sigma >= ||W||_F
+// (for an indefinite W, one-sided Jacobi alone would confuse eigenvalues +mu and -mu). Warp w
+// holds rows 8w .. 8w+7 of every column, in registers. A rotation of columns (i, j) makes g_i and
+// g_j orthogonal (Golub & Van Loan's 2x2 formula on the Gram entries alpha = g_i.g_i,
+// beta = g_j.g_j, gamma = g_i.g_j): the partner column's rows arrive by warp shuffles, the warps'
+// partial gammas meet in shared memory (one barrier per round), and both ends of a pair compute
+// the same rotation from the same sums. Rounds follow the round-robin schedule, so a sweep of N-1
+// rounds meets every pair once. After a sweep whose largest |gamma| / sqrt(alpha beta) was below
+// kOneSidedStop when it began, the columns of G are mu_j v_j: V itself is never formed, v_j =
+// g_j / mu_j and lambda_j = mu_j - sigma with mu_j = ||g_j||. Warm start: G = B V_prev from the
+// eigenvectors kept from the last call (recomputed from G each time, so rounding does not build up).
 constexpr int kOSRows = 8;                 // rows per warp
 // Cyclic Jacobi converges quadratically: a sweep that starts with every pair within
 // kOneSidedStop of orthogonal leaves them within about its square, below FP32 resolution.
@@ -509,8 +510,8 @@ struct OSLayout {
     static constexpr int NP = 32 * CPL;          // players (columns) and rows
     static constexpr int NW = 4 * CPL;           // warps
     static constexpr int LD = NP + 1;
-    // dynamic shared memory: W, V, V^T V (floats), then the partner table (bytes)
-    static constexpr size_t kMatBytes = (size_t)3 * NP * LD * sizeof(float);
+    // dynamic shared memory: W, V (floats), then the partner table (bytes)
+    static constexpr size_t kMatBytes = (size_t)2 * NP * LD * sizeof(float);
     static constexpr size_t kBytes = kMatBytes + (size_t)NP * NP;
 };
 
@@ -521,7 +522,6 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     extern __shared__ __align__(16) unsigned char smem_os[];
     float* Ws = reinterpret_cast<float*>(smem_os);           // W, then V for the rebuild
     float* Vs = Ws + NP * LD;                                // previous eigenvectors (warm start)
-    float* Ss = Vs + NP * LD;                                // V^T V of the previous eigenvectors
     unsigned char* s_partner = smem_os + L::kMatBytes;       // [round][player]
     __shared__ float s_gam[2][NW][NP];                       // partial gamma per warp, by parity
     __shared__ float s_red[NW][NP];
@@ -539,8 +539,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     if (block_stopped<MODE>(a, blk, s, off)) return;
     const int N = s + (s & 1);
     const int r0 = w * kOSRows;
-    // Warm start whenever eigenvectors are kept (they are the identity right after a reset); the
-    // stored V is re-orthonormalized below, so no periodic cold start is needed.
+    // Warm start whenever eigenvectors are kept (they are the identity right after a reset).
     const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
     for (int q = tid; q < NP * NP; q += NT) s_partner[q] = (unsigned char)rr_partner(q % NP, q / NP, N);
@@ -568,7 +567,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     }
     __syncthreads();
 
-    // ---- shift sigma = ||W||_F and the initial columns: G = B V, V = I (cold) or stored
+    // ---- shift sigma = 2 ||W||_F and the initial columns: G = B (cold) or B V_prev (warm)
     float sq[1] = {0.f};
 #pragma unroll
     for (int h = 0; h < CPL; ++h)
@@ -578,41 +577,16 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
             sq[0] = fmaf(wv, wv, sq[0]);
         }
     block_sum_t<float, 1>(sq, red_f);
-    const float sigma = sqrtf(sq[0]);
-    float g[CPL][kOSRows], v[CPL][kOSRows];
+    const float sigma = 2.f * sqrtf(sq[0]);
+    float g[CPL][kOSRows];
     if (warm) {
-        // One Newton-Schulz step V <- V (3I - V^T V) / 2 removes the rounding drift that the
-        // rotations of earlier iterations left in the stored eigenvectors (quadratic in it).
-        for (int q = tid; q < NP * NP; q += NT) {
-            const int i = q / NP, j = q % NP;
-            if (j < i) continue;
-            float acc = 0.f;
-            for (int r = 0; r < NP; ++r) acc = fmaf(Vs[r * LD + i], Vs[r * LD + j], acc);
-            Ss[i * LD + j] = acc;
-            Ss[j * LD + i] = acc;
-        }
-        __syncthreads();
 #pragma unroll
         for (int h = 0; h < CPL; ++h)
 #pragma unroll
             for (int k = 0; k < kOSRows; ++k) {
                 const int r = r0 + k, c = lane + 32 * h;
-                float acc = 0.f;
-                for (int m = 0; m < NP; ++m) acc = fmaf(Vs[r * LD + m], Ss[m * LD + c], acc);
-                v[h][k] = fmaf(-0.5f, acc, 1.5f * Vs[r * LD + c]);
-            }
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < CPL; ++h)
-#pragma unroll
-            for (int k = 0; k < kOSRows; ++k) Vs[(r0 + k) * LD + lane + 32 * h] = v[h][k];
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < CPL; ++h)
-#pragma unroll
-            for (int k = 0; k < kOSRows; ++k) {
-                const int r = r0 + k, c = lane + 32 * h;
-                float acc = sigma * v[h][k];
+                float acc = sigma * Vs[r * LD + c];
+#pragma unroll 4
                 for (int m = 0; m < NP; ++m) acc = fmaf(Ws[r * LD + m], Vs[m * LD + c], acc);
                 g[h][k] = acc;
             }
@@ -622,7 +596,6 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 #pragma unroll
             for (int k = 0; k < kOSRows; ++k) {
                 const int r = r0 + k, c = lane + 32 * h;
-                v[h][k] = r == c ? 1.f : 0.f;
                 g[h][k] = Ws[r * LD + c] + ((r == c && c < N) ? sigma : 0.f);
             }
     }
@@ -721,23 +694,6 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
                 for (int k = 0; k < kOSRows; ++k) g[h][k] = fmaf(sg[h], gp[h][k], c[h] * g[h][k]);
             }
 #pragma unroll
-            for (int k = 0; k < kOSRows; ++k) {
-                float vp[CPL];
-#pragma unroll
-                for (int h = 0; h < CPL; ++h) {
-                    const int pl = p[h] & 31, ph = p[h] >> 5;
-                    float val = 0.f;
-#pragma unroll
-                    for (int hs = 0; hs < CPL; ++hs) {
-                        const float t = __shfl_sync(0xffffffffu, v[hs][k], pl);
-                        if (hs == ph) val = t;
-                    }
-                    vp[h] = val;
-                }
-#pragma unroll
-                for (int h = 0; h < CPL; ++h) v[h][k] = fmaf(sg[h], vp[h], c[h] * v[h][k]);
-            }
-#pragma unroll
             for (int h = 0; h < CPL; ++h)
                 alpha[h] = first[h] ? ai[h] - tt[h] * gam[h] : aj[h] + tt[h] * gam[h];
         }
@@ -753,33 +709,34 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         if (wmx < kOneSidedStop * kOneSidedStop) break;
     }
 
-    // ---- eigenvalues lambda_j = v_j . g_j - sigma, clipped; V into Ws (and HBM)
+    // ---- mu_j = ||g_j||, lambda_j = mu_j - sigma clipped, v_j = g_j / mu_j into Ws (and HBM)
 #pragma unroll
     for (int h = 0; h < CPL; ++h) {
         float pr = 0.f;
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) pr = fmaf(v[h][k], g[h][k], pr);
+        for (int k = 0; k < kOSRows; ++k) pr = fmaf(g[h][k], g[h][k], pr);
         s_red[w][lane + 32 * h] = pr;
     }
     __syncthreads();
     for (int c = tid; c < NP; c += NT) {
         float acc = 0.f;
         for (int ww = 0; ww < NW; ++ww) acc += s_red[ww][c];
-        const float lam = acc - sigma;
+        const float mu = sqrtf(acc);
+        const float lam = mu - sigma;
         dp[c] = (c < N && lam > 0.f) ? lam : 0.f;
+        s_gam[0][0][c] = mu > 0.f ? 1.f / mu : 0.f;
     }
+    __syncthreads();
 #pragma unroll
-    for (int h = 0; h < CPL; ++h)
+    for (int h = 0; h < CPL; ++h) {
+        const int c = lane + 32 * h;
+        const float inv = s_gam[0][0][c];
 #pragma unroll
-        for (int k = 0; k < kOSRows; ++k) Ws[(r0 + k) * LD + lane + 32 * h] = v[h][k];
-    if (vglob != nullptr) {
-#pragma unroll
-        for (int h = 0; h < CPL; ++h) {
-            const int c = lane + 32 * h;
-            if (c >= N) continue;
-#pragma unroll
-            for (int k = 0; k < kOSRows; ++k)
-                if (r0 + k < N) vglob[(r0 + k) * N + c] = v[h][k];
+        for (int k = 0; k < kOSRows; ++k) {
+            const int r = r0 + k;
+            const float v = inv > 0.f ? g[h][k] * inv : (r == c ? 1.f : 0.f);
+            Ws[r * LD + c] = v;
+            if (vglob != nullptr && c < N && r < N) vglob[r * N + c] = v;
         }
     }
     __syncthreads();
@@ -1047,7 +1004,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 // stores its column in the block's shared tile, the two warps meet at a named barrier, and each
 // lane reads its partner's column from the tile (twice, for the Gram entry and for the update,
 // which keeps register use near 64 floats). Two blocks per CTA of four warps.
-constexpr int kOW64LD = 65;
+constexpr int kOW64LD = 68;       // 16-byte rows: columns move through the tile as float4
 constexpr size_t kOW64BlockFloats = 2 * 64 * kOW64LD + 2 * 64;   // tile, V (warm start), alpha, scratch
 constexpr size_t kOW64Bytes = 2 * kOW64BlockFloats * sizeof(float);
 
@@ -1138,14 +1095,21 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
         for (int rd = 0; rd < N - 1; ++rd) {
             const int p = c < N ? rr_partner(c, rd, N) : c;
             pair_sync(pair);                                  // the previous round's reads are done
+            float4* mine = reinterpret_cast<float4*>(Ts + c * LD);
 #pragma unroll
-            for (int r = 0; r < 64; ++r) Ts[c * LD + r] = g[r];
+            for (int k = 0; k < 16; ++k) mine[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
             als[c] = alpha;
             pair_sync(pair);
-            const float* gp = Ts + p * LD;
+            const float4* gp4 = reinterpret_cast<const float4*>(Ts + p * LD);
             float gam = 0.f;
 #pragma unroll
-            for (int r = 0; r < 64; ++r) gam = fmaf(g[r], gp[r], gam);
+            for (int k = 0; k < 16; ++k) {
+                const float4 q = gp4[k];
+                gam = fmaf(g[4 * k], q.x, gam);
+                gam = fmaf(g[4 * k + 1], q.y, gam);
+                gam = fmaf(g[4 * k + 2], q.z, gam);
+                gam = fmaf(g[4 * k + 3], q.w, gam);
+            }
             const float beta = als[p];
             if (p != c && fabsf(gam) > 1.0e-30f) {
                 const bool first = c < p;
@@ -1165,7 +1129,13 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
                 const float sn = t * cc;
                 const float sg = first ? -sn : sn;
 #pragma unroll
-                for (int r = 0; r < 64; ++r) g[r] = fmaf(sg, gp[r], cc * g[r]);
+                for (int k = 0; k < 16; ++k) {
+                    const float4 q = gp4[k];
+                    g[4 * k] = fmaf(sg, q.x, cc * g[4 * k]);
+                    g[4 * k + 1] = fmaf(sg, q.y, cc * g[4 * k + 1]);
+                    g[4 * k + 2] = fmaf(sg, q.z, cc * g[4 * k + 2]);
+                    g[4 * k + 3] = fmaf(sg, q.w, cc * g[4 * k + 3]);
+                }
                 alpha = first ? ai - t * gam : aj + t * gam;
             }
         }
