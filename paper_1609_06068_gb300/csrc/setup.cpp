@@ -20,12 +20,28 @@ int fail(std::string& err, int code, const std::string& msg) {
     return code;
 }
 
-// Lower E_L index of (row, col), row >= col; -1 when the pair is not in the pattern.
-inline long long find_entry(const std::vector<long long>& keys, long long k) {
-    auto it = std::lower_bound(keys.begin(), keys.end(), k);
-    if (it == keys.end() || *it != k) return -1;
-    return (long long)(it - keys.begin());
-}
+// Lower E_L index of (row, col), row >= col; -1 when the pair is not in the pattern. E_L is
+// sorted by column, then row: a binary search among the rows of one column.
+struct EntryIndex {
+    std::vector<long long> col_start;   // [n+1]
+    std::vector<int> rows;              // [|E_L|]
+    void build(const std::vector<long long>& keys, long long n) {
+        col_start.assign(n + 1, 0);
+        rows.resize(keys.size());
+        for (size_t e = 0; e < keys.size(); ++e) {
+            rows[e] = (int)(keys[e] % n);
+            col_start[keys[e] / n + 1]++;
+        }
+        for (long long c = 0; c < n; ++c) col_start[c + 1] += col_start[c];
+    }
+    long long find(long long r, long long c) const {
+        const int* lo = rows.data() + col_start[c];
+        const int* hi = rows.data() + col_start[c + 1];
+        const int* it = std::lower_bound(lo, hi, (int)r);
+        if (it == hi || *it != r) return -1;
+        return (long long)(it - rows.data());
+    }
+};
 
 // Set on the worker threads of a batch build: each problem is then built on one thread.
 thread_local bool t_serial = false;
@@ -134,6 +150,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     if ((long long)keys.size() >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
     const int nEL = (int)keys.size();
     hp.nEL = nEL;
+    EntryIndex index;
+    index.build(keys, n);
     hp.pat_row.resize(nEL);
     hp.pat_col.resize(nEL);
     hp.ew.resize(nEL);
@@ -146,11 +164,11 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     // ---- H_k as a gather map, and its transpose as a CSR scatter map with ascending k.
     hp.gather_idx.resize(SL);
     std::vector<int> cnt(nEL + 1, 0);
-    for (long long q = 0; q < SL; ++q) {
-        const long long e = find_entry(keys, pos_key[q]);
-        hp.gather_idx[q] = (int)e;
-        cnt[e + 1]++;
-    }
+    parallel_for(p, [&](int k) {
+        for (long long q = hp.blk_off[k]; q < hp.blk_off[k] + (long long)hp.blk_size[k] * (hp.blk_size[k] + 1) / 2; ++q)
+            hp.gather_idx[q] = (int)index.find(pos_key[q] % n, pos_key[q] / n);
+    });
+    for (long long q = 0; q < SL; ++q) cnt[hp.gather_idx[q] + 1]++;
     hp.sc_ptr.resize(nEL + 1);
     hp.sc_ptr[0] = 0;
     for (int e = 0; e < nEL; ++e) hp.sc_ptr[e + 1] = hp.sc_ptr[e] + cnt[e + 1];
@@ -177,7 +195,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         const long long r = C_row[t], cc = C_col[t];
         if (r < 0 || r >= n || cc < 0 || cc >= n) return fail(err, SDP_ERR_ARG, "C index out of range");
         if (r < cc) return fail(err, SDP_ERR_ARG, "C must be given as lower coordinates (row >= col)");
-        const long long e = find_entry(keys, key_of(r, cc, n));
+        const long long e = index.find(r, cc);
         if (e < 0) {
             if (C_val[t] == 0.0) continue;
             return fail(err, SDP_ERR_CLIQUE, "a nonzero of C is not covered by the cliques");
@@ -188,7 +206,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         const long long r = pat_row[t], cc = pat_col[t];
         if (r < 0 || r >= n || cc < 0 || cc >= n || r < cc)
             return fail(err, SDP_ERR_ARG, "pattern coordinates out of range or not lower");
-        if (find_entry(keys, key_of(r, cc, n)) < 0)
+        if (index.find(r, cc) < 0)
             return fail(err, SDP_ERR_CLIQUE, "a pattern entry is not covered by the cliques");
     }
     hp.b.assign(b, b + m);
@@ -205,7 +223,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             const long long r = A_row[t], cc = A_col[t];
             if (r < 0 || r >= n || cc < 0 || cc >= n) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A index out of range"; return; }
             if (r < cc) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A must be given as lower coordinates (row >= col)"; return; }
-            const long long e = find_entry(keys, key_of(r, cc, n));
+            const long long e = index.find(r, cc);
             if (e < 0) {
                 if (A_val[t] == 0.0) continue;
                 row_err[i] = SDP_ERR_CLIQUE;
@@ -247,19 +265,46 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         });
     }
     hp.nnz = (long long)hp.a_col.size();
+    // CSC by a parallel transpose: thread t counts the columns of its contiguous block of rows;
+    // exclusive sums over (column, thread) give every thread its write offsets, so each column
+    // lists its rows in increasing order as a serial transpose would.
     hp.c_colptr.assign(nEL + 1, 0);
-    for (long long t = 0; t < hp.nnz; ++t) hp.c_colptr[hp.a_col[t] + 1]++;
-    for (int e = 0; e < nEL; ++e) hp.c_colptr[e + 1] += hp.c_colptr[e];
     hp.c_row.resize(hp.nnz);
     hp.c_val.resize(hp.nnz);
     {
-        std::vector<int> fillp(hp.c_colptr.begin(), hp.c_colptr.end() - 1);
-        for (int i = 0; i < m; ++i)
-            for (int t = hp.a_rowptr[i]; t < hp.a_rowptr[i + 1]; ++t) {
-                const int q = fillp[hp.a_col[t]]++;
-                hp.c_row[q] = (unsigned short)i;
-                hp.c_val[q] = hp.a_val[t];
+        const int nt = std::max(1, std::min(worker_count(), std::max(1, m / 8)));
+        std::vector<std::vector<int>> cnt_t(nt, std::vector<int>(nEL, 0));
+        auto rows_of = [&](int t, int& lo, int& hi) {
+            lo = (int)((long long)m * t / nt);
+            hi = (int)((long long)m * (t + 1) / nt);
+        };
+        parallel_for(nt, [&](int t) {
+            int lo, hi;
+            rows_of(t, lo, hi);
+            for (int tt = hp.a_rowptr[lo]; tt < hp.a_rowptr[hi]; ++tt) cnt_t[t][hp.a_col[tt]]++;
+        });
+        // exclusive offsets: column-major over (column, thread)
+        long long run = 0;
+        for (int e = 0; e < nEL; ++e) {
+            hp.c_colptr[e] = (int)run;
+            for (int t = 0; t < nt; ++t) {
+                const int c0 = cnt_t[t][e];
+                cnt_t[t][e] = (int)run;
+                run += c0;
             }
+        }
+        hp.c_colptr[nEL] = (int)run;
+        parallel_for(nt, [&](int t) {
+            int lo, hi;
+            rows_of(t, lo, hi);
+            std::vector<int>& fillp = cnt_t[t];
+            for (int i = lo; i < hi; ++i)
+                for (int tt = hp.a_rowptr[i]; tt < hp.a_rowptr[i + 1]; ++tt) {
+                    const int q = fillp[hp.a_col[tt]]++;
+                    hp.c_row[q] = (unsigned short)i;
+                    hp.c_val[q] = hp.a_val[tt];
+                }
+        });
     }
 
     // ---- M = A D^-1 A^T on the full symmetric vectors: M_ij = sum_e w_e A_ie A_je / D_e, with
@@ -366,7 +411,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         if (off >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "padded nnz(A) >= 2^31");
         hp.sell_val.assign(off, 0.0);
         hp.sell_row.assign(off, 0);
-        for (int sl = 0; sl < ns; ++sl)
+        parallel_for(ns, [&](int sl) {
             for (int t = 0; t < 32; ++t) {
                 const int c = slot_col[32LL * sl + t];
                 if (c < 0) continue;
@@ -376,6 +421,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                     hp.sell_row[q] = hp.c_row[j];
                 }
             }
+        });
         std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
         std::vector<unsigned short>().swap(hp.c_row);
     }
