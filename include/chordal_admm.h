@@ -63,7 +63,9 @@ typedef struct {
     int max_iter;      /* iteration cap of one admm_solve call (the paper uses 2000)             */
     int check_every;   /* admm_solve reads the device stop flag every check_every iterations;
                           iterations after convergence inside that window are skipped on the
-                          device, so results do not depend on it (0 = default 16)                */
+                          device, so the results of one problem do not depend on it (0 = default
+                          16). A batch is re-planned at these points for the problems still
+                          iterating, which can move its results by rounding.                   */
     int form;          /* SDP_PRIMAL or SDP_DUAL                                                 */
     int prec;          /* SDP_PROJ_FP64 or SDP_PROJ_FP32                                         */
     int flags;         /* reserved, must be 0                                                    */
@@ -147,7 +149,8 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
  * no CTA works on two problems. Each problem keeps its own residuals, objectives and stop test
  * (the definitions below): a problem whose residuals fall below tol, or become NaN/Inf, is frozen
  * (its iterates stop changing) at that iteration, which is what a separate solve of it would
- * return. A call ends when every problem is frozen or its budget is used. For a batch,
+ * return. A call ends when every problem is frozen or its budget is used. Once half of the
+ * problems are frozen, the launches are re-planned (at a stop-flag check) to cover only the rest. For a batch,
  * admm_result.status is SDP_ERR_NAN if a problem stopped on NaN/Inf, else SDP_OK if all converged,
  * else SDP_MAX_ITER; eps_p / eps_d are the maxima over the problems and the objectives their sums
  * (the objectives of the union). admm_reset, sdp_set_state and sdp_set_opts unfreeze every problem.

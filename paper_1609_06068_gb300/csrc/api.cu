@@ -79,6 +79,17 @@ struct sdp_ctx {
     std::vector<int> inst_vtx, inst_row, inst_cl, inst_e, inst_pos;
     std::vector<int> order_h, blk_size_h;   // for rebuilding the projection plans
     int ow_min_blocks = 0;
+    std::vector<int> proj_table[2];         // per precision: variant by padded order (empty = defaults)
+    // What the work schedules are built from, kept so that a batch can be re-planned for the
+    // problems still iterating (frozen problems then get no CTAs at all).
+    struct SchedSource {
+        int ninst = 1, m = 0, SL = 0, num_sms = 0;
+        long long nnz = 0;
+        std::vector<int> inst_row, inst_e, inst_pos, inst_sl, inst_cl, a_rowptr, sell_len, heavy;
+        std::vector<long long> inst_nnz;
+    } src;
+    int planned = 0;                        // problems the current schedules cover
+    size_t row_cap = 0, col_cap = 0;        // capacity of the CSR-chunk and A^T-chunk partial sums
     // Unrolled iterations kept for reverse mode (sdp_unrolled_forward / _backward).
     struct Adjoint {
         int T = 0, K = 0, nseg = 0, n_large = 0;
@@ -89,7 +100,11 @@ struct sdp_ctx {
         double* Vseg = nullptr;             // K x (sum N_k^2): their eigenvectors
         double *lam_prev = nullptr, *Xb = nullptr, *Lb = nullptr, *ub = nullptr;
         double *cbar = nullptr, *bbar = nullptr;
-        cadmm::IterPtrs AP{};               // the forward's pointers with adjoint vectors swapped in
+        // vectors of the adjoint KKT solve, swapped into a copy of the forward's pointers
+        double *xbar = nullptr, *rsw = nullptr, *rbar = nullptr, *ybar = nullptr, *z1 = nullptr;
+        double *tpart = nullptr, *pobj = nullptr;
+        int* conv = nullptr;
+        cadmm::Ctrl* ctrl = nullptr;
         std::vector<void*> seg_allocs;
     } adj;
     cadmm::ProjPlan plan[2]{};    // projection launches per precision (SDP_PROJ_FP64, SDP_PROJ_FP32)
@@ -113,8 +128,8 @@ struct sdp_ctx {
         return SDP_OK;
     }
     template <typename T>
-    int upload(T** ptr, const std::vector<T>& v) {
-        int rc = dalloc(ptr, v.size());
+    int upload(T** ptr, const std::vector<T>& v, size_t capacity = 0) {
+        int rc = dalloc(ptr, std::max(v.size(), capacity));
         if (rc) return rc;
         if (!v.empty()) {
             const cudaError_t e = cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -141,6 +156,9 @@ struct sdp_ctx {
 };
 
 namespace {
+
+int plan_all(sdp_ctx* h);
+int maybe_replan(sdp_ctx* h, cudaStream_t st, bool* done);
 
 int capture_graph(sdp_ctx* h, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
@@ -197,7 +215,7 @@ int rebuild_r_if_primal(sdp_ctx* h, cudaStream_t st) {
 // Every problem of a batch iterates again (after a reset, a state upload or new options).
 int unfreeze(sdp_ctx* h, cudaStream_t st) {
     CK(cadmm::launch_inst_reset(h->P, st));
-    return SDP_OK;
+    return plan_all(h);
 }
 
 int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
@@ -221,6 +239,13 @@ int run_iterations(sdp_ctx* h, int n_iters, cudaStream_t st, admm_result* out) {
             rc = wait_event(h->ev[slot ^ 1], kWaitTimeoutSeconds);
             if (rc) return rc;
             if (h->h_ctrl[slot ^ 1].done) stop = true;
+            else if (h->ninst > 1 && h->h_ctrl[slot ^ 1].active > 0 && 2 * h->h_ctrl[slot ^ 1].active <= h->planned) {
+                bool done = false;
+                if ((rc = maybe_replan(h, st, &done))) return rc;
+                if ((rc = ensure_graphs(h))) return rc;
+                if (done) stop = true;
+                launched_chunks = -1;         // the pipeline restarts after the synchronization
+            }
         }
         ++launched_chunks;
         slot ^= 1;
@@ -259,11 +284,18 @@ struct Schedules {
 };
 
 
-Schedules build_schedules(const HostProblem& hp, int num_sms) {
+Schedules build_schedules(const sdp_ctx::SchedSource& hp, const std::vector<char>& act) {
     Schedules S;
-    const int Q = hp.ninst;
+    const int Q = hp.ninst, num_sms = hp.num_sms;
     int mmax = 1;
-    for (int q = 0; q < Q; ++q) mmax = std::max(mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
+    long long nnz = 0, SL = 0, slices = 0;
+    for (int q = 0; q < Q; ++q) {
+        mmax = std::max(mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
+        if (!act[q]) continue;
+        nnz += hp.inst_nnz[q];
+        SL += hp.inst_pos[q + 1] - hp.inst_pos[q];
+        slices += hp.inst_sl[q + 1] - hp.inst_sl[q];
+    }
     // grids of whole waves: the CTAs each kernel can keep resident on an SM
     const long long rows_res = cadmm::resident_ctas(0, 0);
     const long long cols_res = cadmm::resident_ctas(1, (size_t)mmax * sizeof(double));
@@ -271,42 +303,45 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
     const long long nchunk = 8LL * rows_res * num_sms;
     // CSR: each row split into chunks of about nnz / nchunk nonzeros (at least 1024, at most 256
     // chunks per row); one warp per chunk.
-    const long long rt = std::max<long long>(1024, (hp.nnz + nchunk - 1) / nchunk);
+    const long long rt = std::max<long long>(1024, (nnz + nchunk - 1) / nchunk);
     S.row_chunk.assign(hp.m + 1, 0);
     for (int q = 0; q < Q; ++q)
         for (int i = hp.inst_row[q]; i < hp.inst_row[q + 1]; ++i) {
-            const int lo0 = hp.a_rowptr[i], hi0 = hp.a_rowptr[i + 1];
-            const long long len = hi0 - lo0;
-            const int R = (int)std::max<long long>(1, std::min<long long>(256, (len + rt - 1) / rt));
-            for (int ch = 0; ch < R; ++ch)
-                S.row.push_back({q, lo0 + (int)(len * ch / R), lo0 + (int)(len * (ch + 1) / R), i});
+            if (act[q]) {
+                const int lo0 = hp.a_rowptr[i], hi0 = hp.a_rowptr[i + 1];
+                const long long len = hi0 - lo0;
+                const int R = (int)std::max<long long>(1, std::min<long long>(256, (len + rt - 1) / rt));
+                for (int ch = 0; ch < R; ++ch)
+                    S.row.push_back({q, lo0 + (int)(len * ch / R), lo0 + (int)(len * (ch + 1) / R), i});
+            }
             S.row_chunk[i + 1] = (int)S.row.size();
         }
     // L^-1 / L^-T products: 8 rows (one per warp) per CTA.
     for (int q = 0; q < Q; ++q)
-        for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1]; r += 8)
+        for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1] && act[q]; r += 8)
             S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
-    // A^T: CTA chunks of whole slices with about nnz / (8 SMs) stored elements (at least 2048);
-    // the warps of a CTA take its slices in turn, one lane per column. With fewer than 16 slices
-    // per SM in all, every slice gets a CTA of its own instead, whose warps split the slice's length.
-    const long long ct = std::max<long long>(2048, (hp.nnz + cols_res * num_sms - 1) / (cols_res * num_sms));
-    S.col_split = hp.inst_sl[Q] < 16LL * num_sms;
+    // A^T: CTA chunks of whole slices with about nnz / (resident CTAs x SMs) stored elements (at
+    // least 2048); the warps of a CTA take its slices in turn, one lane per column. With fewer
+    // than 16 slices per SM in all, every slice gets a CTA of its own instead, whose warps split
+    // the slice's length.
+    const long long ct = std::max<long long>(2048, (nnz + cols_res * num_sms - 1) / (cols_res * num_sms));
+    S.col_split = slices < 16LL * num_sms;
     S.inst_col_chunk.assign(Q + 1, 0);
-    for (int q = 0; q < Q && S.col_split; ++q) {
-        for (int sl = hp.inst_sl[q]; sl < hp.inst_sl[q + 1]; ++sl) S.col.push_back({q, sl, sl + 1, 0});
-        S.inst_col_chunk[q + 1] = (int)S.col.size();
-    }
-    for (int q = 0; q < Q && !S.col_split; ++q) {
+    for (int q = 0; q < Q; ++q) {
         int sl = hp.inst_sl[q];
-        const int s1 = hp.inst_sl[q + 1];
-        while (sl < s1) {
-            const int lo = sl;
-            long long acc = 0;
-            while (sl < s1 && (sl == lo || acc + 32LL * hp.sell_len[sl] <= ct)) {
-                acc += 32LL * hp.sell_len[sl];
-                ++sl;
+        const int s1 = act[q] ? hp.inst_sl[q + 1] : sl;
+        if (S.col_split) {
+            for (; sl < s1; ++sl) S.col.push_back({q, sl, sl + 1, 0});
+        } else {
+            while (sl < s1) {
+                const int lo = sl;
+                long long acc = 0;
+                while (sl < s1 && (sl == lo || acc + 32LL * hp.sell_len[sl] <= ct)) {
+                    acc += 32LL * hp.sell_len[sl];
+                    ++sl;
+                }
+                S.col.push_back({q, lo, sl, 0});
             }
-            S.col.push_back({q, lo, sl, 0});
         }
         S.inst_col_chunk[q + 1] = (int)S.col.size();
     }
@@ -314,25 +349,100 @@ Schedules build_schedules(const HostProblem& hp, int num_sms) {
     // Packed positions per CTA of the dual update: about one wave of resident CTAs, 256..2048
     // (1..8 per thread) each.
     const int pos_per = (int)std::max<long long>(
-        256, std::min<long long>(2048, ((long long)hp.SL / (upd_res * num_sms) + 255) / 256 * 256));
+        256, std::min<long long>(2048, (SL / (upd_res * num_sms) + 255) / 256 * 256));
     S.inst_pos_cta.assign(Q + 1, 0);
     S.inst_ent_cta.assign(Q + 1, 0);
     S.inst_heavy_cta.assign(Q + 1, 0);
     size_t h = 0;
     for (int q = 0; q < Q; ++q) {
-        for (int lo = hp.inst_pos[q]; lo < hp.inst_pos[q + 1]; lo += pos_per)
-            S.pos.push_back({q, lo, std::min(lo + pos_per, hp.inst_pos[q + 1]), 0});
-        S.inst_pos_cta[q + 1] = (int)S.pos.size();
-        for (int lo = hp.inst_e[q]; lo < hp.inst_e[q + 1]; lo += 256)
-            S.ent.push_back({q, lo, std::min(lo + 256, hp.inst_e[q + 1]), 0});
-        S.inst_ent_cta[q + 1] = (int)S.ent.size();
         const size_t h0 = h;
         while (h < hp.heavy.size() && hp.heavy[h] < hp.inst_e[q + 1]) ++h;
-        for (size_t lo = h0; lo < h; lo += 8)
-            S.heavy.push_back({q, (int)lo, (int)std::min(lo + 8, h), 0});
+        if (act[q]) {
+            for (int lo = hp.inst_pos[q]; lo < hp.inst_pos[q + 1]; lo += pos_per)
+                S.pos.push_back({q, lo, std::min(lo + pos_per, hp.inst_pos[q + 1]), 0});
+            for (int lo = hp.inst_e[q]; lo < hp.inst_e[q + 1]; lo += 256)
+                S.ent.push_back({q, lo, std::min(lo + 256, hp.inst_e[q + 1]), 0});
+            for (size_t lo = h0; lo < h; lo += 8)
+                S.heavy.push_back({q, (int)lo, (int)std::min(lo + 8, h), 0});
+        }
+        S.inst_pos_cta[q + 1] = (int)S.pos.size();
+        S.inst_ent_cta[q + 1] = (int)S.ent.size();
         S.inst_heavy_cta[q + 1] = (int)S.heavy.size();
     }
     return S;
+}
+
+// Order of the cliques of the active problems, largest first (stable).
+std::vector<int> active_order(const sdp_ctx* h, const std::vector<char>& act) {
+    std::vector<int> order;
+    order.reserve(h->order_h.size());
+    const auto& cl = h->src.inst_cl;
+    for (int k : h->order_h) {
+        const int q = (int)(std::upper_bound(cl.begin(), cl.end(), k) - cl.begin()) - 1;
+        if (act[q]) order.push_back(k);
+    }
+    return order;
+}
+
+template <typename T>
+int copy_to(const T* dst, const std::vector<T>& v) {
+    if (v.empty()) return SDP_OK;
+    CK(cudaMemcpy(const_cast<T*>(dst), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SDP_OK;
+}
+
+// Point the iteration at the problems in `act`: schedules, clique order and projection plans.
+// The device arrays were sized for all problems at setup, so any subset fits. The graphs hold the
+// old launch shapes and are dropped (they are captured again at the next iteration call).
+int apply_plan(sdp_ctx* h, const std::vector<char>& act) {
+    const Schedules S = build_schedules(h->src, act);
+    IterPtrs& P = h->P;
+    int rc;
+    if ((rc = copy_to(P.row_sched, S.row)) || (rc = copy_to(P.row_chunk, S.row_chunk)) ||
+        (rc = copy_to(P.tri_sched, S.tri)) || (rc = copy_to(P.col_sched, S.col)) ||
+        (rc = copy_to(P.pos_sched, S.pos)) || (rc = copy_to(P.ent_sched, S.ent)) ||
+        (rc = copy_to(P.heavy_sched, S.heavy)) || (rc = copy_to(P.inst_col_chunk, S.inst_col_chunk)) ||
+        (rc = copy_to(P.inst_pos_cta, S.inst_pos_cta)) || (rc = copy_to(P.inst_ent_cta, S.inst_ent_cta)) ||
+        (rc = copy_to(P.inst_heavy_cta, S.inst_heavy_cta)))
+        return rc;
+    P.row_chunks = (int)S.row.size();
+    P.tri_ctas = (int)S.tri.size();
+    P.col_chunks = (int)S.col.size();
+    P.col_split = S.col_split ? 1 : 0;
+    P.pos_ctas = (int)S.pos.size();
+    P.ent_ctas = (int)S.ent.size();
+    P.heavy_ctas = (int)S.heavy.size();
+    const std::vector<int> order = active_order(h, act);
+    if ((rc = copy_to(P.order, order))) return rc;
+    for (int prec = 0; prec < 2; ++prec)
+        h->plan[prec] = cadmm::make_proj_plan(order, h->blk_size_h, prec,
+                                              h->proj_table[prec].empty() ? nullptr : h->proj_table[prec].data(),
+                                              h->ow_min_blocks);
+    h->planned = 0;
+    for (char a : act) h->planned += a ? 1 : 0;
+    h->destroy_graphs();
+    return SDP_OK;
+}
+
+int plan_all(sdp_ctx* h) {
+    if (h->planned == h->ninst) return SDP_OK;
+    return apply_plan(h, std::vector<char>(h->ninst, 1));
+}
+
+// Batches: once half of the problems the schedules cover have stopped, re-plan for the rest.
+// Problems that stopped at the current iteration stay in (their primal blocks are copied to the
+// other buffer by the next projection).
+int maybe_replan(sdp_ctx* h, cudaStream_t st, bool* done) {
+    CK(cudaStreamSynchronize(st));
+    Ctrl c{};
+    CK(cudaMemcpy(&c, h->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    *done = c.done != 0;
+    if (c.done || c.active <= 0 || 2 * c.active > h->planned) return SDP_OK;
+    std::vector<int> conv(h->ninst);
+    CK(cudaMemcpy(conv.data(), h->P.inst_conv, sizeof(int) * h->ninst, cudaMemcpyDeviceToHost));
+    std::vector<char> act(h->ninst);
+    for (int q = 0; q < h->ninst; ++q) act[q] = conv[q] < 0 || conv[q] >= c.iter;
+    return apply_plan(h, act);
 }
 
 // The batched projection on caller buffers: blocks largest first, one launch per run of blocks
@@ -428,7 +538,27 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     h->ow_min_blocks = cadmm::proj_ow_min_blocks(num_sms);
     h->plan[SDP_PROJ_FP64] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP64, nullptr, h->ow_min_blocks);
     h->plan[SDP_PROJ_FP32] = cadmm::make_proj_plan(hp.order, hp.blk_size, SDP_PROJ_FP32, nullptr, h->ow_min_blocks);
-    const Schedules S = build_schedules(hp, num_sms);
+    {
+        auto& sr = h->src;
+        sr.ninst = hp.ninst;
+        sr.m = hp.m;
+        sr.SL = hp.SL;
+        sr.nnz = hp.nnz;
+        sr.num_sms = num_sms;
+        sr.inst_row = hp.inst_row;
+        sr.inst_e = hp.inst_e;
+        sr.inst_pos = hp.inst_pos;
+        sr.inst_sl = hp.inst_sl;
+        sr.inst_cl = hp.inst_cl;
+        sr.a_rowptr = hp.a_rowptr;
+        sr.sell_len = hp.sell_len;
+        sr.heavy = hp.heavy;
+        sr.inst_nnz.resize(hp.ninst);
+        for (int q = 0; q < hp.ninst; ++q)
+            sr.inst_nnz[q] = (long long)hp.a_rowptr[hp.inst_row[q + 1]] - hp.a_rowptr[hp.inst_row[q]];
+    }
+    const Schedules S = build_schedules(h->src, std::vector<char>(hp.ninst, 1));
+    h->planned = hp.ninst;
     IterPtrs& P = h->P;
     P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
     P.ninst = hp.ninst;
@@ -459,11 +589,33 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(inst_row, hp.inst_row);
     UP(mblk_off, hp.mblk_off);
     UP(blk_inst, blk_inst);
-    UP(row_sched, S.row);
+    // Re-planning a batch for fewer problems splits their work more finely, so the schedules and
+    // partial sums are sized for the finest split any subset can get (chunks of at least 1024
+    // nonzeros per row, one slice per A^T chunk, 256 positions per update CTA).
+    size_t row_cap = 0, pos_cap = 0;
+    const size_t col_cap = (size_t)hp.inst_sl[hp.ninst];
+    for (int i = 0; i < hp.m; ++i) {
+        const long long len = hp.a_rowptr[i + 1] - hp.a_rowptr[i];
+        row_cap += (size_t)std::max<long long>(1, std::min<long long>(256, (len + 1023) / 1024));
+    }
+    for (int q = 0; q < hp.ninst; ++q) pos_cap += (size_t)(hp.inst_pos[q + 1] - hp.inst_pos[q] + 255) / 256;
+    row_cap = std::max(row_cap, S.row.size());
+    pos_cap = std::max(pos_cap, S.pos.size());
+    h->row_cap = row_cap;
+    h->col_cap = std::max(col_cap, S.col.size());
+#define UPC(field, vec, cap)                                       \
+    do {                                                           \
+        auto* tmp_ = const_cast<std::remove_const_t<std::remove_pointer_t<decltype(P.field)>>*>(P.field); \
+        rc = h->upload(&tmp_, vec, cap);                           \
+        if (rc) return rc;                                         \
+        P.field = tmp_;                                            \
+    } while (0)
+    UPC(row_sched, S.row, row_cap);
     UP(row_chunk, S.row_chunk);
     UP(tri_sched, S.tri);
-    UP(col_sched, S.col);
-    UP(pos_sched, S.pos);
+    UPC(col_sched, S.col, std::max(col_cap, S.col.size()));
+    UPC(pos_sched, S.pos, pos_cap);
+#undef UPC
     UP(ent_sched, S.ent);
     UP(heavy_sched, S.heavy);
     UP(inst_col_chunk, S.inst_col_chunk);
@@ -509,10 +661,10 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
     if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
     if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
-    if ((rc = h->dalloc(&P.tpart, (size_t)P.row_chunks))) return rc;
+    if ((rc = h->dalloc(&P.tpart, row_cap))) return rc;
     if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
-    if ((rc = h->dalloc(&P.part_ent, (size_t)std::max(P.ent_ctas + P.heavy_ctas, P.pos_ctas) * 8))) return rc;
-    if ((rc = h->dalloc(&P.part_obj, (size_t)P.col_chunks))) return rc;
+    if ((rc = h->dalloc(&P.part_ent, std::max<size_t>(P.ent_ctas + P.heavy_ctas, pos_cap) * 8))) return rc;
+    if ((rc = h->dalloc(&P.part_obj, std::max(col_cap, S.col.size())))) return rc;
     if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
     {
         double* vs = nullptr;       // sized for FP64; FP32 blocks use the first half
@@ -808,10 +960,10 @@ int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len) {
     std::vector<int> t(SDP_MAX_CLIQUE + 2, -1);
     if (table)
         for (int i = 0; i < len; ++i) t[i] = table[i];
-    h->plan[prec] = cadmm::make_proj_plan(h->order_h, h->blk_size_h, prec, table ? t.data() : nullptr,
-                                          h->ow_min_blocks);
-    h->destroy_graphs();
-    return SDP_OK;
+    if (table) h->proj_table[prec] = t;
+    else h->proj_table[prec].clear();
+    h->planned = 0;                       // re-plan every problem with the new table
+    return plan_all(h);
 }
 
 int sdp_set_cost(sdp_handle h, const double* c_lower, void* cuda_stream) {
@@ -844,29 +996,15 @@ int ensure_adjoint(sdp_ctx* h, int T, int K) {
     const size_t need_ckpt = (size_t)nseg * 2 * SL, need_seg = (size_t)K * (SL + VS);
     if (A.Xb == nullptr) {
         int rc;
-        auto& P = h->P;
-        A.AP = P;
-        double *xbar, *rsw, *rbar, *ybar, *z1, *tpart, *pobj;
-        int* conv;
-        cadmm::Ctrl* ctrl;
         if ((rc = h->dalloc(&A.lam_prev, SL)) || (rc = h->dalloc(&A.Xb, SL)) || (rc = h->dalloc(&A.Lb, SL)) ||
             (rc = h->dalloc(&A.ub, SL)) || (rc = h->dalloc(&A.cbar, h->nEL)) || (rc = h->dalloc(&A.bbar, h->m)) ||
-            (rc = h->dalloc(&xbar, h->nEL)) || (rc = h->dalloc(&rsw, h->nEL)) || (rc = h->dalloc(&rbar, h->nEL)) ||
-            (rc = h->dalloc(&ybar, h->m)) || (rc = h->dalloc(&z1, h->m)) ||
-            (rc = h->dalloc(&tpart, (size_t)P.row_chunks)) || (rc = h->dalloc(&pobj, (size_t)P.col_chunks)) ||
-            (rc = h->dalloc(&conv, (size_t)h->ninst)) || (rc = h->dalloc(&ctrl, 1)))
+            (rc = h->dalloc(&A.xbar, h->nEL)) || (rc = h->dalloc(&A.rsw, h->nEL)) ||
+            (rc = h->dalloc(&A.rbar, h->nEL)) || (rc = h->dalloc(&A.ybar, h->m)) || (rc = h->dalloc(&A.z1, h->m)) ||
+            (rc = h->dalloc(&A.tpart, h->row_cap)) || (rc = h->dalloc(&A.pobj, h->col_cap)) ||
+            (rc = h->dalloc(&A.conv, (size_t)h->ninst)) || (rc = h->dalloc(&A.ctrl, 1)))
             return rc;
-        CK(cudaMemset(conv, 0xff, sizeof(int) * h->ninst));        // -1: no problem stopped
-        CK(cudaMemset(ctrl, 0, sizeof(cadmm::Ctrl)));             // done = 0 for good
-        A.AP.r = xbar;
-        A.AP.rsw = rsw;
-        A.AP.x = rbar;
-        A.AP.y = ybar;
-        A.AP.z1 = z1;
-        A.AP.tpart = tpart;
-        A.AP.part_obj = pobj;
-        A.AP.inst_conv = conv;
-        A.AP.ctrl = ctrl;
+        CK(cudaMemset(A.conv, 0xff, sizeof(int) * h->ninst));      // -1: no problem stopped
+        CK(cudaMemset(A.ctrl, 0, sizeof(cadmm::Ctrl)));           // done = 0 for good
         A.n_large = 0;
         for (int s : h->blk_size_h) A.n_large += (s + (s & 1)) > 16;
     }
@@ -892,6 +1030,22 @@ int ensure_adjoint(sdp_ctx* h, int T, int K) {
     A.K = K;
     A.nseg = nseg;
     return SDP_OK;
+}
+
+// The forward's pointers (current schedules) with the adjoint solve's vectors swapped in.
+cadmm::IterPtrs adjoint_ptrs(const sdp_ctx* h) {
+    const auto& A = h->adj;
+    cadmm::IterPtrs AP = h->P;
+    AP.r = A.xbar;
+    AP.rsw = A.rsw;
+    AP.x = A.rbar;
+    AP.y = A.ybar;
+    AP.z1 = A.z1;
+    AP.tpart = A.tpart;
+    AP.part_obj = A.pobj;
+    AP.inst_conv = A.conv;
+    AP.ctrl = A.ctrl;
+    return AP;
 }
 
 }  // namespace
@@ -948,6 +1102,7 @@ int sdp_unrolled_backward(sdp_handle h, const double* xbar, double* cbar, double
     CK(cudaSetDevice(h->device));
     cudaStream_t st = as_stream(cuda_stream);
     const cadmm::IterPtrs& P = h->P;
+    const cadmm::IterPtrs AP = adjoint_ptrs(h);
     const double rho = h->opts.rho, rinv = 1.0 / rho;
     const size_t SL = h->SL, VS = (size_t)h->vstore_elems;
     CK(cudaMemsetAsync(A.Xb, 0, sizeof(double) * std::max<size_t>(1, SL), st));
@@ -976,9 +1131,9 @@ int sdp_unrolled_backward(sdp_handle h, const double* xbar, double* cbar, double
             const int t = t0 + j + 1;
             CK(cadmm::launch_dk_vjp(P, A.n_large, A.Wseg + (size_t)j * SL, A.Vseg + (size_t)j * VS, A.Xb, A.Lb,
                                     A.ub, rho, st));
-            CK(cadmm::launch_adj_scatter(P, A.ub, t == A.T ? xbar : nullptr, A.AP.r, A.AP.rsw, st));
-            CK(cadmm::launch_kkt_adjoint(A.AP, st));
-            CK(cadmm::launch_adj_accum(P, A.AP.x, A.AP.y, A.cbar, A.bbar, A.Xb, A.Lb, rinv, st));
+            CK(cadmm::launch_adj_scatter(P, A.ub, t == A.T ? xbar : nullptr, AP.r, AP.rsw, st));
+            CK(cadmm::launch_kkt_adjoint(AP, st));
+            CK(cadmm::launch_adj_accum(P, AP.x, AP.y, A.cbar, A.bbar, A.Xb, A.Lb, rinv, st));
         }
     }
     CK(cadmm::launch_adj_finish(P, A.cbar, A.bbar, cbar, bbar, st));

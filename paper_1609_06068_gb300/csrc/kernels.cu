@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(256) k_finalize_batch(IterPtrs P, int form, do
     C->obj_p = g[2];
     C->obj_d = g[3];
     C->ticket = 0;
+    C->active = ga;
     if (ga == 0) {
         C->status = gn > 0 ? SDP_ERR_NAN : SDP_OK;
         C->done = 1;

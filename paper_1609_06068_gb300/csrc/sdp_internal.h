@@ -18,6 +18,7 @@ struct Ctrl {
     int done;        // nonzero: remaining kernels return immediately
     int status;      // SDP_OK / SDP_MAX_ITER / SDP_ERR_NAN once done
     unsigned int ticket;  // CTAs of the iteration's last kernel that have finished (last one finalizes)
+    int active;      // batches: problems still iterating after the last iteration
     double tol;
     double eps_p, eps_d, obj_p, obj_d;
 };
