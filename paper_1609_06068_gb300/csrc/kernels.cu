@@ -494,19 +494,29 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
         const int e = P.sell_col[32 * sl + lane], len = P.sell_len[sl];
         const double* __restrict__ val = P.sell_val + P.sell_off[sl] + lane;
         const unsigned short* __restrict__ row = P.sell_row + P.sell_off[sl] + lane;
-        double s0 = 0.0, s1 = 0.0;
+        // eight loads in flight per lane, four independent FMA chains
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int k = 0;
-        for (; k + 3 < len; k += 4) {
-            const double v0 = val[32 * k], v1 = val[32 * (k + 1)], v2 = val[32 * (k + 2)], v3 = val[32 * (k + 3)];
-            const int q0 = row[32 * k], q1 = row[32 * (k + 1)], q2 = row[32 * (k + 2)], q3 = row[32 * (k + 3)];
-            s0 = fma(v0, ys[q0], s0);
-            s1 = fma(v1, ys[q1], s1);
-            s0 = fma(v2, ys[q2], s0);
-            s1 = fma(v3, ys[q3], s1);
+        for (; k + 7 < len; k += 8) {
+            double v[8];
+            int q[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                v[t] = val[32 * (k + t)];
+                q[t] = row[32 * (k + t)];
+            }
+            s0 = fma(v[0], ys[q[0]], s0);
+            s1 = fma(v[1], ys[q[1]], s1);
+            s2 = fma(v[2], ys[q[2]], s2);
+            s3 = fma(v[3], ys[q[3]], s3);
+            s0 = fma(v[4], ys[q[4]], s0);
+            s1 = fma(v[5], ys[q[5]], s1);
+            s2 = fma(v[6], ys[q[6]], s2);
+            s3 = fma(v[7], ys[q[7]], s3);
         }
         for (; k < len; ++k) s0 = fma(val[32 * k], ys[row[32 * k]], s0);
         if (e >= 0) {
-            const double xe = (P.r[e] - (s0 + s1)) * P.dinv[e];
+            const double xe = (P.r[e] - ((s0 + s1) + (s2 + s3))) * P.dinv[e];
             P.x[e] = xe;
             obj = fma(wt(P.ew[e]) * P.c[e], xe, obj);
         }
