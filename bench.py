@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", choices=["m", "l", "d"], default=None,
+                    help="the paper's block-arrow sweep varying m, l or d (one JSON line per point)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="for profilers: set up, run this many iterations from a reset, exit (no JSON)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
@@ -499,10 +501,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Section V.A's sweeps: for every point, dual-form solves to 1e-3 (at most 2000 iterations)
+    with FP32 and FP64 eigensolves, device time of cold-start solves (CUDA events), setup time, and
+    the CPU oracle's time per iteration on a bounded sample (scaled to the GPU's iteration count)."""
+    import numpy as np
+    import torch
+
+    import paper_1609_06068_gb300 as cadmm
+    from oracle import chordal_admm as orc
+    from sdp_inputs import SWEEP_MAX_ITER, SWEEP_TOL, SWEEPS, sweep_instance
+
+    cadmm.load_library()
+    torch.cuda.set_device(0)
+    sw = SWEEPS[args.sweep]
+    rho = 0.02
+    for i, val in enumerate(sw["values"]):
+        inst = sweep_instance(args.sweep, i)
+        arrs = _arrays(inst)
+        t0 = time.perf_counter()
+        opts = cadmm.make_opts(rho=rho, tol=SWEEP_TOL, max_iter=SWEEP_MAX_ITER, form="dual", prec="fp32")
+        s = cadmm.ChordalADMM(arrs, opts)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        params = dict(sw["fixed"], **{args.sweep: val})
+        out = dict(sweep=args.sweep, point=i, value=val, params=params, n=inst.n, m=len(inst.b),
+                   p=len(inst.cliques), clique=len(inst.cliques[0]), nnz_A=s.sizes["nnz_A"],
+                   setup_ms=1e3 * setup_s, tol=SWEEP_TOL, rho=rho)
+        for prec in ("fp32", "fp64"):
+            s.set_opts(prec=prec)
+            s.reset()
+            s.solve()                                  # warm-up (graph capture)
+            reps = max(1, min(5, args.steps))
+            ms, res = [], None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.reset()
+                res = s.solve()
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out[prec] = dict(time_to_tol_ms=statistics.median(ms), iters=res["iters"], status=res["status"],
+                             obj_dual=res["obj_dual"], obj_primal=res["obj_primal"])
+        s.close()
+        # CPU oracle: time per dual iteration on a bounded sample, scaled to the GPU's iterations
+        # (skipped above 5 M nonzeros, where the oracle's own setup alone takes minutes)
+        if out["nnz_A"] > 5_000_000:
+            out["cpu_oracle"] = None
+            print(json.dumps(out), flush=True)
+            continue
+        sdp = orc.ChordalSDP(inst.n, inst.cliques, inst.A_ptr, inst.A_row, inst.A_col, inst.A_val,
+                             inst.b, inst.C_row, inst.C_col, inst.C_val)
+        st = orc.admm_init(sdp, "dual")
+        k, t0 = 0, time.perf_counter()
+        while k < 5 and (k == 0 or time.perf_counter() - t0 < args.cpu_seconds / len(sw["values"])):
+            st = orc.dual_iteration(sdp, st, rho)
+            k += 1
+        per_it = (time.perf_counter() - t0) / k
+        out["cpu_oracle"] = dict(ms_per_iter=1e3 * per_it, iters_timed=k, cores=1,
+                                 est_time_to_tol_ms=1e3 * per_it * out["fp64"]["iters"])
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.oracle_worker:
         oracle_worker(args)
+        return
+    if args.sweep is not None:
+        run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

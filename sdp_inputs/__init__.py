@@ -10,4 +10,8 @@ from .blockarrow import (  # noqa: F401
     config_instance,
     config_shapes,
     CONFIGS,
+    SWEEPS,
+    SWEEP_MAX_ITER,
+    SWEEP_TOL,
+    sweep_instance,
 )

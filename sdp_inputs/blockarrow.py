@@ -45,6 +45,28 @@ CONFIGS = {
 }
 
 
+# The paper's three block-arrow sweeps (Section V.A): one parameter varies, the others are fixed,
+# at tolerance 1e-3 and 2000 iterations. The paper's figure with the values is not reproduced
+# here, so the varied values span the ranges its text describes. Point i of sweep "x" uses seed
+# 9000 + 100 * ("mld".index(x)) + i.
+SWEEPS = {
+    "m": dict(fixed=dict(l=40, d=10, h=20), values=[50, 100, 200, 400, 700, 1000]),
+    "l": dict(fixed=dict(m=1000, d=10, h=20), values=[10, 20, 40, 80, 160, 320]),
+    "d": dict(fixed=dict(l=40, h=10, m=1000), values=[5, 10, 15, 20, 30, 40]),
+}
+SWEEP_TOL = 1e-3
+SWEEP_MAX_ITER = 2000
+
+
+def sweep_instance(name: str, i: int) -> "SDPInstance":
+    """Point i of sweep `name` ("m", "l" or "d"), density 30 %."""
+    sw = SWEEPS[name]
+    params = dict(sw["fixed"])
+    params[name] = sw["values"][i]
+    return block_arrow_instance(density=0.30, seed=9000 + 100 * "mld".index(name) + i,
+                                meta=dict(sweep=name, point=i), **params)
+
+
 @dataclass
 class SDPInstance:
     """One SDP ``min <C,X> s.t. <A_i,X> = b_i, X ⪰ 0`` with its chordal decomposition data."""

@@ -138,3 +138,20 @@ def test_switching_form_and_rho():
     ref = orc.admm_solve(sdp, "primal", rho=10.0, tol=1e-4, max_iter=2000)
     assert abs(r["iters"] - ref["iters"]) <= 1
     assert abs(r["obj_primal"] - ref["obj_primal"]) <= 1e-6 * abs(ref["obj_primal"])
+
+
+@pytest.mark.parametrize("name", ["m", "l", "d"])
+def test_sweep_first_point_converges_like_oracle(name):
+    """The first point of each of the paper's block-arrow sweeps (Section V.A) at its tolerance
+    1e-3, dual form, FP64: iteration count within 1 and objective within 1e-6 of the oracle."""
+    torch, cadmm = require_gpu()
+    from sdp_inputs import SWEEP_MAX_ITER, SWEEP_TOL, sweep_instance
+    inst = sweep_instance(name, 0)
+    arrs = sdp_cases.instance_arrays(inst)
+    sdp = make_oracle(arrs)
+    ref = orc.admm_solve(sdp, "dual", rho=0.02, tol=SWEEP_TOL, max_iter=SWEEP_MAX_ITER)
+    with setup_handle(cadmm, arrs, form="dual", prec="fp64", rho=0.02, tol=SWEEP_TOL, max_iter=SWEEP_MAX_ITER) as s:
+        r = s.solve()
+    assert r["status"] == ref["status"]
+    assert abs(r["iters"] - ref["iters"]) <= 1
+    assert abs(r["obj_dual"] - ref["obj_dual"]) <= 1e-6 * abs(ref["obj_dual"])
