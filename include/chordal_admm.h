@@ -128,7 +128,9 @@ typedef struct {
  *   b[m]        right-hand side
  *   C_*         cost matrix C, C_nnz coordinates
  *   pat_*       optional extra pattern coordinates that must be covered (may be NULL/0)
- *   clique_ptr[p+1], clique_vtx  the maximal cliques, vertices strictly ascending
+ *   clique_ptr[p+1], clique_vtx  the maximal cliques, vertices strictly ascending; p = 0 with
+ *               NULL arrays: those of a chordal extension of the aggregate pattern
+ *               (sdp_chordal_cliques on C, every A_i and pat_*)
  *   opts        initial options (copied)
  *   out         receives the handle on success
  * Errors: SDP_ERR_ARG, SDP_ERR_CLIQUE, SDP_ERR_NOT_PD, SDP_ERR_UNSUPPORTED, SDP_ERR_CUDA. */
@@ -170,6 +172,22 @@ int sdp_batch_layout(sdp_handle h, int* vtx_off, int* row_off, int* clique_off, 
  * iteration. */
 int sdp_batch_results(sdp_handle h, int* iters, int* status, double* eps_p, double* eps_d,
                       double* obj_primal, double* obj_dual);
+
+/* Chordal extension of a sparse symmetric pattern (Section II.A: a non-chordal aggregate pattern is
+ * first extended to a chordal one; the paper leaves the extension to heuristics) and the maximal
+ * cliques of the extension. Ordering by maximum cardinality search (ties: smallest vertex index),
+ * which adds nothing to a chordal pattern; symbolic elimination in that order; maximal cliques
+ * listed in elimination order of their defining vertex, vertices ascending.
+ *   n, nnz, row[nnz], col[nnz]  the pattern (host; either triangle or both; diagonal ignored)
+ *   p, nvtx, fill               outputs: number of cliques, total clique length, added lower pairs
+ *   clique_ptr[p+1], clique_vtx[nvtx]  outputs, or NULL to ask for the sizes first
+ * Host-only; needs no GPU. sdp_setup and sdp_setup_batch call it themselves when given p = 0
+ * (and NULL clique arrays), on the union of the coordinates of C, every A_i and the extra pattern.
+ * Errors: SDP_ERR_ARG (bad sizes or indices), SDP_ERR_ARG "too small" when the arrays passed are
+ * smaller than the sizes (call with NULL first). */
+int sdp_chordal_cliques(int n, long long nnz, const int* row, const int* col, int* p, long long* nvtx,
+                        long long* fill, int* clique_ptr, int* clique_vtx, int capacity_p,
+                        long long capacity_vtx);
 
 /* Replace the options (rho, tol, form, precision may all change; the KKT factor does not depend
  * on them). Takes effect at the next admm_iterate / admm_solve. Does not reset the iterates. */

@@ -43,7 +43,7 @@ EXPORTS = [
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
     "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_set_cost",
-    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_free",
+    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_free",
     "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         "project_variant_fits": (_I, [_I, _I, _I]),
         "project_psd_batched_variant": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
         "sdp_set_proj_table": (_I, [_P, _I, _P, _I]),
+        "sdp_chordal_cliques": (_I, [_I, _LL, _P, _P, _P, _P, _P, _P, _P, _I, _LL]),
         "sdp_set_cost": (_I, [_P, _P, _P]),
         "sdp_set_rhs": (_I, [_P, _P, _P]),
         "sdp_unrolled_forward": (_I, [_P, _I, _I, _P, _P]),
@@ -201,6 +202,8 @@ def _problem_arrays(n, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cliqu
         sizes = np.array([len(c) for c in cliques], dtype=np.int64)
         clique_ptr = np.concatenate([[0], np.cumsum(sizes)])
         clique_vtx = np.concatenate([np.asarray(c) for c in cliques]) if len(cliques) else np.zeros(0)
+    elif clique_ptr is None:
+        clique_ptr, clique_vtx = np.zeros(1), np.zeros(0)     # p = 0: the library's chordal extension
     d = dict(n=int(n), A_ptr=_arr(A_ptr, np.int64), A_row=_arr(A_row, np.int32), A_col=_arr(A_col, np.int32),
              A_val=_arr(A_val, np.float64), b=_arr(b, np.float64), C_row=_arr(C_row, np.int32),
              C_col=_arr(C_col, np.int32), C_val=_arr(C_val, np.float64),
@@ -409,6 +412,21 @@ def sdp_set_proj_table(h, prec, table=None):
     else:
         t = _arr(table, np.int32)
     _check(load_library().sdp_set_proj_table(h, p, _ptr(t), len(t)), "sdp_set_proj_table")
+
+
+def sdp_chordal_cliques(n, rows, cols):
+    """(cliques, fill): maximal cliques of the library's chordal extension of a pattern (host only)."""
+    lib = load_library()
+    r, c = _arr(rows, np.int32), _arr(cols, np.int32)
+    p, nv, fill = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib.sdp_chordal_cliques(int(n), len(r), _ptr(r), _ptr(c), ctypes.byref(p), ctypes.byref(nv),
+                                   ctypes.byref(fill), None, None, 0, 0), "sdp_chordal_cliques")
+    cp = np.zeros(p.value + 1, np.int32)
+    cv = np.zeros(max(1, nv.value), np.int32)
+    _check(lib.sdp_chordal_cliques(int(n), len(r), _ptr(r), _ptr(c), ctypes.byref(p), ctypes.byref(nv),
+                                   ctypes.byref(fill), _ptr(cp), _ptr(cv), p.value, nv.value),
+           "sdp_chordal_cliques")
+    return [cv[cp[k]:cp[k + 1]].copy() for k in range(p.value)], int(fill.value)
 
 
 def sdp_set_cost(h, c_lower, stream=None):

@@ -771,6 +771,33 @@ int sdp_batch_results(sdp_handle h, int* iters, int* status, double* eps_p, doub
     return SDP_OK;
 }
 
+int sdp_chordal_cliques(int n, long long nnz, const int* row, const int* col, int* p, long long* nvtx,
+                        long long* fill, int* clique_ptr, int* clique_vtx, int capacity_p,
+                        long long capacity_vtx) {
+    try {
+        std::vector<int> cp, cv;
+        long long f = 0;
+        std::string err;
+        const int rc = cadmm::chordal_cliques(n, nnz, row, col, cp, cv, f, err);
+        if (rc) return set_err(rc, err);
+        const int np = (int)cp.size() - 1;
+        if (p) *p = np;
+        if (nvtx) *nvtx = (long long)cv.size();
+        if (fill) *fill = f;
+        if (clique_ptr || clique_vtx) {
+            if (!clique_ptr || !clique_vtx || capacity_p < np || capacity_vtx < (long long)cv.size())
+                return set_err(SDP_ERR_ARG, "clique arrays too small (call with NULL arrays for the sizes)");
+            std::copy(cp.begin(), cp.end(), clique_ptr);
+            std::copy(cv.begin(), cv.end(), clique_vtx);
+        }
+        return SDP_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(SDP_ERR_ARG, "host out of memory");
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_chordal_cliques");
+    }
+}
+
 int sdp_set_opts(sdp_handle h, const admm_opts* opts) {
     if (!h) return set_err(SDP_ERR_ARG, "NULL handle");
     int rc = check_opts(opts);

@@ -62,6 +62,11 @@ struct HostProblem {
     std::vector<long long> mblk_off;                        // offsets of the L^-1 blocks
 };
 
+// Chordal extension of the symmetric pattern given by nnz (row, col) coordinates and the maximal
+// cliques of the extension (chordal.cpp). fill = lower pairs added.
+int chordal_cliques(int n, long long nnz, const int* row, const int* col, std::vector<int>& clique_ptr,
+                    std::vector<int>& clique_vtx, long long& fill, std::string& err);
+
 // Builds one HostProblem for a batch of independent problems (a block-diagonal problem). On
 // failure fills err (prefixed with the failing instance) and returns the SDP_* status.
 int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& hp, std::string& err);

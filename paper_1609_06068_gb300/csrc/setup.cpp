@@ -73,8 +73,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                        const int* C_col, const double* C_val, long long pat_nnz,
                        const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
                        const int* clique_vtx, HostProblem& hp, std::string& err) {
-    if (n <= 0 || m < 1 || p < 1 || !A_ptr || !b || !clique_ptr || !clique_vtx)
-        return fail(err, SDP_ERR_ARG, "n, m, p must be positive and A_ptr, b, cliques non-NULL");
+    if (n <= 0 || m < 1 || p < 0 || !A_ptr || !b || (p > 0 && (!clique_ptr || !clique_vtx)))
+        return fail(err, SDP_ERR_ARG, "n, m must be positive, p >= 0, and A_ptr, b, cliques non-NULL");
     if (m > SDP_MAX_CONSTRAINTS)
         return fail(err, SDP_ERR_UNSUPPORTED, "m exceeds SDP_MAX_CONSTRAINTS");
     if (C_nnz < 0 || pat_nnz < 0 || (C_nnz > 0 && (!C_row || !C_col || !C_val)) ||
@@ -85,6 +85,32 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         if (A_ptr[i + 1] < A_ptr[i]) return fail(err, SDP_ERR_ARG, "A_ptr must be non-decreasing");
     if (A_ptr[m] > 0 && (!A_row || !A_col || !A_val))
         return fail(err, SDP_ERR_ARG, "A coordinate arrays are NULL");
+
+    // p == 0: the cliques are those of a chordal extension of the aggregate pattern (C, every A_i
+    // and the extra pattern coordinates).
+    std::vector<int> ext_ptr, ext_vtx;
+    if (p == 0) {
+        if (C_nnz > 0 && (!C_row || !C_col)) return fail(err, SDP_ERR_ARG, "bad C arrays");
+        const long long annz = A_ptr[m];
+        std::vector<int> rr, cc;
+        rr.reserve((size_t)(annz + C_nnz + pat_nnz));
+        cc.reserve(rr.capacity());
+        auto add = [&](const int* r, const int* c, long long k) {
+            for (long long t = 0; t < k; ++t) {
+                rr.push_back(r[t]);
+                cc.push_back(c[t]);
+            }
+        };
+        if (annz > 0) add(A_row, A_col, annz);
+        add(C_row, C_col, C_nnz);
+        add(pat_row, pat_col, pat_nnz);
+        long long fill = 0;
+        const int rc = chordal_cliques(n, (long long)rr.size(), rr.data(), cc.data(), ext_ptr, ext_vtx, fill, err);
+        if (rc) return rc;
+        p = (int)ext_ptr.size() - 1;
+        clique_ptr = ext_ptr.data();
+        clique_vtx = ext_vtx.data();
+    }
 
     hp = HostProblem();
     hp.n = n;

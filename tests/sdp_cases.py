@@ -117,6 +117,37 @@ def random_block_arrow(l=3, d=3, h=2, m=6, seed=11, density=0.5) -> dict:
     return problem_from_dense(C, As, b, block_arrow_cliques(l, d, h))
 
 
+def random_sparse_sdp(n=24, m=8, edge_density=0.12, seed=5, density=0.5) -> dict:
+    """A small feasible SDP on a random non-chordal pattern (a cycle through all vertices plus
+    random edges); ``cliques`` is None, so a chordal extension has to supply them."""
+    rng = np.random.default_rng(seed)
+    P = np.eye(n, dtype=bool)
+    for i in range(n):
+        j = (i + 1) % n
+        P[i, j] = P[j, i] = True
+    R = rng.random((n, n)) < edge_density
+    R = np.tril(R, -1)
+    P |= R | R.T
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    X0 = G @ G.T
+    As = []
+    for _ in range(m):
+        A = rng.standard_normal((n, n)) * (rng.random((n, n)) < density)
+        A = np.tril(A) + np.tril(A, -1).T
+        As.append(A * P)
+    b = [float(np.sum(A * X0)) for A in As]
+    Z = rng.standard_normal((n, n))
+    Z = np.tril(Z, -1)
+    Z = (Z + Z.T) * P
+    Z += np.diag(np.abs(Z).sum(axis=1) + 1.0)
+    y0 = rng.standard_normal(m)
+    C = Z + sum(y * A for y, A in zip(y0, As))
+    C[P & (C == 0)] = 1e-3
+    d = problem_from_dense(C, As, b, [list(range(n))])
+    d["cliques"] = None
+    return d
+
+
 def instance_arrays(inst) -> dict:
     """Coordinate arrays of a generated ``SDPInstance``."""
     return dict(n=inst.n, cliques=inst.cliques, A_ptr=inst.A_ptr, A_row=inst.A_row, A_col=inst.A_col,

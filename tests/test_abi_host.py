@@ -122,3 +122,29 @@ def test_project_batched_validates_on_host(lib):
     assert f(dummy, dummy, P(sizes), P(offs[:1]), 1, 0, None) == cadmm.SDP_ERR_UNSUPPORTED
     assert f(dummy, dummy, P(sizes), P(offs[:1]), 1, 5, None) == cadmm.SDP_ERR_ARG
     assert f(None, None, None, None, 0, 0, None) == cadmm.SDP_OK
+
+
+def test_chordal_extension_matches_oracle():
+    """The library's chordal extension (host code, no GPU) gives exactly the oracle's cliques."""
+    import numpy as np
+    from oracle import chordal as ch
+    from sdp_inputs import config_instance
+    cadmm = pytest.importorskip("paper_1609_06068_gb300")
+    cadmm.load_library()
+    rng = np.random.default_rng(3)
+    cases = []
+    inst = config_instance(1)
+    cases.append((inst.n, inst.pat_row, inst.pat_col))
+    for _ in range(30):
+        n = int(rng.integers(1, 60))
+        rows, cols = np.tril_indices(n, -1)
+        keep = rng.random(len(rows)) < rng.uniform(0.01, 0.3)
+        cases.append((n, rows[keep], cols[keep]))
+    n = 17
+    cyc = np.arange(n)
+    cases.append((n, np.maximum(cyc, (cyc + 1) % n), np.minimum(cyc, (cyc + 1) % n)))
+    for n, rows, cols in cases:
+        got, gfill = cadmm.sdp_chordal_cliques(n, rows, cols)
+        want, wfill = ch.chordal_extension(n, rows, cols)
+        assert gfill == wfill
+        assert [list(map(int, c)) for c in got] == [list(c) for c in want]

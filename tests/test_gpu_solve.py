@@ -155,3 +155,30 @@ def test_sweep_first_point_converges_like_oracle(name):
     assert r["status"] == ref["status"]
     assert abs(r["iters"] - ref["iters"]) <= 1
     assert abs(r["obj_dual"] - ref["obj_dual"]) <= 1e-6 * abs(ref["obj_dual"])
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_non_chordal_pattern_via_chordal_extension(form):
+    """sdp_setup with no cliques extends the aggregate pattern itself (Section II.A); the solve then
+    follows the oracle run on the oracle's extension (the same cliques) and reaches the optimum of
+    the single-clique (dense) problem."""
+    torch, cadmm = require_gpu()
+    from oracle import chordal as och
+    arrs = sdp_cases.random_sparse_sdp(n=24, m=8, seed=5)
+    rows = np.concatenate([arrs["A_row"], arrs["C_row"]])
+    cols = np.concatenate([arrs["A_col"], arrs["C_col"]])
+    cliques, fill = och.chordal_extension(arrs["n"], rows, cols)
+    assert fill > 0                                    # the pattern was not chordal
+    ext = dict(arrs, cliques=[np.array(c, np.int32) for c in cliques])
+    sdp = make_oracle(ext)
+    ref = orc.admm_solve(sdp, form, rho=1.0, tol=1e-6, max_iter=20000)
+    dense = make_oracle(dict(arrs, cliques=[np.arange(arrs["n"], dtype=np.int32)]))
+    ref_dense = orc.admm_solve(dense, form, rho=1.0, tol=1e-8, max_iter=50000)
+    with setup_handle(cadmm, arrs, form=form, rho=1.0, tol=1e-6, max_iter=20000) as s:
+        r = s.solve()
+        assert s.sizes["p"] == len(cliques)
+    key = "obj_primal" if form == "primal" else "obj_dual"
+    assert r["status"] == cadmm.SDP_OK and ref["status"] == 0
+    assert abs(r["iters"] - ref["iters"]) <= 1
+    assert abs(r[key] - ref[key]) <= 1e-6 * abs(ref[key])
+    assert abs(r[key] - ref_dense[key]) <= 1e-4 * abs(ref_dense[key])
