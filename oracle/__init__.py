@@ -10,6 +10,8 @@ from .chordal_admm import (  # noqa: F401
     ChordalSDP,
     OracleError,
     proj_psd,
+    proj_soc,
+    proj_cone,
     admm_init,
     primal_iteration,
     dual_iteration,

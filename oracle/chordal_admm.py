@@ -61,6 +61,35 @@ def proj_psd(W: np.ndarray) -> np.ndarray:
     return 0.5 * (X + X.T)
 
 
+def proj_soc(w: np.ndarray) -> np.ndarray:
+    """Projection onto the second-order cone {(t, u) : ‖u‖ ≤ t} (the cone CDCS admits beside the
+    PSD one, Section V): the point itself inside the cone, zero inside its polar, otherwise
+    ((t + ‖u‖)/2) (1, u/‖u‖)."""
+    t, u = float(w[0]), np.asarray(w[1:], dtype=np.float64)
+    nu = float(np.sqrt(np.dot(u, u)))
+    if nu <= t:
+        return np.array(w, dtype=np.float64)
+    if nu <= -t:
+        return np.zeros(len(w))
+    a = 0.5 * (t + nu)
+    return np.concatenate([[a], (a / nu) * u])
+
+
+def proj_cone(kind: str, w: np.ndarray, dual: bool) -> np.ndarray:
+    """Projection onto a non-PSD cone block (primal form) or onto its dual cone (dual form).
+
+    The free cone ℝ^q has the dual cone {0}; the nonnegative orthant and the second-order cone
+    are self-dual.
+    """
+    if kind == "free":
+        return np.zeros(len(w)) if dual else np.array(w, dtype=np.float64)
+    if kind == "nonneg":
+        return np.maximum(w, 0.0)
+    if kind == "soc":
+        return proj_soc(w)
+    raise OracleError(-1, f"unknown cone {kind!r}")
+
+
 def _mat(v: np.ndarray, s: int) -> np.ndarray:
     """vec⁻¹: column-major s×s matrix from its stacked columns."""
     return v.reshape(s, s, order="F")
@@ -81,9 +110,19 @@ class ChordalSDP:
     Inputs are the standard-form data (Section I): ``A_i`` and ``C`` in lower-triangle coordinate
     form (row >= col; off-diagonal entries stand for both (i,j) and (j,i)), ``b``, and the maximal
     cliques of the chordal aggregate pattern (Section III.A assumes them given).
+
+    ``cones`` (optional) adds variables in the other cones CDCS accepts (Section V: ℝ^q, the
+    nonnegative orthant, second-order cones; only the PSD cone is decomposed): a dict with
+    ``n_free``, ``n_lin``, ``soc_dims`` (list), the constraint coefficients of the cone variables
+    as a CSR by constraint ``A_ptr``, ``A_var``, ``A_val``, and their cost ``c`` (length
+    n_free + n_lin + Σ soc_dims; variables ordered free, nonnegative, then each second-order cone
+    as (t, u)). They are appended to ``x`` after the pattern pairs; each cone is one block (the
+    free and the nonnegative variables one block each) whose selector picks its variables, so
+    ``D`` is 1 on them. The block kinds are ``self.kinds``: "psd" for the cliques, then "free",
+    "nonneg", "soc".
     """
 
-    def __init__(self, n, cliques, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val):
+    def __init__(self, n, cliques, A_ptr, A_row, A_col, A_val, b, C_row, C_col, C_val, cones=None):
         self.n = int(n)
         self.m = len(b)
         self.b = np.asarray(b, dtype=np.float64)
@@ -97,11 +136,21 @@ class ChordalSDP:
 
         # Ordered pattern E = ∪ C_k × C_k, column-major: sort by (col, row) via key col*n + row.
         keys = np.unique(np.concatenate(
-            [(c[None, :] * n + c[:, None]).ravel() for c in self.cliques]))
+            [(c[None, :] * n + c[:, None]).ravel() for c in self.cliques])) if self.p else np.zeros(0, np.int64)
         self.keys = keys
-        self.E_row = keys % n
-        self.E_col = keys // n
-        self.nE = len(keys)
+        self.nE_mat = len(keys)
+        cones = cones or {}
+        nf, nl = int(cones.get("n_free", 0)), int(cones.get("n_lin", 0))
+        qd = [int(q) for q in cones.get("soc_dims", [])]
+        if nf < 0 or nl < 0 or any(q < 1 for q in qd):
+            raise OracleError(-1, "cone sizes must be nonnegative and second-order cones non-empty")
+        self.n_cone = nf + nl + sum(qd)
+        # Cone variable j sits after the pattern pairs; as the diagonal pair (n + j, n + j) of a
+        # virtual vertex it keeps the lower-pattern helpers below valid.
+        virt = np.arange(n, n + self.n_cone, dtype=np.int64)
+        self.E_row = np.concatenate([keys % n if n else keys, virt])
+        self.E_col = np.concatenate([keys // n if n else keys, virt])
+        self.nE = self.nE_mat + self.n_cone
 
         # H_k as index arrays: block entry (a, b) of vec(E_k X E_kᵀ) sits at a + b*s and selects
         # X[C_k(a), C_k(b)] (Section III.A, H_k = E_k ⊗ E_k).
@@ -112,6 +161,17 @@ class ChordalSDP:
             bb = np.repeat(np.arange(s), s)       # column index
             self.idx.append(np.searchsorted(keys, c[bb] * n + c[a]))
 
+        # Cone blocks: one selector per cone over the appended variables.
+        self.kinds = ["psd"] * self.p
+        start = self.nE_mat
+        for kind, q in [("free", nf), ("nonneg", nl)] + [("soc", q) for q in qd]:
+            if q == 0:
+                continue
+            self.kinds.append(kind)
+            self.idx.append(np.arange(start, start + q))
+            start += q
+        self.nblk = len(self.kinds)
+
         # D = Σ_k H_kᵀ H_k (Section III.B.1): diagonal, entry = number of cliques covering it.
         D = np.zeros(self.nE)
         for ix in self.idx:
@@ -120,6 +180,10 @@ class ChordalSDP:
 
         # Data in vectorised form: c = vec(C) on E, A = [vec(A_1) ... vec(A_m)]ᵀ on E.
         self.c = self._full_from_lower(C_row, C_col, C_val)
+        if self.n_cone:
+            cc = cones.get("c")
+            if cc is not None:
+                self.c[self.nE_mat:] = np.asarray(cc, dtype=np.float64)
         A_ptr = np.asarray(A_ptr, dtype=np.int64)
         rows, cols, vals = [], [], []
         for i in range(self.m):
@@ -129,6 +193,17 @@ class ChordalSDP:
             cols.append(nz)
             vals.append(v)
             rows.append(np.full(len(nz), i))
+        if self.n_cone:
+            cptr = np.asarray(cones["A_ptr"], dtype=np.int64)
+            cvar = np.asarray(cones["A_var"], dtype=np.int64)
+            cval = np.asarray(cones["A_val"], dtype=np.float64)
+            if np.any(cvar < 0) or np.any(cvar >= self.n_cone):
+                raise OracleError(-1, "cone variable index out of range")
+            for i in range(self.m):
+                sl = slice(cptr[i], cptr[i + 1])
+                cols.append(self.nE_mat + cvar[sl])
+                vals.append(cval[sl])
+                rows.append(np.full(sl.stop - sl.start, i))
         self.A = scipy.sparse.csr_matrix(
             (np.concatenate(vals) if vals else np.zeros(0),
              (np.concatenate(rows) if rows else np.zeros(0, int),
@@ -158,7 +233,8 @@ class ChordalSDP:
         k2 = rows * n + cols
         p1 = np.searchsorted(self.keys, k1)
         p2 = np.searchsorted(self.keys, k2)
-        ok1 = (p1 < self.nE) & (self.keys[np.minimum(p1, self.nE - 1)] == k1)
+        ok1 = (p1 < self.nE_mat) & (self.keys[np.minimum(p1, max(self.nE_mat - 1, 0))] == k1) \
+            if self.nE_mat else np.zeros(len(k1), bool)
         if not np.all(ok1):
             raise OracleError(-2, "a data nonzero lies outside the union of clique blocks")
         full = np.zeros(self.nE)
@@ -183,6 +259,18 @@ class ChordalSDP:
 
     def block_sizes(self):
         return [len(c) for c in self.cliques]
+
+    def block_len(self, k: int) -> int:
+        """Length of block k: s² for a clique (full column-major block), q for a cone."""
+        return len(self.idx[k])
+
+    def project(self, k: int, w: np.ndarray, dual: bool = False) -> np.ndarray:
+        """Projection of block k (Eqs. XkUpdate / zkUpdate): P₊ on a clique block, the cone's own
+        projection (its dual cone's in the dual form) on a cone block."""
+        if self.kinds[k] == "psd":
+            s = len(self.cliques[k])
+            return _vec(proj_psd(_mat(w, s)))
+        return proj_cone(self.kinds[k], w, dual)
 
     @staticmethod
     def block_to_packed(xk: np.ndarray, s: int) -> np.ndarray:
@@ -209,7 +297,7 @@ class ChordalSDP:
     def HT_sum(self, blocks) -> np.ndarray:
         """Σ_k H_kᵀ v_k, accumulating cliques in ascending k from zero (Section III.B.1)."""
         acc = np.zeros(self.nE)
-        for k in range(self.p):
+        for k in range(self.nblk):
             acc[self.idx[k]] += blocks[k]
         return acc
 
@@ -236,7 +324,7 @@ def _norm_blocks(blocks) -> float:
 
 def admm_init(sdp: ChordalSDP, form: str) -> dict:
     """Zero initial guesses (Algorithm 1 / 2 take them as inputs)."""
-    zeros = [np.zeros(len(c) ** 2) for c in sdp.cliques]
+    zeros = [np.zeros(sdp.block_len(k)) for k in range(sdp.nblk)]
     st = dict(form=form, iter=0, x=np.zeros(sdp.nE), y=np.zeros(sdp.m),
               lam=[z.copy() for z in zeros])
     if form == "primal":
@@ -253,20 +341,18 @@ def primal_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     """One pass of Algorithm 1: x-update, clique projections, multipliers, residuals."""
     rinv = 1.0 / rho
     # Eq. (OptCondMinYPrimal): right-hand side Σ H_kᵀ(x_k + ρ⁻¹λ_k) − ρ⁻¹c and b.
-    r = sdp.HT_sum([st["xk"][k] + rinv * st["lam"][k] for k in range(sdp.p)]) - rinv * sdp.c
+    K = range(sdp.nblk)
+    r = sdp.HT_sum([st["xk"][k] + rinv * st["lam"][k] for k in K]) - rinv * sdp.c
     x, y = sdp.kkt_solve(r, sdp.b)
     # Eq. (XkUpdate): x_k = vec P_k[vec⁻¹(H_k x − ρ⁻¹λ_k)].
-    u = [sdp.H(k, x) for k in range(sdp.p)]
-    xk_new = []
-    for k in range(sdp.p):
-        s = len(sdp.cliques[k])
-        xk_new.append(_vec(proj_psd(_mat(u[k] - rinv * st["lam"][k], s))))
+    u = [sdp.H(k, x) for k in K]
+    xk_new = [sdp.project(k, u[k] - rinv * st["lam"][k]) for k in K]
     # Eq. (LambdakUpdate): λ_k += ρ (x_k − H_k x).
-    lam_new = [st["lam"][k] + rho * (xk_new[k] - u[k]) for k in range(sdp.p)]
+    lam_new = [st["lam"][k] + rho * (xk_new[k] - u[k]) for k in K]
     # Residuals (reading of Section III.B's stopping test, see module docstring).
-    pri = _norm_blocks([xk_new[k] - u[k] for k in range(sdp.p)])
+    pri = _norm_blocks([xk_new[k] - u[k] for k in K])
     pri_den = max(_norm_blocks(xk_new), _norm_blocks(u), 1e-12)
-    dres = sdp.HT_sum([xk_new[k] - st["xk"][k] for k in range(sdp.p)])
+    dres = sdp.HT_sum([xk_new[k] - st["xk"][k] for k in K])
     dual_den = max(float(np.linalg.norm(sdp.HT_sum(lam_new))), 1e-12)
     out = dict(st)
     out.update(iter=st["iter"] + 1, x=x, y=y, xk=xk_new, lam=lam_new, r=r, u=u,
@@ -279,23 +365,21 @@ def dual_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     """One pass of Algorithm 2: projections, (y, x), v_k, multipliers, residuals."""
     rinv = 1.0 / rho
     # Eq. (zkUpdate): z_k = vec P_k[vec⁻¹(v_k − ρ⁻¹λ_k)].
-    zk = []
-    for k in range(sdp.p):
-        s = len(sdp.cliques[k])
-        zk.append(_vec(proj_psd(_mat(st["vk"][k] - rinv * st["lam"][k], s))))
+    K = range(sdp.nblk)
+    zk = [sdp.project(k, st["vk"][k] - rinv * st["lam"][k], dual=True) for k in K]
     # Eq. (OptCondMinYDual): right-hand side c − Σ H_kᵀ(z_k + ρ⁻¹λ_k) and −ρ⁻¹b.
-    r = sdp.c - sdp.HT_sum([zk[k] + rinv * st["lam"][k] for k in range(sdp.p)])
+    r = sdp.c - sdp.HT_sum([zk[k] + rinv * st["lam"][k] for k in K])
     x, y = sdp.kkt_solve(r, -(rinv * sdp.b))
     # Eq. (vkEqn): v_k = z_k + ρ⁻¹λ_k + H_k x.
-    u = [sdp.H(k, x) for k in range(sdp.p)]
-    vk_new = [zk[k] + rinv * st["lam"][k] + u[k] for k in range(sdp.p)]
+    u = [sdp.H(k, x) for k in K]
+    vk_new = [zk[k] + rinv * st["lam"][k] + u[k] for k in K]
     # Eq. (DualMultUpdate) with the sign that Eq. (MultUpdateDualSDP) implies: λ_k = −ρ H_k x.
-    lam_new = [-rho * u[k] for k in range(sdp.p)]
+    lam_new = [-rho * u[k] for k in K]
     # The general update of Eq. (MultUpdateDualSDP), kept for the identity check in the tests.
-    lam_general = [st["lam"][k] + rho * (zk[k] - vk_new[k]) for k in range(sdp.p)]
-    pri = _norm_blocks([zk[k] - vk_new[k] for k in range(sdp.p)])
+    lam_general = [st["lam"][k] + rho * (zk[k] - vk_new[k]) for k in K]
+    pri = _norm_blocks([zk[k] - vk_new[k] for k in K])
     pri_den = max(_norm_blocks(zk), _norm_blocks(vk_new), 1e-12)
-    dres = _norm_blocks([vk_new[k] - st["vk"][k] for k in range(sdp.p)])
+    dres = _norm_blocks([vk_new[k] - st["vk"][k] for k in K])
     dual_den = max(_norm_blocks(lam_new), 1e-12)
     out = dict(st)
     out.update(iter=st["iter"] + 1, x=x, y=y, zk=zk, vk=vk_new, lam=lam_new, r=r, u=u,

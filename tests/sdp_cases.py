@@ -152,3 +152,149 @@ def instance_arrays(inst) -> dict:
     """Coordinate arrays of a generated ``SDPInstance``."""
     return dict(n=inst.n, cliques=inst.cliques, A_ptr=inst.A_ptr, A_row=inst.A_row, A_col=inst.A_col,
                 A_val=inst.A_val, b=inst.b, C_row=inst.C_row, C_col=inst.C_col, C_val=inst.C_val)
+
+
+def _empty_matrix_part(n=0) -> dict:
+    z32 = np.zeros(0, np.int32)
+    return dict(n=n, cliques=[], A_row=z32, A_col=z32, A_val=np.zeros(0), C_row=z32, C_col=z32,
+                C_val=np.zeros(0))
+
+
+def random_conic(l=2, d=3, h=2, n_free=3, n_lin=5, soc_dims=(3, 4), m=6, seed=21, density=0.6) -> dict:
+    """A feasible problem over a block-arrow PSD part (none when l = 0) and the other cones: free,
+    nonnegative and second-order variables. Built from interior points x0 (primal) and (y0, z0)
+    (dual; z0 = 0 on the free variables, whose dual cone is {0}), so both have optima and they
+    agree. Returns sdp_setup's arrays plus ``cones`` (the dict the oracle and sdp_setup_conic take)."""
+    rng = np.random.default_rng(seed)
+    soc_dims = [int(q) for q in soc_dims]
+    nc = n_free + n_lin + sum(soc_dims)
+    if l > 0:
+        P = block_arrow_dense_pattern(l, d, h)
+        n = P.shape[0]
+        G = rng.standard_normal((n, n)) / np.sqrt(n)
+        X0 = G @ G.T
+        As = []
+        for _ in range(m):
+            A = rng.standard_normal((n, n)) * (rng.random((n, n)) < density)
+            A = np.tril(A) + np.tril(A, -1).T
+            As.append(A * P)
+        Z = rng.standard_normal((n, n))
+        Z = np.tril(Z, -1)
+        Z = (Z + Z.T) * P
+        Z += np.diag(np.abs(Z).sum(axis=1) + 1.0)
+    Ac = rng.standard_normal((m, nc)) * (rng.random((m, nc)) < density)
+    x0 = np.empty(nc)
+    z0 = np.empty(nc)
+    x0[:n_free] = rng.standard_normal(n_free)
+    z0[:n_free] = 0.0
+    x0[n_free:n_free + n_lin] = rng.uniform(0.5, 1.5, n_lin)
+    z0[n_free:n_free + n_lin] = rng.uniform(0.5, 1.5, n_lin)
+    o = n_free + n_lin
+    for q in soc_dims:
+        for v in (x0, z0):
+            u = rng.standard_normal(q - 1) * 0.5 / np.sqrt(q)
+            v[o] = np.linalg.norm(u) + rng.uniform(0.5, 1.5)
+            v[o + 1:o + q] = u
+        o += q
+    y0 = rng.standard_normal(m)
+    b = Ac @ x0
+    c_cone = Ac.T @ y0 + z0
+    if l > 0:
+        b = b + np.array([float(np.sum(A * X0)) for A in As])
+        C = Z + sum(y * A for y, A in zip(y0, As))
+        C[P & (C == 0)] = 1e-3
+        arrs = problem_from_dense(C, As, b, block_arrow_cliques(l, d, h))
+    else:
+        arrs = _empty_matrix_part()
+        arrs.update(A_ptr=np.zeros(m + 1, np.int64), b=np.asarray(b, np.float64))
+    ptr, var, val = [0], [], []
+    for i in range(m):
+        nz = np.flatnonzero(Ac[i])
+        var.append(nz)
+        val.append(Ac[i, nz])
+        ptr.append(ptr[-1] + len(nz))
+    arrs["cones"] = dict(n_free=n_free, n_lin=n_lin, soc_dims=soc_dims,
+                         A_ptr=np.asarray(ptr, np.int64), A_var=np.concatenate(var).astype(np.int32),
+                         A_val=np.concatenate(val).astype(np.float64), c=c_cone)
+    return arrs
+
+
+def cone_matrix(arrs) -> np.ndarray:
+    """The constraint coefficients of the cone variables as a dense m x n_cone matrix."""
+    cn = arrs["cones"]
+    m = len(arrs["b"])
+    nc = cn["n_free"] + cn["n_lin"] + sum(cn["soc_dims"])
+    M = np.zeros((m, nc))
+    for i in range(m):
+        for t in range(cn["A_ptr"][i], cn["A_ptr"][i + 1]):
+            M[i, cn["A_var"][t]] += cn["A_val"][t]
+    return M
+
+
+def cones_from_dense(Ac: np.ndarray, c, n_free=0, n_lin=0, soc_dims=()) -> dict:
+    ptr, var, val = [0], [], []
+    for i in range(Ac.shape[0]):
+        nz = np.flatnonzero(Ac[i])
+        var.append(nz)
+        val.append(Ac[i, nz])
+        ptr.append(ptr[-1] + len(nz))
+    return dict(n_free=n_free, n_lin=n_lin, soc_dims=list(soc_dims), A_ptr=np.asarray(ptr, np.int64),
+                A_var=np.concatenate(var).astype(np.int32) if var else np.zeros(0, np.int32),
+                A_val=np.concatenate(val).astype(np.float64) if val else np.zeros(0),
+                c=np.asarray(c, np.float64))
+
+
+def lp_as_diagonal_sdp(Ac: np.ndarray, b, c) -> dict:
+    """min cᵀw, Aw = b, w ≥ 0 as an SDP on a diagonal pattern: w_j = X_jj, singleton cliques."""
+    n = Ac.shape[1]
+    As = [np.diag(Ac[i]) for i in range(Ac.shape[0])]
+    d = problem_from_dense(np.diag(np.asarray(c, np.float64)), As, b, [[j] for j in range(n)])
+    d["cliques"] = [np.array([j], np.int32) for j in range(n)]
+    return d
+
+
+def socp_as_arrow_sdp(Ac: np.ndarray, b, c, n_lin: int, soc_dims) -> dict:
+    """A problem over nonnegative and second-order variables as an SDP: w_j ≥ 0 is a 1 x 1 block,
+    and (t, u) ∈ Q^q iff the arrow matrix [[t, uᵀ], [u, t I]] is PSD, imposed on a q x q block
+    by equality constraints (equal diagonal, zero off-diagonal outside the first column)."""
+    n = n_lin + sum(soc_dims)
+    m0 = Ac.shape[0]
+    cost = np.zeros((n, n))
+    rows = [np.zeros((n, n)) for _ in range(m0)]
+    bb = list(np.asarray(b, np.float64))
+    cliques = []
+
+    def put(M, var_pos, coef):
+        i, j = var_pos
+        if i == j:
+            M[i, i] += coef
+        else:
+            M[i, j] += 0.5 * coef
+            M[j, i] += 0.5 * coef
+
+    pos = [(j, j) for j in range(n_lin)]
+    cliques += [[j] for j in range(n_lin)]
+    o = n_lin
+    extra = []
+    for q in soc_dims:
+        pos.append((o, o))
+        pos += [(o + i, o) for i in range(1, q)]
+        cliques.append(list(range(o, o + q)))
+        for i in range(1, q):
+            E = np.zeros((n, n))
+            E[o + i, o + i] = 1.0
+            E[o, o] = -1.0
+            extra.append(E)
+            for k in range(1, i):
+                E = np.zeros((n, n))
+                E[o + i, o + k] = E[o + k, o + i] = 0.5
+                extra.append(E)
+        o += q
+    for v, p in enumerate(pos):
+        put(cost, p, c[v])
+        for i in range(m0):
+            put(rows[i], p, Ac[i, v])
+    As = rows + extra
+    bb += [0.0] * len(extra)
+    d = problem_from_dense(cost, As, bb, cliques)
+    return d
