@@ -89,6 +89,8 @@ typedef struct {
     long long S_lower;     /* S_L   */
     long long nnz_A;       /* stored nonzeros of A on E_L (after merging duplicates) */
     int batch;             /* problems in the handle (1 for sdp_setup, count for sdp_setup_batch) */
+    long long n_cone;      /* variables in non-PSD cones (sdp_setup_conic); they are the last
+                              n_cone entries of nE_lower and positions of S_lower              */
 } sdp_sizes;
 
 /* One problem of a batch: the arguments of sdp_setup, with the same meaning, in a struct. */
@@ -172,6 +174,38 @@ int sdp_batch_layout(sdp_handle h, int* vtx_off, int* row_off, int* clique_off, 
  * iteration. */
 int sdp_batch_results(sdp_handle h, int* iters, int* status, double* eps_p, double* eps_d,
                       double* obj_primal, double* obj_dual);
+
+/* ---- products with other cones (Section V: CDCS accepts products of R^q, the nonnegative
+ * orthant, second-order cones and the PSD cone, and decomposes only the PSD one)
+ * The problem becomes  min <C, X> + c^T x  s.t.  <A_i, X> + a_i^T x = b_i,  X in S^n_+(E, ?),
+ * x in R^{n_free} x R_+^{n_lin} x Q^{q_1} x ... x Q^{q_k}  with Q^q = {(t, u) : ||u|| <= t}.
+ * The cone variables are appended to the pattern entries: the handle's entry vector is E_L
+ * followed by them (sdp_get_maps reports cone variable j as the diagonal pair (n + j, n + j)),
+ * and its packed block vector is the clique blocks followed by one block per cone (all free
+ * variables one block, all nonnegative ones one block, then each second-order cone), each block
+ * the cone's own variables in order, so D = 1 on them and their weight in every inner product is
+ * 1. Each iteration projects these blocks onto their cone (primal form) or its dual cone (dual
+ * form: {0} for the free block, the others are self-dual); the affine step, the multiplier
+ * updates and the residuals are those of the SDP with the longer vectors. */
+typedef struct {
+    int n_free;                 /* free variables (first)                                        */
+    int n_lin;                  /* nonnegative variables (next)                                  */
+    int n_soc;                  /* number of second-order cones (last, in order)                 */
+    const int* soc_dims;        /* [n_soc] their dimensions q_j >= 1 (t first, then u)           */
+    const long long* A_ptr;     /* [m+1] constraint i owns terms A_ptr[i] .. A_ptr[i+1]-1         */
+    const int* A_var;           /* cone variable of each term, 0 <= j < n_cone (duplicates add)  */
+    const double* A_val;        /* coefficient of each term                                      */
+    const double* c;            /* [n_cone] cost of the cone variables (NULL: zero)              */
+} sdp_cones;
+
+/* sdp_setup for a problem with cone variables beside the PSD matrix. `problem` holds the matrix
+ * part as in sdp_setup (n = 0 with p = 0 and no matrix data: no PSD part at all); `cones` may be
+ * NULL (then this is sdp_setup). Host pointers, copied. Not available for batches or
+ * sdp_unrolled_forward / sdp_unrolled_backward (SDP_ERR_UNSUPPORTED there).
+ * Errors: as sdp_setup; SDP_ERR_ARG for negative cone sizes, a second-order cone of dimension
+ * < 1, no variables at all, or a cone variable index out of range. */
+int sdp_setup_conic(const sdp_problem* problem, const sdp_cones* cones, const admm_opts* opts,
+                    sdp_handle* out);
 
 /* Chordal extension of a sparse symmetric pattern (Section II.A: a non-chordal aggregate pattern is
  * first extended to a chordal one; the paper leaves the extension to heuristics) and the maximal

@@ -38,7 +38,7 @@ PRECS = {"fp64": SDP_PROJ_FP64, "fp32": SDP_PROJ_FP32}
 
 # Symbols the header declares (checked by the CPU test suite against the built library).
 EXPORTS = [
-    "sdp_setup", "sdp_setup_batch", "sdp_batch_layout", "sdp_batch_results", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
+    "sdp_setup", "sdp_setup_batch", "sdp_setup_conic", "sdp_batch_layout", "sdp_batch_results", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
@@ -71,7 +71,14 @@ class admm_result(ctypes.Structure):
 class sdp_sizes(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
                 ("max_clique", ctypes.c_int), ("nE_lower", ctypes.c_longlong),
-                ("S_lower", ctypes.c_longlong), ("nnz_A", ctypes.c_longlong), ("batch", ctypes.c_int)]
+                ("S_lower", ctypes.c_longlong), ("nnz_A", ctypes.c_longlong), ("batch", ctypes.c_int),
+                ("n_cone", ctypes.c_longlong)]
+
+
+class sdp_cones(ctypes.Structure):
+    _fields_ = [("n_free", ctypes.c_int), ("n_lin", ctypes.c_int), ("n_soc", ctypes.c_int),
+                ("soc_dims", ctypes.c_void_p), ("A_ptr", ctypes.c_void_p), ("A_var", ctypes.c_void_p),
+                ("A_val", ctypes.c_void_p), ("c", ctypes.c_void_p)]
 
 
 class sdp_problem(ctypes.Structure):
@@ -102,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         "sdp_setup": (_I, [_I, _I, _P, _P, _P, _P, _P, _LL, _P, _P, _P, _LL, _P, _P, _I, _P, _P,
                            ctypes.POINTER(admm_opts), ctypes.POINTER(_P)]),
         "sdp_setup_batch": (_I, [_I, ctypes.POINTER(sdp_problem), ctypes.POINTER(admm_opts), ctypes.POINTER(_P)]),
+        "sdp_setup_conic": (_I, [ctypes.POINTER(sdp_problem), ctypes.POINTER(sdp_cones), ctypes.POINTER(admm_opts),
+                                 ctypes.POINTER(_P)]),
         "sdp_batch_layout": (_I, [_P, _P, _P, _P, _P, _P]),
         "sdp_batch_results": (_I, [_P, _P, _P, _P, _P, _P, _P]),
         "sdp_set_opts": (_I, [_P, ctypes.POINTER(admm_opts)]),
@@ -249,6 +258,31 @@ def sdp_setup_batch(problems, opts=None):
     opts = opts if opts is not None else make_opts()
     h = ctypes.c_void_p()
     _check(lib.sdp_setup_batch(len(keep), arr, ctypes.byref(opts), ctypes.byref(h)), "sdp_setup_batch")
+    return h
+
+
+def _cone_arrays(cones: dict) -> dict:
+    nc = int(cones.get("n_free", 0)) + int(cones.get("n_lin", 0)) + int(np.sum(cones.get("soc_dims", [])))
+    return dict(n_free=int(cones.get("n_free", 0)), n_lin=int(cones.get("n_lin", 0)),
+                soc_dims=_arr(cones.get("soc_dims", []), np.int32), A_ptr=_arr(cones["A_ptr"], np.int64),
+                A_var=_arr(cones["A_var"], np.int32), A_val=_arr(cones["A_val"], np.float64),
+                c=_arr(cones["c"], np.float64) if cones.get("c") is not None else None, n_cone=nc)
+
+
+def sdp_setup_conic(problem: dict, cones: dict | None, opts=None):
+    """A problem with variables in free, nonnegative and second-order cones beside the PSD matrix:
+    ``problem`` has sdp_setup's keyword arguments (n = 0 and cliques = [] for no PSD part),
+    ``cones`` the keys n_free, n_lin, soc_dims, A_ptr, A_var, A_val and c."""
+    lib = load_library()
+    d = _problem_arrays(**{k: v for k, v in problem.items() if k in _PROBLEM_KEYS})
+    pr = _problem_struct(d)
+    cd = _cone_arrays(cones) if cones is not None else None
+    cs = None if cd is None else sdp_cones(cd["n_free"], cd["n_lin"], len(cd["soc_dims"]), _ptr(cd["soc_dims"]),
+                                           _ptr(cd["A_ptr"]), _ptr(cd["A_var"]), _ptr(cd["A_val"]), _ptr(cd["c"]))
+    opts = opts if opts is not None else make_opts()
+    h = ctypes.c_void_p()
+    _check(lib.sdp_setup_conic(ctypes.byref(pr), ctypes.byref(cs) if cs is not None else None,
+                               ctypes.byref(opts), ctypes.byref(h)), "sdp_setup_conic")
     return h
 
 
@@ -493,7 +527,9 @@ class ChordalADMM:
         """``arrays``: one problem (a dict of sdp_setup's keyword arguments) or a list of them (a
         batch, set up with sdp_setup_batch)."""
         self.opts = opts if opts is not None else make_opts()
-        if isinstance(arrays, dict):
+        if isinstance(arrays, dict) and arrays.get("cones") is not None:
+            self.h = sdp_setup_conic(arrays, arrays["cones"], self.opts)
+        elif isinstance(arrays, dict):
             self.h = sdp_setup(arrays["n"], arrays["A_ptr"], arrays["A_row"], arrays["A_col"],
                                arrays["A_val"], arrays["b"], arrays["C_row"], arrays["C_col"],
                                arrays["C_val"], cliques=arrays["cliques"], opts=self.opts)

@@ -72,6 +72,7 @@ struct sdp_ctx {
     int device = 0;
     admm_opts opts{};
     int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0, ninst = 1;
+    int n_cone = 0;               // non-PSD cone variables (last n_cone entries and positions)
     long long vstore_elems = 0;   // sum over cliques of N_k^2
     long long nnz = 0;
     // host copies needed after setup
@@ -522,7 +523,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     CK(cudaGetDevice(&h->device));
     h->opts = *opts;
     h->n = hp.n; h->m = hp.m; h->p = hp.p; h->smax = hp.smax;
-    h->nEL = hp.nEL; h->SL = hp.SL; h->nnz = hp.nnz; h->ninst = hp.ninst;
+    h->nEL = hp.nEL; h->SL = hp.SL; h->nnz = hp.nnz; h->ninst = hp.ninst; h->n_cone = hp.n_cone;
     h->pat_row = hp.pat_row; h->pat_col = hp.pat_col;
     h->blk_off = hp.blk_off; h->gather_idx = hp.gather_idx;
     h->inst_vtx = hp.inst_vtx; h->inst_row = hp.inst_row; h->inst_cl = hp.inst_cl;
@@ -572,6 +573,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     P.ent_ctas = (int)S.ent.size();
     P.heavy_ctas = (int)S.heavy.size();
     P.n_heavy = (int)hp.heavy.size();
+    P.ncs = (int)hp.cone_lo.size();
     std::vector<int> blk_inst(hp.p);
     for (int q = 0; q < hp.ninst; ++q)
         for (int k = hp.inst_cl[q]; k < hp.inst_cl[q + 1]; ++k) blk_inst[k] = q;
@@ -648,6 +650,9 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(sell_val, hp.sell_val);
     UP(Linv, hp.Linv);
     UP(LinvT, hp.LinvT);
+    UP(cone_lo, hp.cone_lo);
+    UP(cone_hi, hp.cone_hi);
+    UP(cone_kind, hp.cone_kind);
 #undef UP
     if ((rc = h->dalloc(&P.inst_res, (size_t)hp.ninst * 4))) return rc;
     if ((rc = h->dalloc(&P.inst_conv, (size_t)hp.ninst))) return rc;
@@ -662,7 +667,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
     if ((rc = h->dalloc(&P.vk, hp.SL))) return rc;
     if ((rc = h->dalloc(&P.tpart, row_cap))) return rc;
-    if ((rc = h->dalloc(&P.part_blk, (size_t)hp.p * 4))) return rc;
+    if ((rc = h->dalloc(&P.part_blk, ((size_t)hp.p + P.ncs) * 4))) return rc;
     if ((rc = h->dalloc(&P.part_ent, std::max<size_t>(P.ent_ctas + P.heavy_ctas, pos_cap) * 8))) return rc;
     if ((rc = h->dalloc(&P.part_obj, std::max(col_cap, S.col.size())))) return rc;
     if ((rc = h->dalloc(&P.ctrl, 1))) return rc;
@@ -705,13 +710,34 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         HostProblem hp;
         std::string err;
         rc = cadmm::build_host_problem(n, m, A_ptr, A_row, A_col, A_val, b, C_nnz, C_row, C_col, C_val,
-                                       pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, hp, err);
+                                       pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, nullptr, hp, err);
         if (rc) return set_err(rc, err);
         return create_handle(hp, opts, out);
     } catch (const std::bad_alloc&) {
         return set_err(SDP_ERR_ARG, "host out of memory");
     } catch (...) {
         return set_err(SDP_ERR_ARG, "unexpected exception in sdp_setup");
+    }
+}
+
+int sdp_setup_conic(const sdp_problem* pr, const sdp_cones* cones, const admm_opts* opts, sdp_handle* out) {
+    try {
+        if (!out) return set_err(SDP_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (!pr) return set_err(SDP_ERR_ARG, "problem is NULL");
+        int rc = check_opts(opts);
+        if (rc) return rc;
+        HostProblem hp;
+        std::string err;
+        rc = cadmm::build_host_problem(pr->n, pr->m, pr->A_ptr, pr->A_row, pr->A_col, pr->A_val, pr->b,
+                                       pr->C_nnz, pr->C_row, pr->C_col, pr->C_val, pr->pat_nnz, pr->pat_row,
+                                       pr->pat_col, pr->p, pr->clique_ptr, pr->clique_vtx, cones, hp, err);
+        if (rc) return set_err(rc, err);
+        return create_handle(hp, opts, out);
+    } catch (const std::bad_alloc&) {
+        return set_err(SDP_ERR_ARG, "host out of memory");
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_setup_conic");
     }
 }
 
@@ -857,6 +883,7 @@ int sdp_get_sizes(sdp_handle h, sdp_sizes* out) {
     out->n = h->n; out->m = h->m; out->p = h->p; out->max_clique = h->smax;
     out->nE_lower = h->nEL; out->S_lower = h->SL; out->nnz_A = h->nnz;
     out->batch = h->ninst;
+    out->n_cone = h->n_cone;
     return SDP_OK;
 }
 
@@ -1085,6 +1112,7 @@ int sdp_unrolled_forward(sdp_handle h, int T, int ckpt_every, double* x_out, voi
     if (h->opts.form != SDP_PRIMAL || h->opts.prec != SDP_PROJ_FP64)
         return set_err(SDP_ERR_ARG, "unrolled differentiation needs form SDP_PRIMAL and prec SDP_PROJ_FP64");
     if (h->smax > 32) return set_err(SDP_ERR_UNSUPPORTED, "unrolled differentiation takes cliques of order <= 32");
+    if (h->n_cone > 0) return set_err(SDP_ERR_UNSUPPORTED, "unrolled differentiation takes PSD cones only");
     CK(cudaSetDevice(h->device));
     cudaStream_t st = as_stream(cuda_stream);
     try {

@@ -67,7 +67,7 @@ __device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int 
     Ctrl* C = P.ctrl;
     double v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (form == SDP_PRIMAL) {
-        for (int k = threadIdx.x; k < P.p; k += blockDim.x) {
+        for (int k = threadIdx.x; k < P.p + P.ncs; k += blockDim.x) {   // cliques, then cone segments
             v[0] += P.part_blk[k * 4 + 0];
             v[1] += P.part_blk[k * 4 + 1];
             v[2] += P.part_blk[k * 4 + 2];
@@ -713,6 +713,89 @@ ProjArgs proj_args_for(const IterPtrs& P, double rho) {
     return a;
 }
 
+// ---------------------------------------------------------------- non-PSD cone blocks
+// Section V: besides the PSD cone, CDCS accepts R^q (free), the nonnegative orthant and
+// second-order cones Q^q = {(t, u) : ||u|| <= t}, and does not decompose them. Their variables are
+// one block per cone after the clique blocks; each block is projected onto its cone in the primal
+// form (Eq. XkUpdate) and onto the dual cone in the dual form (Eq. zkUpdate): {0} for R^q, the
+// others are self-dual. The second-order projection is the point itself inside the cone, zero
+// inside its polar cone, else ((t + ||u||) / 2) (1, u / ||u||). One CTA per segment; the epilogue
+// is that of the PSD projections, with weight 1 on every position.
+constexpr int kConeThreads = 256;
+
+template <int MODE>
+__device__ __forceinline__ double cone_w(const IterPtrs& P, int q, double rinv) {
+    if (MODE == PROJ_PRIMAL) return __dsub_rn(P.x[P.gather_idx[q]], __dmul_rn(rinv, P.lam[q]));
+    return __dsub_rn(P.vk[q], __dmul_rn(rinv, P.lam[q]));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kConeThreads) k_project_cones(IterPtrs P, double rho, double rinv) {
+    __shared__ double red[33 * 3];
+    pdl_wait();
+    if (P.ctrl->done) return;
+    const int sg = blockIdx.x;
+    const int lo = P.cone_lo[sg], hi = P.cone_hi[sg], kind = P.cone_kind[sg];
+    double t_out = 0.0, f = 1.0;          // second-order cone: t -> t_out, u -> f u
+    if (kind == kConeSoc) {
+        double ss[1] = {0.0};
+        for (int q = lo + 1 + (int)threadIdx.x; q < hi; q += blockDim.x) {
+            const double w = cone_w<MODE>(P, q, rinv);
+            ss[0] = fma(w, w, ss[0]);
+        }
+        block_sum<1>(ss, red);
+        const double t = cone_w<MODE>(P, lo, rinv);
+        const double nu = sqrt(ss[0]);
+        if (nu <= t) {
+            t_out = t;
+        } else if (nu <= -t) {
+            f = 0.0;
+        } else {
+            t_out = 0.5 * (t + nu);
+            f = t_out / nu;
+        }
+    }
+    pdl_trigger();
+    double pv[3] = {0.0, 0.0, 0.0};
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL) xk_new = (P.ctrl->iter & 1) ? P.xk[0] : P.xk[1];
+    for (int q = lo + (int)threadIdx.x; q < hi; q += blockDim.x) {
+        const double w = cone_w<MODE>(P, q, rinv);
+        double xv;
+        if (kind == kConeFree) xv = (MODE == PROJ_PRIMAL) ? w : 0.0;
+        else if (kind == kConeNonneg) xv = w > 0.0 ? w : 0.0;
+        else xv = (q == lo) ? t_out : f * w;
+        if (MODE == PROJ_PRIMAL) {
+            const double u = P.x[P.gather_idx[q]];
+            const double d = xv - u;
+            xk_new[q] = xv;
+            P.lam[q] = P.lam[q] + rho * d;                     // Eq. LambdakUpdate
+            pv[0] += d * d;
+            pv[1] += xv * xv;
+            pv[2] += u * u;
+        } else {
+            P.xk[0][q] = xv;                                   // z_k
+        }
+    }
+    if (MODE == PROJ_PRIMAL) {
+        block_sum<3>(pv, red);
+        if (threadIdx.x == 0) {
+            double* part = P.part_blk + (size_t)(P.p + sg) * 4;
+            part[0] = pv[0];
+            part[1] = pv[1];
+            part[2] = pv[2];
+            part[3] = 0.0;
+        }
+    }
+}
+
+cudaError_t launch_project_cones(const IterPtrs& P, int mode, double rho, cudaStream_t st) {
+    if (P.ncs <= 0) return cudaSuccess;
+    if (mode == PROJ_PRIMAL)
+        return launch_pdl(k_project_cones<PROJ_PRIMAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
+    return launch_pdl(k_project_cones<PROJ_DUAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
+}
+
 // All runs of the projection plan, largest cliques first.
 cudaError_t launch_project_plan(const ProjArgs& a, const IterPtrs& P, const ProjPlan& plan, int mode, int prec,
                                 cudaStream_t st) {
@@ -773,7 +856,7 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
 }  // namespace
 
 int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form) {
-    return (form == SDP_PRIMAL ? 5 : 6) + plan.runs + (P.ninst > 1 ? 1 : 0);
+    return (form == SDP_PRIMAL ? 5 : 6) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
 }
 
 int phase_count(const IterPtrs& P, int form) { return (form == SDP_PRIMAL ? 6 : 7) + (P.ninst > 1 ? 1 : 0); }
@@ -797,6 +880,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_project_plan(a, P, plan, PROJ_PRIMAL, prec, st)) != cudaSuccess) return e;
+        if ((e = launch_project_cones(P, PROJ_PRIMAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
                             rho, 0)) != cudaSuccess)
@@ -805,6 +889,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         a.out = P.xk[0];
         mk.mark();
         if ((e = launch_project_plan(a, P, plan, PROJ_DUAL, prec, st)) != cudaSuccess) return e;
+        if ((e = launch_project_cones(P, PROJ_DUAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
                             rinv)) != cudaSuccess)

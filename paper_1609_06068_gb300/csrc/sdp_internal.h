@@ -60,7 +60,16 @@ struct HostProblem {
     std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
                                                                       // E_L entries, positions, rows, slices
     std::vector<long long> mblk_off;                        // offsets of the L^-1 blocks
+    // Non-PSD cones: n_cone variables after the E_L entries (and after the clique blocks in the
+    // packed vector), projected in segments [cone_lo, cone_hi) of kind kCone*.
+    int n_cone = 0;
+    std::vector<int> cone_lo, cone_hi, cone_kind;
 };
+
+// Kinds of cone segments, and the longest free / nonnegative segment (their projections are
+// elementwise, so long runs are cut; a second-order cone is always one segment).
+constexpr int kConeFree = 0, kConeNonneg = 1, kConeSoc = 2;
+constexpr int kConeChunk = 4096;
 
 // Chordal extension of the symmetric pattern given by nnz (row, col) coordinates and the maximal
 // cliques of the extension (chordal.cpp). fill = lower pairs added.
@@ -76,7 +85,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                        const double* A_val, const double* b, long long C_nnz, const int* C_row,
                        const int* C_col, const double* C_val, long long pat_nnz,
                        const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
-                       const int* clique_vtx, HostProblem& hp, std::string& err);
+                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err);
 
 // ---------------------------------------------------------------- kernel launch parameters
 
@@ -168,7 +177,9 @@ struct IterPtrs {
     void* vstore;         // eigenvector blocks for warm starts (projection precision)
     const long long* voff;
     double* tpart;        // [row_chunks]
-    double* part_blk;     // [p * 4]
+    double* part_blk;     // [(p + ncs) * 4]: cliques, then cone segments
+    // non-PSD cone segments (single problems only): positions [cone_lo, cone_hi), kind kCone*
+    int ncs; const int* cone_lo; const int* cone_hi; const int* cone_kind;
     double* part_ent;     // [max(ent_ctas + heavy_ctas, pos_ctas) * 8]
     double* part_obj;     // [col_chunks]
     Ctrl* ctrl;

@@ -72,9 +72,25 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                        const double* A_val, const double* b, long long C_nnz, const int* C_row,
                        const int* C_col, const double* C_val, long long pat_nnz,
                        const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
-                       const int* clique_vtx, HostProblem& hp, std::string& err) {
-    if (n <= 0 || m < 1 || p < 0 || !A_ptr || !b || (p > 0 && (!clique_ptr || !clique_vtx)))
-        return fail(err, SDP_ERR_ARG, "n, m must be positive, p >= 0, and A_ptr, b, cliques non-NULL");
+                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err) {
+    // ---- cone variables (free, nonnegative, second-order), appended after the pattern entries
+    long long nc = 0;
+    if (cones) {
+        if (cones->n_free < 0 || cones->n_lin < 0 || cones->n_soc < 0 || (cones->n_soc > 0 && !cones->soc_dims))
+            return fail(err, SDP_ERR_ARG, "cone sizes must be nonnegative and soc_dims non-NULL");
+        nc = (long long)cones->n_free + cones->n_lin;
+        for (int j = 0; j < cones->n_soc; ++j) {
+            if (cones->soc_dims[j] < 1) return fail(err, SDP_ERR_ARG, "second-order cone of dimension < 1");
+            nc += cones->soc_dims[j];
+        }
+        if (nc >= (1LL << 30)) return fail(err, SDP_ERR_UNSUPPORTED, "too many cone variables");
+        if (m >= 1 && !cones->A_ptr) return fail(err, SDP_ERR_ARG, "cones->A_ptr is NULL");
+    }
+    const bool has_psd = n > 0;
+    if (n < 0 || (!has_psd && (nc == 0 || p != 0)))
+        return fail(err, SDP_ERR_ARG, "n must be positive (n = 0 needs cone variables and p = 0)");
+    if (m < 1 || p < 0 || !A_ptr || !b || (p > 0 && (!clique_ptr || !clique_vtx)))
+        return fail(err, SDP_ERR_ARG, "m must be positive, p >= 0, and A_ptr, b, cliques non-NULL");
     if (m > SDP_MAX_CONSTRAINTS)
         return fail(err, SDP_ERR_UNSUPPORTED, "m exceeds SDP_MAX_CONSTRAINTS");
     if (C_nnz < 0 || pat_nnz < 0 || (C_nnz > 0 && (!C_row || !C_col || !C_val)) ||
@@ -85,11 +101,22 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         if (A_ptr[i + 1] < A_ptr[i]) return fail(err, SDP_ERR_ARG, "A_ptr must be non-decreasing");
     if (A_ptr[m] > 0 && (!A_row || !A_col || !A_val))
         return fail(err, SDP_ERR_ARG, "A coordinate arrays are NULL");
+    if (nc > 0) {
+        const long long* cp = cones->A_ptr;
+        if (cp[0] != 0) return fail(err, SDP_ERR_ARG, "cones->A_ptr[0] must be 0");
+        for (int i = 0; i < m; ++i)
+            if (cp[i + 1] < cp[i]) return fail(err, SDP_ERR_ARG, "cones->A_ptr must be non-decreasing");
+        if (cp[m] > 0 && (!cones->A_var || !cones->A_val))
+            return fail(err, SDP_ERR_ARG, "cone coefficient arrays are NULL");
+        for (long long t = 0; t < cp[m]; ++t)
+            if (cones->A_var[t] < 0 || cones->A_var[t] >= nc)
+                return fail(err, SDP_ERR_ARG, "cone variable index out of range");
+    }
 
     // p == 0: the cliques are those of a chordal extension of the aggregate pattern (C, every A_i
     // and the extra pattern coordinates).
     std::vector<int> ext_ptr, ext_vtx;
-    if (p == 0) {
+    if (p == 0 && has_psd) {
         if (C_nnz > 0 && (!C_row || !C_col)) return fail(err, SDP_ERR_ARG, "bad C arrays");
         const long long annz = A_ptr[m];
         std::vector<int> rr, cc;
@@ -140,6 +167,9 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         hp.smax = std::max(hp.smax, s);
     }
     hp.blk_off[p] = (int)SL;
+    const long long SL_mat = SL;      // clique blocks; the cone blocks follow
+    SL += nc;
+    if (SL >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "packed block length >= 2^31");
     hp.SL = (int)SL;
     hp.voff.resize(p + 1);
     hp.voff[0] = 0;
@@ -156,8 +186,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
 
     // ---- lower pattern E_L = union of lower clique pairs, column-major (key = col*n + row).
     // Packed positions are enumerated in storage order: clique, column b, rows a >= b.
-    std::vector<long long> pos_key(SL);
-    hp.pos_w.resize(SL);
+    std::vector<long long> pos_key(SL_mat);
+    hp.pos_w.assign(SL, 1);
     {
         long long q = 0;
         for (int k = 0; k < p; ++k) {
@@ -173,27 +203,52 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     std::vector<long long> keys(pos_key);
     std::sort(keys.begin(), keys.end());
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    if ((long long)keys.size() >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
-    const int nEL = (int)keys.size();
+    if ((long long)keys.size() + nc >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
+    const int nEL_mat = (int)keys.size();
+    const int nEL = nEL_mat + (int)nc;    // cone variable j is entry nEL_mat + j
     hp.nEL = nEL;
+    hp.n_cone = (int)nc;
     EntryIndex index;
-    index.build(keys, n);
+    index.build(keys, std::max(n, 1));
     hp.pat_row.resize(nEL);
     hp.pat_col.resize(nEL);
-    hp.ew.resize(nEL);
-    for (int e = 0; e < nEL; ++e) {
+    hp.ew.assign(nEL, 1);
+    for (int e = 0; e < nEL_mat; ++e) {
         hp.pat_row[e] = (int)(keys[e] % n);
         hp.pat_col[e] = (int)(keys[e] / n);
         hp.ew[e] = hp.pat_row[e] == hp.pat_col[e] ? 1 : 2;
     }
+    for (int j = 0; j < (int)nc; ++j) hp.pat_row[nEL_mat + j] = hp.pat_col[nEL_mat + j] = n + j;
 
-    // ---- H_k as a gather map, and its transpose as a CSR scatter map with ascending k.
+    // ---- H_k as a gather map, and its transpose as a CSR scatter map with ascending k. The
+    // block of a cone selects its own variables.
     hp.gather_idx.resize(SL);
     std::vector<int> cnt(nEL + 1, 0);
     parallel_for(p, [&](int k) {
         for (long long q = hp.blk_off[k]; q < hp.blk_off[k] + (long long)hp.blk_size[k] * (hp.blk_size[k] + 1) / 2; ++q)
             hp.gather_idx[q] = (int)index.find(pos_key[q] % n, pos_key[q] / n);
     });
+    for (long long j = 0; j < nc; ++j) hp.gather_idx[SL_mat + j] = nEL_mat + (int)j;
+    if (nc > 0) {
+        // Projection segments: every second-order cone is one; the free and the nonnegative
+        // variables are cut into pieces of at most kConeChunk (their projections are elementwise).
+        auto add = [&](long long lo, long long len, int kind, bool whole) {
+            for (long long a = 0; a < len; a += whole ? len : kConeChunk) {
+                hp.cone_lo.push_back((int)(SL_mat + lo + a));
+                hp.cone_hi.push_back((int)(SL_mat + lo + std::min(len, a + (whole ? len : kConeChunk))));
+                hp.cone_kind.push_back(kind);
+            }
+        };
+        long long o = 0;
+        add(o, cones->n_free, kConeFree, false);
+        o += cones->n_free;
+        add(o, cones->n_lin, kConeNonneg, false);
+        o += cones->n_lin;
+        for (int j = 0; j < cones->n_soc; ++j) {
+            add(o, cones->soc_dims[j], kConeSoc, true);
+            o += cones->soc_dims[j];
+        }
+    }
     for (long long q = 0; q < SL; ++q) cnt[hp.gather_idx[q] + 1]++;
     hp.sc_ptr.resize(nEL + 1);
     hp.sc_ptr[0] = 0;
@@ -228,6 +283,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         }
         hp.c[e] += C_val[t];
     }
+    if (nc > 0 && cones->c)
+        for (long long j = 0; j < nc; ++j) hp.c[nEL_mat + j] = cones->c[j];
     for (long long t = 0; t < pat_nnz; ++t) {
         const long long r = pat_row[t], cc = pat_col[t];
         if (r < 0 || r >= n || cc < 0 || cc >= n || r < cc)
@@ -258,6 +315,9 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             }
             row.emplace_back((int)e, A_val[t]);
         }
+        if (nc > 0)
+            for (long long t = cones->A_ptr[i]; t < cones->A_ptr[i + 1]; ++t)
+                row.emplace_back(nEL_mat + cones->A_var[t], cones->A_val[t]);
         std::sort(row.begin(), row.end(),
                   [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
         size_t w = 0;
@@ -481,7 +541,7 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
                     rcs[q] = build_host_problem(pr.n, pr.m, pr.A_ptr, pr.A_row, pr.A_col, pr.A_val, pr.b,
                                                 pr.C_nnz, pr.C_row, pr.C_col, pr.C_val, pr.pat_nnz,
                                                 pr.pat_row, pr.pat_col, pr.p, pr.clique_ptr, pr.clique_vtx,
-                                                parts[q], errs[q]);
+                                                nullptr, parts[q], errs[q]);
                 }
             });
         for (auto& x : th) x.join();

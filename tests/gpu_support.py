@@ -19,11 +19,15 @@ def require_gpu():
 
 def make_oracle(arrs) -> orc.ChordalSDP:
     return orc.ChordalSDP(arrs["n"], arrs["cliques"], arrs["A_ptr"], arrs["A_row"], arrs["A_col"],
-                          arrs["A_val"], arrs["b"], arrs["C_row"], arrs["C_col"], arrs["C_val"])
+                          arrs["A_val"], arrs["b"], arrs["C_row"], arrs["C_col"], arrs["C_val"],
+                          cones=arrs.get("cones"))
 
 
 def blocks_to_packed(sdp: orc.ChordalSDP, blocks) -> np.ndarray:
-    return np.concatenate([sdp.block_to_packed(b, len(c)) for b, c in zip(blocks, sdp.cliques)])
+    """Oracle blocks in the packed layout: clique blocks as lower triangles, cone blocks as they are."""
+    out = [sdp.block_to_packed(b, len(c)) for b, c in zip(blocks[:sdp.p], sdp.cliques)]
+    out += [np.asarray(b, dtype=np.float64) for b in blocks[sdp.p:]]
+    return np.concatenate(out) if out else np.zeros(0)
 
 
 def packed_to_blocks(sdp: orc.ChordalSDP, packed: np.ndarray):
@@ -33,6 +37,10 @@ def packed_to_blocks(sdp: orc.ChordalSDP, packed: np.ndarray):
         n = s * (s + 1) // 2
         out.append(sdp.packed_to_block(packed[pos:pos + n], s))
         pos += n
+    for k in range(sdp.p, sdp.nblk):
+        q = sdp.block_len(k)
+        out.append(np.array(packed[pos:pos + q], dtype=np.float64))
+        pos += q
     return out
 
 

@@ -148,3 +148,31 @@ def test_chordal_extension_matches_oracle():
         want, wfill = ch.chordal_extension(n, rows, cols)
         assert gfill == wfill
         assert [list(map(int, c)) for c in got] == [list(c) for c in want]
+
+
+def _conic_rc(arrs, **cone_changes):
+    cones = dict(arrs["cones"], **cone_changes)
+    try:
+        cadmm.sdp_setup_conic(arrs, cones, cadmm.make_opts())
+    except cadmm.SDPError as exc:
+        return exc.code, str(exc)
+    return cadmm.SDP_OK, ""
+
+
+def test_setup_conic_validates_cones_on_host(lib):
+    arrs = sdp_cases.random_conic(l=2, d=2, h=1, n_free=2, n_lin=3, soc_dims=(3,), m=4, seed=5)
+    assert _conic_rc(arrs, n_free=-1)[0] == cadmm.SDP_ERR_ARG
+    rc, msg = _conic_rc(arrs, soc_dims=[0])
+    assert rc == cadmm.SDP_ERR_ARG and "dimension" in msg
+    bad_var = np.array(arrs["cones"]["A_var"])
+    bad_var[0] = 2 + 3 + 3
+    rc, msg = _conic_rc(arrs, A_var=bad_var)
+    assert rc == cadmm.SDP_ERR_ARG and "out of range" in msg
+    bad_ptr = np.array(arrs["cones"]["A_ptr"])
+    bad_ptr[0] = 1
+    assert _conic_rc(arrs, A_ptr=bad_ptr)[0] == cadmm.SDP_ERR_ARG
+    # no PSD part and no cone variables at all
+    empty = sdp_cases._empty_matrix_part()
+    empty.update(A_ptr=np.zeros(2, np.int64), b=np.ones(1))
+    empty["cones"] = sdp_cases.cones_from_dense(np.zeros((1, 0)), np.zeros(0))
+    assert _conic_rc(empty)[0] == cadmm.SDP_ERR_ARG
