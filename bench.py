@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", choices=["m", "l", "d"], default=None,
                     help="the paper's block-arrow sweep varying m, l or d (one JSON line per point)")
+    ap.add_argument("--conic", action="store_true",
+                    help="time the conic workload (the n = 1020 SDP plus nonnegative and second-order cones)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="for profilers: set up, run this many iterations from a reset, exit (no JSON)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
@@ -565,10 +567,82 @@ def run_sweep(args):
         print(json.dumps(out), flush=True)
 
 
+def run_conic(args):
+    """Section V's product cones: the n = 1020 block-arrow SDP with 10^6 nonnegative variables and
+    10^5 second-order cones of dimension 10 (sdp_inputs.CONIC). Dual form, FP32 eigensolves:
+    iterations per second over fixed-length runs (CUDA events), a solve to 1e-4, the per-kernel
+    phase times, and the cone projection's HBM roofline (algorithmic bytes per position: read v_k
+    and lambda_k, write z_k, 24 B; the second-order cones' norm pass re-reads u from cache)."""
+    import torch
+
+    import paper_1609_06068_gb300 as cadmm
+    from sdp_inputs import CONIC, config_instance, conic_extension
+
+    cadmm.load_library()
+    torch.cuda.set_device(0)
+    cfg = CONIC
+    inst = config_instance(cfg["base"])
+    ext = conic_extension(inst, cfg["n_free"], cfg["n_lin"], [cfg["soc_dim"]] * cfg["soc_count"],
+                          cfg["per_var"], cfg["seed"])
+    arrs = _arrays(inst)
+    arrs["b"] = ext["b"]
+    arrs["cones"] = ext["cones"]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    out = dict(workload=cfg["name"], form=cfg["form"], prec=cfg["prec"], rho=cfg["rho"])
+    stream = torch.cuda.current_stream()
+    for label, a in (("sdp_only", dict(arrs, b=inst.b, cones=None)), ("conic", arrs)):
+        t0 = time.perf_counter()
+        opts = cadmm.make_opts(rho=cfg["rho"], tol=0.0, max_iter=cfg["iters"], form=cfg["form"], prec=cfg["prec"])
+        s = cadmm.ChordalADMM(a, opts)
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        s.reset()
+        s.iterate(cfg["iters"])                                       # warm-up, graph capture
+        ms = []
+        for _ in range(max(3, min(args.steps, 10))):
+            s.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.iterate(cfg["iters"])
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        phases = cadmm.sdp_time_phases(s.h, reps=20, stream=stream)
+        s.set_opts(tol=1e-4, max_iter=2000)
+        s.reset()
+        r = s.solve()
+        entry = dict(setup_ms=setup_ms, iters_per_s=cfg["iters"] / (med * 1e-3), ms_per_iter=med / cfg["iters"],
+                     n_cone=s.sizes["n_cone"], nE_lower=s.sizes["nE_lower"], S_lower=s.sizes["S_lower"],
+                     nnz_A=s.sizes["nnz_A"], phases_ms=phases,
+                     solve_to_tol=dict(tol=1e-4, iters=r["iters"], status=r["status"], obj_dual=r["obj_dual"],
+                                        obj_primal=r["obj_primal"], eps_p=r["eps_p"], eps_d=r["eps_d"]))
+        if label == "conic" and "project_cones" in phases:
+            nbytes = 24.0 * s.sizes["n_cone"]
+            gbs = nbytes / (phases["project_cones"] * 1e-3) / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            entry["roofline_project_cones"] = dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s",
+                                                   frac=gbs / peak, bytes_per_launch=nbytes,
+                                                   peak_source="of measured (MEASURED_PEAKS.json hbm_gbs)"
+                                                   if "hbm_gbs" in peaks else "of fallback")
+        out[label] = entry
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.oracle_worker:
         oracle_worker(args)
+        return
+    if args.conic:
+        run_conic(args)
         return
     if args.sweep is not None:
         run_sweep(args)

@@ -653,6 +653,8 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(cone_lo, hp.cone_lo);
     UP(cone_hi, hp.cone_hi);
     UP(cone_kind, hp.cone_kind);
+    UP(soc_pos, hp.soc_pos);
+    UP(soc_q, hp.soc_q);
 #undef UP
     if ((rc = h->dalloc(&P.inst_res, (size_t)hp.ninst * 4))) return rc;
     if ((rc = h->dalloc(&P.inst_conv, (size_t)hp.ninst))) return rc;
@@ -1224,7 +1226,7 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
 
 const char* sdp_phase_name(sdp_handle h, int i) {
     if (!h) return nullptr;
-    return cadmm::phase_name(h->opts.form, h->ninst > 1, i);
+    return cadmm::phase_name(h->opts.form, h->ninst > 1, h->P.ncs > 0, i);
 }
 
 void sdp_free(sdp_handle h) { delete h; }

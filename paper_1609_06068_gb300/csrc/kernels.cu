@@ -719,14 +719,50 @@ ProjArgs proj_args_for(const IterPtrs& P, double rho) {
 // one block per cone after the clique blocks; each block is projected onto its cone in the primal
 // form (Eq. XkUpdate) and onto the dual cone in the dual form (Eq. zkUpdate): {0} for R^q, the
 // others are self-dual. The second-order projection is the point itself inside the cone, zero
-// inside its polar cone, else ((t + ||u||) / 2) (1, u / ||u||). One CTA per segment; the epilogue
-// is that of the PSD projections, with weight 1 on every position.
+// inside its polar cone, else ((t + ||u||) / 2) (1, u / ||u||). One CTA per segment: a range of
+// free or nonnegative positions, one large second-order cone, or up to kSmallSocPerCta cones of
+// dimension <= kSmallSoc taken by one thread each. GB300 issues FP64 at a small fraction of its
+// FP32 rate, so a small cone is not spread over lanes: a lane per element would repeat the norm's
+// reduction, the square root and the division for every lane of the cone. The thread reads its
+// cone twice (the norm, then the result; the second pass hits L1). The epilogue is that of the
+// PSD projections, with weight 1 on every position.
 constexpr int kConeThreads = 256;
 
 template <int MODE>
 __device__ __forceinline__ double cone_w(const IterPtrs& P, int q, double rinv) {
     if (MODE == PROJ_PRIMAL) return __dsub_rn(P.x[P.gather_idx[q]], __dmul_rn(rinv, P.lam[q]));
     return __dsub_rn(P.vk[q], __dmul_rn(rinv, P.lam[q]));
+}
+
+// Second-order projection factors from t and ||u||: t -> t_out, u -> f u.
+__device__ __forceinline__ void soc_factors(double t, double nu, double& t_out, double& f) {
+    if (nu <= t) {
+        t_out = t;
+        f = 1.0;
+    } else if (nu <= -t) {
+        t_out = 0.0;
+        f = 0.0;
+    } else {
+        t_out = 0.5 * (t + nu);
+        f = t_out / nu;
+    }
+}
+
+// Epilogue of one projected position xv (weight 1), shared by every cone kind.
+template <int MODE>
+__device__ __forceinline__ void cone_store(const IterPtrs& P, double* xk_new, int q, double xv, double rho,
+                                           double (&pv)[3]) {
+    if (MODE == PROJ_PRIMAL) {
+        const double u = P.x[P.gather_idx[q]];
+        const double d = xv - u;
+        xk_new[q] = xv;
+        P.lam[q] = P.lam[q] + rho * d;                         // Eq. LambdakUpdate
+        pv[0] += d * d;
+        pv[1] += xv * xv;
+        pv[2] += u * u;
+    } else {
+        P.xk[0][q] = xv;                                       // z_k
+    }
 }
 
 template <int MODE>
@@ -736,47 +772,45 @@ __global__ void __launch_bounds__(kConeThreads) k_project_cones(IterPtrs P, doub
     if (P.ctrl->done) return;
     const int sg = blockIdx.x;
     const int lo = P.cone_lo[sg], hi = P.cone_hi[sg], kind = P.cone_kind[sg];
-    double t_out = 0.0, f = 1.0;          // second-order cone: t -> t_out, u -> f u
-    if (kind == kConeSoc) {
-        double ss[1] = {0.0};
-        for (int q = lo + 1 + (int)threadIdx.x; q < hi; q += blockDim.x) {
-            const double w = cone_w<MODE>(P, q, rinv);
-            ss[0] = fma(w, w, ss[0]);
-        }
-        block_sum<1>(ss, red);
-        const double t = cone_w<MODE>(P, lo, rinv);
-        const double nu = sqrt(ss[0]);
-        if (nu <= t) {
-            t_out = t;
-        } else if (nu <= -t) {
-            f = 0.0;
-        } else {
-            t_out = 0.5 * (t + nu);
-            f = t_out / nu;
-        }
-    }
-    pdl_trigger();
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (P.ctrl->iter & 1) ? P.xk[0] : P.xk[1];
-    for (int q = lo + (int)threadIdx.x; q < hi; q += blockDim.x) {
-        const double w = cone_w<MODE>(P, q, rinv);
-        double xv;
-        if (kind == kConeFree) xv = (MODE == PROJ_PRIMAL) ? w : 0.0;
-        else if (kind == kConeNonneg) xv = w > 0.0 ? w : 0.0;
-        else xv = (q == lo) ? t_out : f * w;
-        if (MODE == PROJ_PRIMAL) {
-            const double u = P.x[P.gather_idx[q]];
-            const double d = xv - u;
-            xk_new[q] = xv;
-            P.lam[q] = P.lam[q] + rho * d;                     // Eq. LambdakUpdate
-            pv[0] += d * d;
-            pv[1] += xv * xv;
-            pv[2] += u * u;
-        } else {
-            P.xk[0][q] = xv;                                   // z_k
+    if (kind == kConeSocSmall) {
+        const int c = lo + (int)threadIdx.x;
+        if (c < hi) {
+            const int p0 = P.soc_pos[c], qd = P.soc_q[c];
+            const double t = cone_w<MODE>(P, p0, rinv);
+            double ss = 0.0;
+            for (int j = 1; j < qd; ++j) {
+                const double w = cone_w<MODE>(P, p0 + j, rinv);
+                ss = fma(w, w, ss);
+            }
+            double t_out, f;
+            soc_factors(t, sqrt(ss), t_out, f);
+            cone_store<MODE>(P, xk_new, p0, t_out, rho, pv);
+            for (int j = 1; j < qd; ++j) cone_store<MODE>(P, xk_new, p0 + j, f * cone_w<MODE>(P, p0 + j, rinv), rho, pv);
+        }
+    } else {
+        double t_out = 0.0, f = 1.0;          // large second-order cone: t -> t_out, u -> f u
+        if (kind == kConeSoc) {
+            double ss[1] = {0.0};
+            for (int q = lo + 1 + (int)threadIdx.x; q < hi; q += blockDim.x) {
+                const double w = cone_w<MODE>(P, q, rinv);
+                ss[0] = fma(w, w, ss[0]);
+            }
+            block_sum<1>(ss, red);
+            soc_factors(cone_w<MODE>(P, lo, rinv), sqrt(ss[0]), t_out, f);
+        }
+        for (int q = lo + (int)threadIdx.x; q < hi; q += blockDim.x) {
+            const double w = cone_w<MODE>(P, q, rinv);
+            double xv;
+            if (kind == kConeFree) xv = (MODE == PROJ_PRIMAL) ? w : 0.0;
+            else if (kind == kConeNonneg) xv = w > 0.0 ? w : 0.0;
+            else xv = (q == lo) ? t_out : f * w;
+            cone_store<MODE>(P, xk_new, q, xv, rho, pv);
         }
     }
+    pdl_trigger();
     if (MODE == PROJ_PRIMAL) {
         block_sum<3>(pv, red);
         if (threadIdx.x == 0) {
@@ -859,7 +893,9 @@ int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form) {
     return (form == SDP_PRIMAL ? 5 : 6) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
 }
 
-int phase_count(const IterPtrs& P, int form) { return (form == SDP_PRIMAL ? 6 : 7) + (P.ninst > 1 ? 1 : 0); }
+int phase_count(const IterPtrs& P, int form) {
+    return (form == SDP_PRIMAL ? 6 : 7) + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
+}
 
 cudaError_t iteration_prepare() {
     // y / z / t staged in shared memory: up to SDP_MAX_CONSTRAINTS doubles.
@@ -880,6 +916,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_project_plan(a, P, plan, PROJ_PRIMAL, prec, st)) != cudaSuccess) return e;
+        if (P.ncs > 0) mk.mark();
         if ((e = launch_project_cones(P, PROJ_PRIMAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
@@ -889,6 +926,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         a.out = P.xk[0];
         mk.mark();
         if ((e = launch_project_plan(a, P, plan, PROJ_DUAL, prec, st)) != cudaSuccess) return e;
+        if (P.ncs > 0) mk.mark();
         if ((e = launch_project_cones(P, PROJ_DUAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
         if ((e = launch_pdl(k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
@@ -905,19 +943,18 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
     return cudaGetLastError();
 }
 
-const char* phase_name(int form, bool batch, int i) {
-    static const char* primal[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols",
-                                   "project_primal", "scatter_primal+finalize", "finalize_batch"};
-    static const char* dual[] = {"project_dual", "scatter_dual", "spmv_rows", "tri_lower",
+const char* phase_name(int form, bool batch, bool cones, int i) {
+    static const char* primal[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols", "project_primal",
+                                   "project_cones", "scatter_primal+finalize", "finalize_batch"};
+    static const char* dual[] = {"project_dual", "project_cones", "scatter_dual", "spmv_rows", "tri_lower",
                                  "tri_upper", "spmv_cols", "update_dual+finalize", "finalize_batch"};
-    static const char* primal_b[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols",
-                                     "project_primal", "scatter_primal", "finalize_batch"};
-    static const char* dual_b[] = {"project_dual", "scatter_dual", "spmv_rows", "tri_lower",
-                                   "tri_upper", "spmv_cols", "update_dual", "finalize_batch"};
-    const int n = (form == SDP_PRIMAL ? 6 : 7) + (batch ? 1 : 0);
+    const char** list = form == SDP_PRIMAL ? primal : dual;
+    const int cone_at = form == SDP_PRIMAL ? 5 : 1;
+    const int n = (form == SDP_PRIMAL ? 6 : 7) + (cones ? 1 : 0) + (batch ? 1 : 0);
     if (i < 0 || i >= n) return nullptr;
-    if (form == SDP_PRIMAL) return batch ? primal_b[i] : primal[i];
-    return batch ? dual_b[i] : dual[i];
+    if (!cones && i >= cone_at) ++i;                    // no cone phase: skip its slot
+    if (batch && i == (form == SDP_PRIMAL ? 6 : 7)) return form == SDP_PRIMAL ? "scatter_primal" : "update_dual";
+    return list[i];
 }
 
 int resident_ctas(int kernel, size_t smem) {

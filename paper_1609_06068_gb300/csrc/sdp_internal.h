@@ -64,12 +64,17 @@ struct HostProblem {
     // packed vector), projected in segments [cone_lo, cone_hi) of kind kCone*.
     int n_cone = 0;
     std::vector<int> cone_lo, cone_hi, cone_kind;
+    std::vector<int> soc_pos, soc_q;            // small second-order cones: first position, dimension
 };
 
 // Kinds of cone segments, and the longest free / nonnegative segment (their projections are
 // elementwise, so long runs are cut; a second-order cone is always one segment).
-constexpr int kConeFree = 0, kConeNonneg = 1, kConeSoc = 2;
+// kConeSocSmall segments hold up to kSmallSocPerCta second-order cones of dimension <= kSmallSoc
+// (one thread each; the segment's range indexes soc_pos / soc_q), the other kinds a position range.
+constexpr int kConeFree = 0, kConeNonneg = 1, kConeSoc = 2, kConeSocSmall = 3;
 constexpr int kConeChunk = 4096;
+constexpr int kSmallSoc = 32;
+constexpr int kSmallSocPerCta = 256;
 
 // Chordal extension of the symmetric pattern given by nnz (row, col) coordinates and the maximal
 // cliques of the extension (chordal.cpp). fill = lower pairs added.
@@ -180,6 +185,7 @@ struct IterPtrs {
     double* part_blk;     // [(p + ncs) * 4]: cliques, then cone segments
     // non-PSD cone segments (single problems only): positions [cone_lo, cone_hi), kind kCone*
     int ncs; const int* cone_lo; const int* cone_hi; const int* cone_kind;
+    const int* soc_pos; const int* soc_q;         // small second-order cones (kConeSocSmall segments)
     double* part_ent;     // [max(ent_ctas + heavy_ctas, pos_ctas) * 8]
     double* part_obj;     // [col_chunks]
     Ctrl* ctrl;
@@ -236,7 +242,7 @@ cudaError_t launch_vstore_identity(const IterPtrs& P, int prec, cudaStream_t st)
 cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,
                              cudaStream_t st, cudaEvent_t* ev = nullptr);
 int phase_count(const IterPtrs& P, int form);
-const char* phase_name(int form, bool batch, int i);
+const char* phase_name(int form, bool batch, bool cones, int i);
 cudaError_t launch_primal_rebuild_r(const IterPtrs& P, double rho, cudaStream_t st);
 cudaError_t launch_gather(const IterPtrs& P, const double* x, double* blocks, cudaStream_t st);
 cudaError_t launch_scatter(const IterPtrs& P, const double* blocks, double* out, cudaStream_t st);

@@ -244,9 +244,22 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         o += cones->n_free;
         add(o, cones->n_lin, kConeNonneg, false);
         o += cones->n_lin;
+        // second-order cones: dimension <= kSmallSoc in groups (a warp each), larger ones alone
         for (int j = 0; j < cones->n_soc; ++j) {
-            add(o, cones->soc_dims[j], kConeSoc, true);
-            o += cones->soc_dims[j];
+            const int q = cones->soc_dims[j];
+            if (q <= kSmallSoc) {
+                hp.soc_pos.push_back((int)(SL_mat + o));
+                hp.soc_q.push_back(q);
+            } else {
+                add(o, q, kConeSoc, true);
+            }
+            o += q;
+        }
+        const int ns = (int)hp.soc_pos.size();
+        for (int a = 0; a < ns; a += kSmallSocPerCta) {
+            hp.cone_lo.push_back(a);
+            hp.cone_hi.push_back(std::min(ns, a + kSmallSocPerCta));
+            hp.cone_kind.push_back(kConeSocSmall);
         }
     }
     for (long long q = 0; q < SL; ++q) cnt[hp.gather_idx[q] + 1]++;

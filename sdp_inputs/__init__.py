@@ -10,6 +10,8 @@ from .blockarrow import (  # noqa: F401
     config_instance,
     config_shapes,
     CONFIGS,
+    CONIC,
+    conic_extension,
     SWEEPS,
     SWEEP_MAX_ITER,
     SWEEP_TOL,

@@ -221,3 +221,65 @@ def config_instance(config: int, instance: int = 0, **overrides) -> SDPInstance:
     params.update(overrides)
     return block_arrow_instance(seed=config_seed(config, instance),
                                 meta=dict(config=config, instance=instance), **params)
+
+
+# A conic workload (Section V: CDCS also accepts free, nonnegative and second-order variables,
+# which are not decomposed): the n = 1020 block-arrow SDP with 10^6 nonnegative variables and
+# 10^5 second-order cones of dimension 10 added, each cone variable in 2 random constraints.
+CONIC = dict(name="blockarrow_l100_d10_h20_m200+lin1e6+soc1e5x10", base=1, n_free=0, n_lin=1_000_000,
+             soc_count=100_000, soc_dim=10, per_var=2, seed=7000, rho=0.02, form="dual", prec="fp32",
+             iters=200)
+
+
+def conic_extension(inst: SDPInstance, n_free: int, n_lin: int, soc_dims, per_var: int, seed: int) -> dict:
+    """Variables in the other cones added to the SDP ``inst``: returns the new right-hand side
+    ``b`` and the ``cones`` dict (n_free, n_lin, soc_dims, A_ptr, A_var, A_val, c).
+
+    Each cone variable gets N(0,1) coefficients in ``per_var`` distinct random constraints. The
+    primal point x0 is interior (free: N(0,1); nonnegative: U(0.5, 1.5); second-order: u ~
+    N(0, 1/q), t = ‖u‖ + U(0.5, 1.5)) and so is the dual slack z0 (0 on the free variables, whose
+    dual cone is {0}); ``b += A_cone x0`` and ``c_cone = A_coneᵀ y0 + z0`` keep (X0, x0) primal and
+    (y0, Z0, z0) dual feasible."""
+    soc_dims = np.asarray(soc_dims, dtype=np.int64)
+    m = len(inst.b)
+    nc = int(n_free + n_lin + soc_dims.sum())
+    ss = np.random.SeedSequence(seed).spawn(4)
+    rng_a, rng_x, rng_z, rng_r = (np.random.default_rng(s) for s in ss)
+    k = min(per_var, m)
+    # distinct rows per variable: uniform draws, rows with a repeat drawn again
+    rows = rng_r.integers(0, m, size=(nc, k))
+    while k > 1:
+        srt = np.sort(rows, axis=1)
+        bad = np.flatnonzero((np.diff(srt, axis=1) == 0).any(axis=1))
+        if len(bad) == 0:
+            break
+        rows[bad] = rng_r.integers(0, m, size=(len(bad), k))
+    vals = rng_a.standard_normal((nc, k))
+    starts = n_free + n_lin + np.concatenate([[0], np.cumsum(soc_dims)[:-1]]).astype(np.int64)
+
+    def interior(rng, zero_free):
+        v = np.empty(nc)
+        v[:n_free] = 0.0 if zero_free else rng.standard_normal(n_free)
+        v[n_free:n_free + n_lin] = rng.uniform(0.5, 1.5, n_lin)
+        for q in np.unique(soc_dims):                      # cones grouped by dimension
+            st = starts[soc_dims == q]
+            u = rng.standard_normal((len(st), q - 1)) / math.sqrt(q)
+            v[st] = np.linalg.norm(u, axis=1) + rng.uniform(0.5, 1.5, len(st))
+            v[st[:, None] + np.arange(1, q)[None, :]] = u
+        return v
+
+    x0 = interior(rng_x, False)
+    z0 = interior(rng_z, True)
+    var = np.repeat(np.arange(nc), k)
+    row = rows.ravel()
+    val = vals.ravel()
+    order = np.lexsort((var, row))
+    row, var, val = row[order], var[order], val[order]
+    A_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(A_ptr, row + 1, 1)
+    A_ptr = np.cumsum(A_ptr)
+    b = inst.b + np.bincount(row, weights=val * x0[var], minlength=m)
+    c = np.bincount(var, weights=val * inst.y0[row], minlength=nc) + z0
+    cones = dict(n_free=int(n_free), n_lin=int(n_lin), soc_dims=soc_dims.astype(np.int32), A_ptr=A_ptr,
+                 A_var=var.astype(np.int32), A_val=val, c=c)
+    return dict(b=b, cones=cones, x0=x0, z0=z0)

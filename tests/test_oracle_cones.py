@@ -223,3 +223,28 @@ def test_planted_identity_as_free_dual_projection_is_caught(monkeypatch):
     monkeypatch.setattr(orc, "proj_cone", wrong)
     with pytest.raises(AssertionError):
         test_free_block_matches_the_split_problem("dual")
+
+
+def test_conic_extension_keeps_both_points_feasible():
+    """The conic workload's inputs: (X0, x0) satisfies the new constraints, x0 lies inside its
+    cones, and c_cone − A_coneᵀ y0 = z0 lies inside the dual cones (0 on the free variables)."""
+    from sdp_inputs import config_instance, conic_extension
+    inst = config_instance(0)
+    qd = [3, 1, 5]
+    ext = conic_extension(inst, 2, 4, qd, 2, 11)
+    cn = ext["cones"]
+    m, nc = len(inst.b), 2 + 4 + sum(qd)
+    Ac = np.zeros((m, nc))
+    for i in range(m):
+        for t in range(cn["A_ptr"][i], cn["A_ptr"][i + 1]):
+            Ac[i, cn["A_var"][t]] += cn["A_val"][t]
+    assert np.all((Ac != 0).sum(axis=0) == 2)                       # two constraints per variable
+    np.testing.assert_allclose(ext["b"] - inst.b, Ac @ ext["x0"], rtol=0, atol=1e-12)
+    z = cn["c"] - Ac.T @ inst.y0
+    np.testing.assert_allclose(z, ext["z0"], rtol=0, atol=1e-12)
+    assert np.all(z[:2] == 0.0) and np.all(z[2:6] > 0) and np.all(ext["x0"][2:6] > 0)
+    o = 6
+    for q in qd:
+        for v in (ext["x0"], z):
+            assert np.linalg.norm(v[o + 1:o + q]) < v[o]
+        o += q
