@@ -60,10 +60,36 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
     __syncthreads();
 }
 
+// The same sum for a CTA of exactly NT threads, transposed: every thread parks its K values in
+// shared memory (value-major, buf holds K * NT + K doubles), then warp k adds value k's NT
+// partials (NT / 32 per lane in order, then the shuffle tree). GB300 issues FP64 adds at a small
+// fraction of its FP32 rate, so this matters: a shuffle tree in every warp for every value issues
+// K * 5 adds per warp plus a second tree, this issues K * (NT / 32 + 5) adds in all.
+template <int K, int NT>
+__device__ __forceinline__ void block_sum_t(double (&v)[K], double* buf) {
+    static_assert(K <= NT / 32, "one warp per value");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) buf[k * NT + tid] = v[k];
+    __syncthreads();
+    if (warp < K) {
+        const double* col = buf + warp * NT + lane;
+        double s = col[0];
+#pragma unroll
+        for (int j = 1; j < NT / 32; ++j) s += col[32 * j];
+        s = warp_sum(s);
+        if (lane == 0) buf[K * NT + warp] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = buf[K * NT + k];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- residuals and stop test
 // Run by one whole CTA (the last to finish the iteration's final kernel).
 __device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int n_part) {
-    __shared__ double red[33 * 7];
+    __shared__ double red[7 * kEntThreads + 7];     // callers run kEntThreads threads
     Ctrl* C = P.ctrl;
     double v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (form == SDP_PRIMAL) {
@@ -82,11 +108,19 @@ __device__ void finalize_iteration(const IterPtrs& P, int form, double rho, int 
     }
     for (int q = threadIdx.x; q < P.col_chunks; q += blockDim.x) v[5] += P.part_obj[q];
     for (int i = threadIdx.x; i < P.m; i += blockDim.x) v[6] = fma(P.b[i], P.y[i], v[6]);
-    block_sum<7>(v, red);
-    if (threadIdx.x != 0) return;
-    double eps_p, eps_d, obj_p, obj_d;
-    eps_p = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-12);
-    eps_d = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-12);
+    block_sum_t<7, kEntThreads>(v, red);
+    if (threadIdx.x >= 32) return;
+    // The five square roots in lanes 0-4 and the two ratios in lanes 0-1 at once (each is a
+    // chain of dependent FP64 operations; in one thread they would run one after another).
+    const int lane = threadIdx.x;
+    const double sq = sqrt(lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : lane == 3 ? v[3] : v[4]);
+    const double q0 = __shfl_sync(0xffffffffu, sq, 0), q1 = __shfl_sync(0xffffffffu, sq, 1);
+    const double q2 = __shfl_sync(0xffffffffu, sq, 2), q3 = __shfl_sync(0xffffffffu, sq, 3);
+    const double q4 = __shfl_sync(0xffffffffu, sq, 4);
+    const double ratio = lane == 0 ? q0 / fmax(fmax(q1, q2), 1e-12) : rho * q3 / fmax(q4, 1e-12);
+    const double eps_p = __shfl_sync(0xffffffffu, ratio, 0), eps_d = __shfl_sync(0xffffffffu, ratio, 1);
+    if (lane != 0) return;
+    double obj_p, obj_d;
     if (form == SDP_PRIMAL) {
         obj_p = v[5];
         obj_d = -rho * v[6];
@@ -258,7 +292,7 @@ __device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int
 // lanes' sums meet in a fixed shuffle tree (deterministic; equal to the ascending sum up to
 // rounding, where a sequential sum over thousands of cliques would serialize the whole warp).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, double rho, int use_current) {
-    __shared__ double red[33 * 2];
+    __shared__ double red[2 * kEntThreads + 2];
     pdl_wait();
     if (P.ctrl->done) return;
     const bool odd = (P.ctrl->iter & 1) != 0;
@@ -322,7 +356,7 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
     }
     if (use_current) return;
     pdl_trigger();
-    block_sum<2>(v, red);
+    block_sum_t<2, kEntThreads>(v, red);
     if (threadIdx.x == 0) {
         P.part_ent[blockIdx.x * 8 + 0] = v[0];
         P.part_ent[blockIdx.x * 8 + 1] = v[1];
@@ -575,7 +609,7 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols_split(IterPtrs P) {
 // v_k = z_k + rho^-1 lambda_k + H_k x (Eq. vkEqn), lambda_k = -rho H_k x (Eq. DualMultUpdate with
 // the sign Eq. MultUpdateDualSDP implies), and the residual sums; the last CTA finalizes.
 __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double rho, double rinv) {
-    __shared__ double red[33 * 5];
+    __shared__ double red[5 * kEntThreads + 5];
     pdl_wait();
     if (P.ctrl->done) return;
     const Sched sc = P.pos_sched[blockIdx.x];
@@ -636,7 +670,7 @@ __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double 
         }
     }
     pdl_trigger();
-    block_sum<5>(v, red);
+    block_sum_t<5, kEntThreads>(v, red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) P.part_ent[blockIdx.x * 8 + k] = v[k];
