@@ -82,3 +82,39 @@ def test_thirty_iterations_track_oracle(form):
         r = s.iterate(30)
         assert r["iters"] == 30
         compare_state(s.state(), sdp, st, tol=1e-9)
+
+
+@pytest.mark.parametrize("name,rho", [("small", 0.7), ("config1", 0.02), ("cones", 0.5)])
+def test_primal_multipliers_reproduce_dual_blocks(name, rho):
+    """Section IV's primal/dual correspondence on the GPU (the derivation and its CPU pin are in
+    tests/test_oracle_scaling.py): the primal form at penalty 1/ρ, started from the state matched
+    to the dual form's iterates 0..2 at penalty ρ, returns the dual form's z_k as its λ_k and
+    ρ(x'_{k−2} − 2x'_{k−1}) as its x at every later iteration."""
+    torch, cadmm = require_gpu()
+    if name == "small":
+        arrs = sdp_cases.random_block_arrow(l=3, d=3, h=2, m=5, seed=4)
+    elif name == "config1":
+        arrs = sdp_cases.instance_arrays(config_instance(1))
+    else:
+        arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=4, soc_dims=(3, 1, 40), m=6, seed=21)
+    K = 12
+    with setup_handle(cadmm, arrs, form="dual", rho=rho, tol=0.0) as d:
+        xs, zs = [np.zeros(d.sizes["nE_lower"])], [np.zeros(d.sizes["S_lower"])]
+        for _ in range(K):
+            d.iterate(1)
+            st = d.state()
+            xs.append(st["x"])
+            zs.append(st["blk_a"])
+        gidx = cadmm.sdp_get_maps(d.h)["gather_idx"]
+    with setup_handle(cadmm, arrs, form="primal", rho=1.0 / rho, tol=0.0) as p:
+        x = rho * (xs[0] - 2.0 * xs[1])
+        cadmm.sdp_set_state(p.h, x=x, y=np.zeros(len(arrs["b"])), blk_a=x[gidx] + rho * (zs[2] - zs[1]),
+                            blk_b=zs[2])
+        g_lam = g_x = 0.0
+        for k in range(3, K + 1):
+            p.iterate(1)
+            st = p.state()
+            g_lam = max(g_lam, float(np.max(np.abs(st["blk_b"] - zs[k])) / max(np.max(np.abs(zs[k])), 1.0)))
+            xr = rho * (xs[k - 2] - 2.0 * xs[k - 1])
+            g_x = max(g_x, float(np.max(np.abs(st["x"] - xr)) / max(np.max(np.abs(xr)), 1.0)))
+    assert g_lam <= 1e-9 and g_x <= 1e-9, (g_lam, g_x)
