@@ -257,6 +257,10 @@ int sdp_get_state(sdp_handle h, double* x, double* y, double* blk_a, double* blk
 int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* blk_a,
                   const double* blk_b, const double* blk_c);
 
+/* Diagnostic: the Jacobi sweeps each clique's eigensolver took in the handle's last iteration
+ * (host array [p], in clique order; 0 for a clique the iteration skipped). Synchronous. */
+int sdp_proj_sweeps(sdp_handle h, int* sweeps);
+
 /* The index maps built by sdp_setup (host outputs, any may be NULL): the lower pattern E_L as
  * (pat_row, pat_col) [nE_lower], the packed block offsets blk_off [p+1], and gather_idx [S_L]:
  * for every packed block position, the E_L index it reads (H_k as an index map). */

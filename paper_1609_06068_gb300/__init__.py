@@ -43,7 +43,7 @@ EXPORTS = [
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
     "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_set_cost",
-    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_free",
+    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_proj_sweeps", "sdp_free",
     "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "sdp_chordal_cliques": (_I, [_I, _LL, _P, _P, _P, _P, _P, _P, _P, _I, _LL]),
         "sdp_set_cost": (_I, [_P, _P, _P]),
         "sdp_set_rhs": (_I, [_P, _P, _P]),
+        "sdp_proj_sweeps": (_I, [_P, _P]),
         "sdp_unrolled_forward": (_I, [_P, _I, _I, _P, _P]),
         "sdp_unrolled_backward": (_I, [_P, _P, _P, _P, _P]),
         "sdp_free": (None, [_P]),
@@ -361,6 +362,13 @@ def sdp_get_state(h) -> dict:
 def sdp_set_state(h, x=None, y=None, blk_a=None, blk_b=None, blk_c=None):
     arrs = [None if v is None else _arr(v, np.float64) for v in (x, y, blk_a, blk_b, blk_c)]
     _check(load_library().sdp_set_state(h, *(_ptr(a) for a in arrs)), "sdp_set_state")
+
+
+def sdp_proj_sweeps(h) -> np.ndarray:
+    """Jacobi sweeps per clique in the handle's last iteration (diagnostic)."""
+    out = np.zeros(sdp_get_sizes(h)["p"], np.int32)
+    _check(load_library().sdp_proj_sweeps(h, _ptr(out)), "sdp_proj_sweeps")
+    return out
 
 
 def sdp_get_maps(h) -> dict:

@@ -906,6 +906,16 @@ int sdp_get_state(sdp_handle h, double* x, double* y, double* blk_a, double* blk
     return SDP_OK;
 }
 
+int sdp_proj_sweeps(sdp_handle h, int* sweeps) {
+    if (!h || !sweeps) return set_err(SDP_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    std::vector<double> part((size_t)h->p * 4);
+    if (h->p > 0) CK(cudaMemcpy(part.data(), h->P.part_blk, part.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < h->p; ++k) sweeps[k] = (int)part[(size_t)k * 4 + 3];
+    return SDP_OK;
+}
+
 int sdp_set_state(sdp_handle h, const double* x, const double* y, const double* blk_a,
                   const double* blk_b, const double* blk_c) {
     if (!h) return set_err(SDP_ERR_ARG, "NULL handle");

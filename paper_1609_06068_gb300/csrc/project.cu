@@ -548,13 +548,19 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
     for (int q = tid; q < NP * NP; q += NT) s_partner[q] = (unsigned char)rr_partner(q % NP, q / NP, N);
 
-    // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s
+    // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s. Each thread reads its
+    // entries once, all loads in flight, and keeps them until the scale is known.
+    constexpr int KQ = NP * NP / (32 * NW);
+    double wv[KQ];
     double wmax = 0.0;
-    for (int q = tid; q < s * s; q += NT) {
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+        const int q = tid + k * NT;
         const int ra = q % s, cb = q / s;
-        if (ra < cb) continue;
-        wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv)));
+        wv[k] = (q < s * s && ra >= cb) ? load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv) : 0.0;
     }
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) wmax = fmax(wmax, fabs(wv[k]));
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
     for (int q = tid; q < NP * NP; q += NT) {
@@ -562,12 +568,15 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         if (i >= s || j >= s) Ws[i * LD + j] = 0.f;
         if (warm) Vs[i * LD + j] = (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
     }
-    for (int q = tid; q < s * s; q += NT) {
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+        const int q = tid + k * NT;
         const int ra = q % s, cb = q / s;
-        if (ra < cb) continue;
-        const float wt = (float)ldexp(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv), -e2);
-        Ws[ra * LD + cb] = wt;
-        Ws[cb * LD + ra] = wt;
+        if (q < s * s && ra >= cb) {
+            const float wt = (float)ldexp(wv[k], -e2);
+            Ws[ra * LD + cb] = wt;
+            Ws[cb * LD + ra] = wt;
+        }
     }
     __syncthreads();
 
@@ -854,22 +863,44 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
     const bool warm = act && a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = (act && a.vstore != nullptr) ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
 
-    // ---- W scaled by 2^-e2 (exact) into the segment's tile, both triangles, zero padding
+    // ---- W scaled by 2^-e2 (exact) into the segment's tile, both triangles, zero padding. Up to
+    // 16 rows the lane reads its column once, all loads in flight, and keeps it until the scale is
+    // known; 32 doubles per lane would spill, so NR = 32 reads the column twice.
+    constexpr int KW = NR <= 16 ? NR : 1;
+    double wc[KW];
     double wmax = 0.0;
-    if (c < s)
-        for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
+    if constexpr (NR <= 16) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            wc[r] = (r >= c && r < s) ? load_w<MODE>(a, off, packed_pos(r, c, s), rinv) : 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) wmax = fmax(wmax, fabs(wc[r]));
+    } else {
+        if (c < s)
+            for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
+    }
     wmax = seg_maxd<NR>(wmax);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
     const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
 #pragma unroll
     for (int r = 0; r < NR; ++r) Ws[r * LD + c] = 0.f;
     __syncwarp();
-    if (c < s)
-        for (int r = c; r < s; ++r) {
-            const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
-            Ws[r * LD + c] = wt;
-            Ws[c * LD + r] = wt;
-        }
+    if constexpr (NR <= 16) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r >= c && r < s) {
+                const float wt = (float)(wc[r] * down);
+                Ws[r * LD + c] = wt;
+                Ws[c * LD + r] = wt;
+            }
+    } else {
+        if (c < s)
+            for (int r = c; r < s; ++r) {
+                const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
+                Ws[r * LD + c] = wt;
+                Ws[c * LD + r] = wt;
+            }
+    }
     __syncwarp();
 
     // ---- sigma = 2 ||W||_F and the initial columns: G = B (cold) or B V_prev (warm)

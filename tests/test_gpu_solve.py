@@ -182,3 +182,15 @@ def test_non_chordal_pattern_via_chordal_extension(form):
     assert abs(r["iters"] - ref["iters"]) <= 1
     assert abs(r[key] - ref[key]) <= 1e-6 * abs(ref[key])
     assert abs(r[key] - ref_dense[key]) <= 1e-4 * abs(ref_dense[key])
+
+
+def test_projection_sweep_diagnostic(cfg0):
+    """sdp_proj_sweeps: per clique, the Jacobi sweeps of the last iteration (FP32 one-sided
+    eigensolver: at least one sweep, at most its cap of 20)."""
+    torch, cadmm = require_gpu()
+    arrs, sdp, _ = cfg0
+    with setup_handle(cadmm, arrs, form="dual", prec="fp32", rho=1.0, tol=0.0) as s:
+        s.iterate(20)
+        sw = cadmm.sdp_proj_sweeps(s.h)
+    assert sw.shape == (sdp.p,)
+    assert sw.min() >= 1 and sw.max() <= 20
