@@ -595,6 +595,15 @@ def run_conic(args):
         pass
     out = dict(workload=cfg["name"], form=cfg["form"], prec=cfg["prec"], rho=cfg["rho"])
     stream = torch.cuda.current_stream()
+    if args.profile_iters > 0:
+        # a short, fixed sequence of launches for a profiler: reset, then K iterations
+        opts = cadmm.make_opts(rho=cfg["rho"], tol=0.0, max_iter=args.profile_iters, form=cfg["form"],
+                               prec=cfg["prec"])
+        with cadmm.ChordalADMM(arrs, opts) as s:
+            s.reset()
+            s.iterate(args.profile_iters)
+            torch.cuda.synchronize()
+        return
     for label, a in (("sdp_only", dict(arrs, b=inst.b, cones=None)), ("conic", arrs)):
         t0 = time.perf_counter()
         opts = cadmm.make_opts(rho=cfg["rho"], tol=0.0, max_iter=cfg["iters"], form=cfg["form"], prec=cfg["prec"])

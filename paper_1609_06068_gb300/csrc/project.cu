@@ -593,16 +593,24 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     const float sigma = 2.f * sqrtf(sq[0]);
     float g[CPL][kOSRows];
     if (warm) {
+        // G = B V_prev, summed over m in order for every entry; each V_prev entry is read once per
+        // lane and each W entry once per warp (a broadcast)
 #pragma unroll
         for (int h = 0; h < CPL; ++h)
 #pragma unroll
-            for (int k = 0; k < kOSRows; ++k) {
-                const int r = r0 + k, c = lane + 32 * h;
-                float acc = sigma * Vs[r * LD + c];
+            for (int k = 0; k < kOSRows; ++k) g[h][k] = sigma * Vs[(r0 + k) * LD + lane + 32 * h];
 #pragma unroll 4
-                for (int m = 0; m < NP; ++m) acc = fmaf(Ws[r * LD + m], Vs[m * LD + c], acc);
-                g[h][k] = acc;
+        for (int m = 0; m < NP; ++m) {
+            float vm[CPL];
+#pragma unroll
+            for (int h = 0; h < CPL; ++h) vm[h] = Vs[m * LD + lane + 32 * h];
+#pragma unroll
+            for (int k = 0; k < kOSRows; ++k) {
+                const float wrm = Ws[(r0 + k) * LD + m];
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) g[h][k] = fmaf(wrm, vm[h], g[h][k]);
             }
+        }
     } else {
 #pragma unroll
         for (int h = 0; h < CPL; ++h)
@@ -740,15 +748,18 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         s_gam[0][0][c] = mu > 0.f ? 1.f / mu : 0.f;
     }
     __syncthreads();
+    // V into Ws, and V diag(max(lambda, 0)) into Vs (the warm-start buffer is free now)
 #pragma unroll
     for (int h = 0; h < CPL; ++h) {
         const int c = lane + 32 * h;
         const float inv = s_gam[0][0][c];
+        const float dc = dp[c];
 #pragma unroll
         for (int k = 0; k < kOSRows; ++k) {
             const int r = r0 + k;
             const float v = inv > 0.f ? g[h][k] * inv : (r == c ? 1.f : 0.f);
             Ws[r * LD + c] = v;
+            Vs[r * LD + c] = v * dc;
             if (vglob != nullptr && c < N && r < N) vglob[r * N + c] = v;
         }
     }
@@ -763,7 +774,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
         float acc = 0.f;
-        for (int i = 0; i < N; ++i) acc = fmaf(Ws[ra * LD + i] * dp[i], Ws[cb * LD + i], acc);
+        for (int i = 0; i < N; ++i) acc = fmaf(Vs[ra * LD + i], Ws[cb * LD + i], acc);
         const double xv = ldexp((double)acc, e2);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
