@@ -2,10 +2,15 @@
 // factorization"): clique index maps, D, A on the lower pattern, and the cached factor of A D^-1 A^T.
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <atomic>
+#include <functional>
+#include <mutex>
 #include <numeric>
 #include <thread>
+
+#include <unistd.h>
 
 #include "sdp_internal.h"
 
@@ -48,7 +53,89 @@ thread_local bool t_serial = false;
 
 int worker_count() { return t_serial ? 1 : (int)std::max(1u, std::thread::hardware_concurrency()); }
 
-// Runs f(i) for i in [0, n) on up to hardware_concurrency threads (contiguous slices).
+// Worker threads started on first use and kept for the life of the process: a setup runs a dozen
+// parallel loops of a millisecond or less, where starting and joining fresh threads for each
+// loop cost about as much as the loop. One caller at a time runs tasks on it (a concurrent caller,
+// or a process forked from this one, which has no workers, starts threads of its own). The calling
+// thread takes tasks too; the call returns once every task has run and no worker is inside the
+// task loop, so the next call cannot mix with it.
+class WorkerPool {
+public:
+    static WorkerPool& get() {
+        static WorkerPool pool;
+        return pool;
+    }
+    int threads() const { return (int)th_.size() + 1; }
+    // Runs task(t) for t in [0, n); false (nothing run) when another caller holds the pool.
+    bool try_run(int n, const std::function<void(int)>& task) {
+        if (getpid() != pid_) return false;
+        std::unique_lock<std::mutex> use(use_mu_, std::try_to_lock);
+        if (!use.owns_lock()) return false;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            task_ = &task;
+            n_ = n;
+            next_.store(0);
+            done_ = 0;
+            ++gen_;
+        }
+        cv_.notify_all();
+        take_tasks();
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return done_ == n_ && active_ == 0; });
+        task_ = nullptr;
+        return true;
+    }
+    ~WorkerPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+
+private:
+    WorkerPool() : pid_(getpid()) {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        for (int i = 0; i + 1 < hw; ++i) th_.emplace_back([this]() { worker(); });
+    }
+    void take_tasks() {
+        for (;;) {
+            const int t = next_.fetch_add(1);
+            if (t >= n_) return;
+            (*task_)(t);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (++done_ == n_) done_cv_.notify_all();
+        }
+    }
+    void worker() {
+        unsigned long long seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                ++active_;
+            }
+            take_tasks();
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--active_ == 0 && done_ == n_) done_cv_.notify_all();
+        }
+    }
+    const pid_t pid_;
+    std::vector<std::thread> th_;
+    std::mutex use_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)>* task_ = nullptr;
+    int n_ = 0, done_ = 0, active_ = 0;
+    std::atomic<int> next_{0};
+    unsigned long long gen_ = 0;
+    bool stop_ = false;
+};
+
+// Runs f(i) for i in [0, n) in up to hardware_concurrency contiguous slices.
 template <typename F>
 void parallel_for(int n, F f) {
     const int hw = worker_count();
@@ -57,12 +144,13 @@ void parallel_for(int n, F f) {
         for (int i = 0; i < n; ++i) f(i);
         return;
     }
+    const std::function<void(int)> slice = [&](int t) {
+        const int lo = (int)((long long)n * t / nt), hi = (int)((long long)n * (t + 1) / nt);
+        for (int i = lo; i < hi; ++i) f(i);
+    };
+    if (WorkerPool::get().try_run(nt, slice)) return;
     std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&, t]() {
-            const int lo = (int)((long long)n * t / nt), hi = (int)((long long)n * (t + 1) / nt);
-            for (int i = lo; i < hi; ++i) f(i);
-        });
+    for (int t = 0; t < nt; ++t) th.emplace_back(slice, t);
     for (auto& x : th) x.join();
 }
 
@@ -331,8 +419,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         if (nc > 0)
             for (long long t = cones->A_ptr[i]; t < cones->A_ptr[i + 1]; ++t)
                 row.emplace_back(nEL_mat + cones->A_var[t], cones->A_val[t]);
-        std::sort(row.begin(), row.end(),
-                  [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
+        auto by_entry = [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; };
+        if (!std::is_sorted(row.begin(), row.end(), by_entry)) std::sort(row.begin(), row.end(), by_entry);
         size_t w = 0;
         for (size_t t = 0; t < row.size(); ++t) {
             if (w > 0 && row[w - 1].first == row[t].first) row[w - 1].second += row[t].second;
@@ -382,17 +470,30 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             rows_of(t, lo, hi);
             for (int tt = hp.a_rowptr[lo]; tt < hp.a_rowptr[hi]; ++tt) cnt_t[t][hp.a_col[tt]]++;
         });
-        // exclusive offsets: column-major over (column, thread)
-        long long run = 0;
-        for (int e = 0; e < nEL; ++e) {
-            hp.c_colptr[e] = (int)run;
-            for (int t = 0; t < nt; ++t) {
-                const int c0 = cnt_t[t][e];
-                cnt_t[t][e] = (int)run;
-                run += c0;
+        // exclusive offsets, column-major over (column, thread): column totals, their prefix sum,
+        // then each column's per-thread offsets (columns in parallel)
+        const int nchunk = std::max(1, std::min(worker_count(), nEL / 4096 + 1));
+        parallel_for(nchunk, [&](int k) {
+            const int e0 = (int)((long long)nEL * k / nchunk), e1 = (int)((long long)nEL * (k + 1) / nchunk);
+            for (int e = e0; e < e1; ++e) {
+                int tot = 0;
+                for (int t = 0; t < nt; ++t) tot += cnt_t[t][e];
+                hp.c_colptr[e + 1] = tot;
             }
-        }
-        hp.c_colptr[nEL] = (int)run;
+        });
+        hp.c_colptr[0] = 0;
+        for (int e = 0; e < nEL; ++e) hp.c_colptr[e + 1] += hp.c_colptr[e];
+        parallel_for(nchunk, [&](int k) {
+            const int e0 = (int)((long long)nEL * k / nchunk), e1 = (int)((long long)nEL * (k + 1) / nchunk);
+            for (int e = e0; e < e1; ++e) {
+                int run = hp.c_colptr[e];
+                for (int t = 0; t < nt; ++t) {
+                    const int c0 = cnt_t[t][e];
+                    cnt_t[t][e] = run;
+                    run += c0;
+                }
+            }
+        });
         parallel_for(nt, [&](int t) {
             int lo, hi;
             rows_of(t, lo, hi);
@@ -428,14 +529,15 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                 }
             }
         };
-        const unsigned hw = (unsigned)std::max(1, std::min(worker_count(), chunks));
-        for (int base = 0; base < chunks; base += (int)hw) {
-            std::vector<std::thread> th;
-            for (int ch = base; ch < std::min(chunks, base + (int)hw); ++ch) th.emplace_back(work, ch);
-            for (auto& t : th) t.join();
-        }
-        for (int ch = 0; ch < chunks; ++ch)
-            for (size_t q = 0; q < mm; ++q) M[q] += part[ch][q];
+        parallel_for(chunks, work);
+        // the chunks add up in a fixed order; rows of M in parallel
+        parallel_for(m, [&](int i) {
+            double* Mi = M.data() + (size_t)i * m;
+            for (int ch = 0; ch < chunks; ++ch) {
+                const double* Pi = part[ch].data() + (size_t)i * m;
+                for (int j = 0; j < m; ++j) Mi[j] += Pi[j];
+            }
+        });
     }
 
     // ---- Cholesky M = L L^T (row-major lower, in place). A pivot at or below 1e-12 of the
