@@ -491,10 +491,10 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
 constexpr int kOSRows = 8;                 // rows per warp
 // Cyclic Jacobi converges quadratically: a sweep that starts with every pair within
 // kOneSidedStop of orthogonal leaves them within about its square divided by the relative gap of
-// the shifted spectrum, which the shift 2 ||W||_F makes small for clustered eigenvalues: 3e-4
-// left a 1e-4 error on a 20 x 20 block with four 5-fold clusters, 1e-4 stays below 2e-5. (Looser
-// thresholds were faster on the n = 1020 workload: 11.4k / 11.7k / 12.0k iterations per second
-// at 1e-4 / 3e-4 / 1e-3.)
+// the shifted spectrum, which the shift 2 ||W||_F makes small for clustered eigenvalues. With
+// 1e-4 the projection error stays below 1e-4 ||W|| (cold starts on 20 x 20 blocks with four
+// 5-fold clusters reached 7.5e-5; 3e-4 left 1e-4 on such a block). (Looser thresholds were faster
+// on the n = 1020 workload: 11.4k / 11.7k / 12.0k iterations per second at 1e-4 / 3e-4 / 1e-3.)
 constexpr float kOneSidedStop = 1.0e-4f;
 constexpr int kOneSidedMaxSweeps = 20;
 

@@ -559,10 +559,10 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         }
     }
     // ---- L^-1 (lower) by forward substitution on the unit vectors, and its transpose.
+    // Columns are independent: in parallel, each with its own work vector.
     hp.Linv.assign(mm, 0.0);
-    std::vector<double> xcol(m);
-    for (int j = 0; j < m; ++j) {
-        std::fill(xcol.begin(), xcol.end(), 0.0);
+    parallel_for(m, [&](int j) {
+        std::vector<double> xcol(m, 0.0);
         xcol[j] = 1.0 / L[(size_t)j * m + j];
         for (int i = j + 1; i < m; ++i) {
             const double* Li = L.data() + (size_t)i * m;
@@ -571,7 +571,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             xcol[i] = -s / Li[i];
         }
         for (int i = j; i < m; ++i) hp.Linv[(size_t)i * m + j] = xcol[i];
-    }
+    });
     hp.LinvT.assign(mm, 0.0);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j <= i; ++j) hp.LinvT[(size_t)j * m + i] = hp.Linv[(size_t)i * m + j];
@@ -584,16 +584,15 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         constexpr int kWindow = 256;
         const int ns = (nEL + 31) / 32;
         std::vector<int> slot_col(32LL * ns, -1);
-        std::vector<int> cols;
-        for (int w0 = 0; w0 < nEL; w0 += kWindow) {
-            const int w1 = std::min(w0 + kWindow, nEL);
-            cols.resize(w1 - w0);
+        parallel_for((nEL + kWindow - 1) / kWindow, [&](int w) {      // windows are independent
+            const int w0 = w * kWindow, w1 = std::min(w0 + kWindow, nEL);
+            std::vector<int> cols(w1 - w0);
             std::iota(cols.begin(), cols.end(), w0);
             std::stable_sort(cols.begin(), cols.end(), [&](int x, int y) {
                 return hp.c_colptr[x + 1] - hp.c_colptr[x] > hp.c_colptr[y + 1] - hp.c_colptr[y];
             });
             for (int t = 0; t < w1 - w0; ++t) slot_col[w0 + t] = cols[t];
-        }
+        });
         hp.sell_col.assign(slot_col.begin(), slot_col.end());
         hp.sell_len.resize(ns);
         hp.sell_off.resize(ns + 1);
