@@ -123,8 +123,9 @@ typedef struct {
 /* ---- setup (Algorithms 1-2, "Setup: chordal decomposition, KKT factorization") -------------
  * Builds the clique index maps (H_k as gather indices and their inverse as a CSR scatter map),
  * D = sum_k H_k^T H_k (Section III.B.1), A on E_L in CSR and CSC form, M = A D^-1 A^T and its
- * Cholesky factor L (computed once and cached; the per-iteration triangular solves use L^-1 and
- * L^-T formed here), uploads everything to the device and zeroes the iterates.
+ * Cholesky factor L (computed once and cached; the per-iteration solve uses (L L^T)^-1 = L^-T L^-1
+ * formed here, one product instead of two triangular ones), uploads everything to the device and
+ * zeroes the iterates.
  *   n, m        matrix order and number of constraints (1 <= m <= SDP_MAX_CONSTRAINTS)
  *   A_ptr[m+1]  constraint i owns coordinates A_ptr[i] .. A_ptr[i+1]-1 of A_row/A_col/A_val
  *   b[m]        right-hand side
@@ -149,7 +150,7 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
  * problem q follow those of problem q-1 (sdp_batch_layout gives the offsets), so every vector the
  * handle reads or returns (sdp_get_state, sdp_set_state, sdp_get_solution, sdp_get_maps, the
  * device buffers of sdp_gather / sdp_scatter) is the concatenation of the problems' vectors, and
- * each problem's L^-1 is its own block. Every kernel of an iteration covers all problems at once;
+ * each problem's (A D^-1 A^T)^-1 is its own block. Every kernel of an iteration covers all problems at once;
  * no CTA works on two problems. Each problem keeps its own residuals, objectives and stop test
  * (the definitions below): a problem whose residuals fall below tol, or become NaN/Inf, is frozen
  * (its iterates stop changing) at that iteration, which is what a separate solve of it would

@@ -102,7 +102,7 @@ struct sdp_ctx {
         double *lam_prev = nullptr, *Xb = nullptr, *Lb = nullptr, *ub = nullptr;
         double *cbar = nullptr, *bbar = nullptr;
         // vectors of the adjoint KKT solve, swapped into a copy of the forward's pointers
-        double *xbar = nullptr, *rsw = nullptr, *rbar = nullptr, *ybar = nullptr, *z1 = nullptr;
+        double *xbar = nullptr, *rsw = nullptr, *rbar = nullptr, *ybar = nullptr;
         double *tpart = nullptr, *pobj = nullptr;
         int* conv = nullptr;
         cadmm::Ctrl* ctrl = nullptr;
@@ -648,8 +648,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(sell_off, hp.sell_off);
     UP(sell_row, hp.sell_row);
     UP(sell_val, hp.sell_val);
-    UP(Linv, hp.Linv);
-    UP(LinvT, hp.LinvT);
+    UP(Minv, hp.Minv);
     UP(cone_lo, hp.cone_lo);
     UP(cone_hi, hp.cone_hi);
     UP(cone_kind, hp.cone_kind);
@@ -663,7 +662,6 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     if ((rc = h->dalloc(&P.y, hp.m))) return rc;
     if ((rc = h->dalloc(&P.r, hp.nEL))) return rc;
     if ((rc = h->dalloc(&P.rsw, hp.nEL))) return rc;
-    if ((rc = h->dalloc(&P.z1, hp.m))) return rc;
     if ((rc = h->dalloc(&P.xk[0], hp.SL))) return rc;
     if ((rc = h->dalloc(&P.xk[1], hp.SL))) return rc;
     if ((rc = h->dalloc(&P.lam, hp.SL))) return rc;
@@ -851,7 +849,6 @@ int admm_reset(sdp_handle h, void* cuda_stream) {
     IterPtrs& P = h->P;
     CK(cudaMemsetAsync(P.x, 0, sizeof(double) * std::max(1, P.nEL), st));
     CK(cudaMemsetAsync(P.y, 0, sizeof(double) * P.m, st));
-    CK(cudaMemsetAsync(P.z1, 0, sizeof(double) * P.m, st));
     CK(cudaMemsetAsync(P.r, 0, sizeof(double) * std::max(1, P.nEL), st));
     CK(cudaMemsetAsync(P.rsw, 0, sizeof(double) * std::max(1, P.nEL), st));
     for (int i = 0; i < 2; ++i) CK(cudaMemsetAsync(P.xk[i], 0, sizeof(double) * std::max(1, P.SL), st));
@@ -1065,7 +1062,7 @@ int ensure_adjoint(sdp_ctx* h, int T, int K) {
         if ((rc = h->dalloc(&A.lam_prev, SL)) || (rc = h->dalloc(&A.Xb, SL)) || (rc = h->dalloc(&A.Lb, SL)) ||
             (rc = h->dalloc(&A.ub, SL)) || (rc = h->dalloc(&A.cbar, h->nEL)) || (rc = h->dalloc(&A.bbar, h->m)) ||
             (rc = h->dalloc(&A.xbar, h->nEL)) || (rc = h->dalloc(&A.rsw, h->nEL)) ||
-            (rc = h->dalloc(&A.rbar, h->nEL)) || (rc = h->dalloc(&A.ybar, h->m)) || (rc = h->dalloc(&A.z1, h->m)) ||
+            (rc = h->dalloc(&A.rbar, h->nEL)) || (rc = h->dalloc(&A.ybar, h->m)) ||
             (rc = h->dalloc(&A.tpart, h->row_cap)) || (rc = h->dalloc(&A.pobj, h->col_cap)) ||
             (rc = h->dalloc(&A.conv, (size_t)h->ninst)) || (rc = h->dalloc(&A.ctrl, 1)))
             return rc;
@@ -1106,7 +1103,6 @@ cadmm::IterPtrs adjoint_ptrs(const sdp_ctx* h) {
     AP.rsw = A.rsw;
     AP.x = A.rbar;
     AP.y = A.ybar;
-    AP.z1 = A.z1;
     AP.tpart = A.tpart;
     AP.part_obj = A.pobj;
     AP.inst_conv = A.conv;

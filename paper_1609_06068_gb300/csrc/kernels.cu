@@ -1,8 +1,8 @@
 // Per-iteration kernels of the decomposed ADMM other than the PSD projection:
 //   scatter      r = sum_k H_k^T(.) and the KKT right-hand side (Eqs. OptCondMinYPrimal/Dual)
 //   spmv_rows    t = A (w r / D)           (block elimination, first pass over A; CSR)
-//   tri_lower    z = L^-1 (t - rhs2)       (cached factor of A D^-1 A^T, Section III.B.1)
-//   tri_upper    y = L^-T z
+//   solve_y      y = M^-1 (t - rhs2)       (M = A D^-1 A^T, inverse formed at setup from its
+//                                           cached Cholesky factor, Section III.B.1)
 //   spmv_cols    x = (r - A^T y) / D       (second pass over A; CSC)
 //   update_dual  v_k = z_k + rho^-1 lambda_k + H_k x, lambda_k = -rho H_k x (Eqs. vkEqn,
 //                DualMultUpdate with the sign Eq. MultUpdateDualSDP implies)
@@ -437,10 +437,12 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     if (lane == 0) P.tpart[ch] = t;
 }
 
-// ---------------------------------------------------------------- z = L^-1 (t - rhs2)
-// rhs2 = b (primal), -rho^-1 b (dual) or 0 (kKktZeroRhs: the adjoint solve). One warp per row of
-// L^-1.
-__global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double rinv, int form) {
+// ---------------------------------------------------------------- y = M^-1 (t - rhs2)
+// t = A (w r / D) from the row chunks' partial sums, rhs2 = b (primal), -rho^-1 b (dual) or 0
+// (kKktZeroRhs: the adjoint solve). M^-1 = (A D^-1 A^T)^-1 is formed at setup from the Cholesky
+// factor (L^-T L^-1), so the block elimination's two triangular products are one product: each
+// CTA stages t - rhs2 of its problem in shared memory, one warp per row of M^-1.
+__global__ void __launch_bounds__(kTriThreads) k_solve_y(IterPtrs P, double rinv, int form) {
     extern __shared__ double u[];
     pdl_wait();
     if (P.ctrl->done) return;
@@ -455,45 +457,17 @@ __global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double ri
         u[i] = t - rhs2;
     }
     __syncthreads();
-    const double* Lb = P.Linv + P.mblk_off[sc.q];
+    const double* Mb = P.Minv + P.mblk_off[sc.q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
-        const int row = grow - r0;
-        const double* Lr = Lb + (size_t)row * m;
+        const double* Mr = Mb + (size_t)(grow - r0) * m;
         double a0 = 0.0, a1 = 0.0;
         int j = lane;
-        for (; j + 32 <= row; j += 64) {
-            a0 = fma(Lr[j], u[j], a0);
-            a1 = fma(Lr[j + 32], u[j + 32], a1);
+        for (; j + 32 < m; j += 64) {
+            a0 = fma(Mr[j], u[j], a0);
+            a1 = fma(Mr[j + 32], u[j + 32], a1);
         }
-        if (j <= row) a0 = fma(Lr[j], u[j], a0);
-        const double acc = warp_sum(a0 + a1);
-        if (lane == 0) P.z1[grow] = acc;
-    }
-}
-
-// ---------------------------------------------------------------- y = L^-T z
-__global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
-    extern __shared__ double zs[];
-    pdl_wait();
-    if (P.ctrl->done) return;
-    const Sched sc = P.tri_sched[blockIdx.x];
-    if (stopped(P, sc.q)) return;
-    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = P.z1[r0 + i];
-    __syncthreads();
-    const double* Lb = P.LinvT + P.mblk_off[sc.q];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
-        const int row = grow - r0;
-        const double* Lr = Lb + (size_t)row * m;
-        double a0 = 0.0, a1 = 0.0;
-        int i = row + lane;
-        for (; i + 32 < m; i += 64) {
-            a0 = fma(Lr[i], zs[i], a0);
-            a1 = fma(Lr[i + 32], zs[i + 32], a1);
-        }
-        if (i < m) a0 = fma(Lr[i], zs[i], a0);
+        if (j < m) a0 = fma(Mr[j], u[j], a0);
         const double acc = warp_sum(a0 + a1);
         if (lane == 0) P.y[grow] = acc;
     }
@@ -905,9 +879,7 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
         return e;
     const size_t mbytes = (size_t)P.mmax * sizeof(double);   // the largest problem's y, staged
     mk.mark();
-    if ((e = launch_pdl(k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) return e;
-    mk.mark();
-    if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_solve_y, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) return e;
     mk.mark();
     if (P.col_split)
         e = launch_pdl(k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
@@ -924,19 +896,18 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
 }  // namespace
 
 int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form) {
-    return (form == SDP_PRIMAL ? 5 : 6) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
+    return (form == SDP_PRIMAL ? 4 : 5) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
 }
 
 int phase_count(const IterPtrs& P, int form) {
-    return (form == SDP_PRIMAL ? 6 : 7) + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
+    return (form == SDP_PRIMAL ? 5 : 6) + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
 }
 
 cudaError_t iteration_prepare() {
     // y / z / t staged in shared memory: up to SDP_MAX_CONSTRAINTS doubles.
     const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -978,16 +949,16 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
 }
 
 const char* phase_name(int form, bool batch, bool cones, int i) {
-    static const char* primal[] = {"spmv_rows", "tri_lower", "tri_upper", "spmv_cols", "project_primal",
-                                   "project_cones", "scatter_primal+finalize", "finalize_batch"};
-    static const char* dual[] = {"project_dual", "project_cones", "scatter_dual", "spmv_rows", "tri_lower",
-                                 "tri_upper", "spmv_cols", "update_dual+finalize", "finalize_batch"};
+    static const char* primal[] = {"spmv_rows", "solve_y", "spmv_cols", "project_primal", "project_cones",
+                                   "scatter_primal+finalize", "finalize_batch"};
+    static const char* dual[] = {"project_dual", "project_cones", "scatter_dual", "spmv_rows", "solve_y",
+                                 "spmv_cols", "update_dual+finalize", "finalize_batch"};
     const char** list = form == SDP_PRIMAL ? primal : dual;
-    const int cone_at = form == SDP_PRIMAL ? 5 : 1;
-    const int n = (form == SDP_PRIMAL ? 6 : 7) + (cones ? 1 : 0) + (batch ? 1 : 0);
+    const int cone_at = form == SDP_PRIMAL ? 4 : 1;
+    const int n = (form == SDP_PRIMAL ? 5 : 6) + (cones ? 1 : 0) + (batch ? 1 : 0);
     if (i < 0 || i >= n) return nullptr;
     if (!cones && i >= cone_at) ++i;                    // no cone phase: skip its slot
-    if (batch && i == (form == SDP_PRIMAL ? 6 : 7)) return form == SDP_PRIMAL ? "scatter_primal" : "update_dual";
+    if (batch && i == (form == SDP_PRIMAL ? 5 : 6)) return form == SDP_PRIMAL ? "scatter_primal" : "update_dual";
     return list[i];
 }
 

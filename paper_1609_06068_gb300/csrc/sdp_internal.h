@@ -54,12 +54,12 @@ struct HostProblem {
     std::vector<long long> sell_off;            // [nslices+1]
     std::vector<unsigned short> sell_row;
     std::vector<double> sell_val;
-    std::vector<double> Linv, LinvT;            // per instance an m_q x m_q row-major block
+    std::vector<double> Minv;                   // (A D^-1 A^T)^-1: per instance an m_q x m_q row-major block
     // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
     int ninst = 1;
     std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
                                                                       // E_L entries, positions, rows, slices
-    std::vector<long long> mblk_off;                        // offsets of the L^-1 blocks
+    std::vector<long long> mblk_off;                        // offsets of the M^-1 blocks
     // Non-PSD cones: n_cone variables after the E_L entries (and after the clique blocks in the
     // packed vector), projected in segments [cone_lo, cone_hi) of kind kCone*.
     int n_cone = 0;
@@ -150,7 +150,7 @@ struct IterPtrs {
     int mmax;                       // largest number of constraints of one problem
     const int* inst_cl;             // [ninst+1] first clique of each problem
     const int* inst_row;            // [ninst+1] first constraint of each problem
-    const long long* mblk_off;      // [ninst+1] offset of each problem's block of L^-1 and L^-T
+    const long long* mblk_off;      // [ninst+1] offset of each problem's block of M^-1
     const int* blk_inst;            // [p] problem of each clique
     // Work schedules. The two passes over A are split into warp-sized chunks (8 per CTA); the
     // other kernels give one Sched per CTA.
@@ -175,9 +175,9 @@ struct IterPtrs {
     const int* a_rowptr; const int* a_col; const double* a_val;
     const int* sell_col; const int* sell_len; const long long* sell_off;    // A^T, sliced ELL
     const unsigned short* sell_row; const double* sell_val;                  // rows within the problem
-    const double* Linv; const double* LinvT;
+    const double* Minv;                            // (A D^-1 A^T)^-1 blocks at mblk_off
     // state
-    double* x; double* y; double* r; double* rsw; double* z1;
+    double* x; double* y; double* r; double* rsw;
     double* xk[2]; double* lam; double* vk;
     void* vstore;         // eigenvector blocks for warm starts (projection precision)
     const long long* voff;

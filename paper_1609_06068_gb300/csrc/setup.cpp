@@ -558,9 +558,10 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             Li[j] = s / ljj;
         }
     }
-    // ---- L^-1 (lower) by forward substitution on the unit vectors, and its transpose.
-    // Columns are independent: in parallel, each with its own work vector.
-    hp.Linv.assign(mm, 0.0);
+    // ---- L^-1 (lower) by forward substitution on the unit vectors (columns are independent: in
+    // parallel, each with its own work vector), then M^-1 = L^-T L^-1, so that the affine step's
+    // y is one product: M^-1_ij = sum_{k >= max(i, j)} L^-1_ki L^-1_kj, k ascending.
+    std::vector<double> Linv(mm, 0.0);
     parallel_for(m, [&](int j) {
         std::vector<double> xcol(m, 0.0);
         xcol[j] = 1.0 / L[(size_t)j * m + j];
@@ -570,11 +571,18 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             for (int k = j; k < i; ++k) s += Li[k] * xcol[k];
             xcol[i] = -s / Li[i];
         }
-        for (int i = j; i < m; ++i) hp.Linv[(size_t)i * m + j] = xcol[i];
+        for (int i = j; i < m; ++i) Linv[(size_t)i * m + j] = xcol[i];
     });
-    hp.LinvT.assign(mm, 0.0);
+    hp.Minv.assign(mm, 0.0);
+    parallel_for(m, [&](int i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (int k = i; k < m; ++k) s += Linv[(size_t)k * m + i] * Linv[(size_t)k * m + j];
+            hp.Minv[(size_t)i * m + j] = s;
+        }
+    });
     for (int i = 0; i < m; ++i)
-        for (int j = 0; j <= i; ++j) hp.LinvT[(size_t)j * m + i] = hp.Linv[(size_t)i * m + j];
+        for (int j = i + 1; j < m; ++j) hp.Minv[(size_t)i * m + j] = hp.Minv[(size_t)j * m + i];
 
     // ---- A^T as sliced ELL (32 columns per slice, one lane per column on the device). Within
     // each window of 256 consecutive columns the columns are ordered by length (longest first,
@@ -706,7 +714,7 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         hp.gather_idx.reserve(SL); hp.pos_w.reserve(SL); hp.sc_pos.reserve(SL);
         hp.b.reserve(m); hp.a_rowptr.reserve(m + 1);
         hp.a_col.reserve(nnz); hp.a_val.reserve(nnz);
-        hp.Linv.reserve(mm); hp.LinvT.reserve(mm);
+        hp.Minv.reserve(mm);
     };
     reserve_all();
     hp.sc_ptr.push_back(0);
@@ -749,8 +757,7 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         for (int i = 0; i < h.m; ++i) hp.a_rowptr.push_back(h.a_rowptr[i + 1] + a0);
         for (int c : h.a_col) hp.a_col.push_back(c + e0);
         hp.a_val.insert(hp.a_val.end(), h.a_val.begin(), h.a_val.end());
-        hp.Linv.insert(hp.Linv.end(), h.Linv.begin(), h.Linv.end());
-        hp.LinvT.insert(hp.LinvT.end(), h.LinvT.begin(), h.LinvT.end());
+        hp.Minv.insert(hp.Minv.end(), h.Minv.begin(), h.Minv.end());
         h = HostProblem();   // release the part as soon as it is copied
     }
     hp.blk_off.push_back((int)SL);
