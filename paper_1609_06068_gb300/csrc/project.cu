@@ -191,6 +191,22 @@ __device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int p
     return __dsub_rn(a.v[off + pos], __dmul_rn(rinv, a.lam[off + pos]));
 }
 
+// Scaling of a block by the exact power of two 2^-e2 and back. A multiplication by 2^k rounds like
+// ldexp(x, k) (both are correctly rounded), but on GB300 ldexp is a sequence of FP64 operations
+// per element where the multiplication is one; 2^k is formed once per block, as a double while
+// |k| <= 1000, and ldexp itself scales the rare block whose exponent lies beyond that.
+struct Pow2 {
+    bool plain;
+    int e;
+    double down, up;
+};
+__device__ __forceinline__ Pow2 pow2_of(int e2) {
+    const bool plain = e2 >= -1000 && e2 <= 1000;
+    return Pow2{plain, e2, plain ? ldexp(1.0, -e2) : 0.0, plain ? ldexp(1.0, e2) : 0.0};
+}
+__device__ __forceinline__ double scale_down(const Pow2& p, double x) { return p.plain ? x * p.down : ldexp(x, -p.e); }
+__device__ __forceinline__ double scale_up(const Pow2& p, double x) { return p.plain ? x * p.up : ldexp(x, p.e); }
+
 // Batches: true when clique blk belongs to a problem that has stopped, so the CTA must return.
 // In the primal form the iteration right after the stop copies the block's current x_k to the
 // other ping-pong buffer first, so both hold it for every later parity.
@@ -250,6 +266,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     }
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    const Pow2 p2 = pow2_of(e2);
     T* Wt = warm ? Wb : Ax;
     for (int q = tid; q < N * N; q += NT) {
         const int i = q / N, j = q - (q / N) * N;
@@ -258,7 +275,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
-        const T wt = (T)ldexp(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv), -e2);
+        const T wt = (T)scale_down(p2, load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv));
         Wt[ra * LD + cb] = wt;
         Wt[cb * LD + ra] = wt;
     }
@@ -445,7 +462,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
         const T* Vb = Vx + cb * LD;
         T acc = T(0);
         for (int i = 0; i < N; ++i) acc = fma(Va[i] * dp[i], Vb[i], acc);
-        const double xv = ldexp((double)acc, e2);
+        const double xv = scale_up(p2, (double)acc);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
             const double u = a.x[a.gather_idx[off + pos]];
@@ -500,7 +517,7 @@ constexpr int kOneSidedMaxSweeps = 20;
 
 // Round-robin partner of player i in round rd for N players (N even, n = N - 1 odd): player n
 // meets player rd; every other i meets (2 rd - i) mod n, or player n when that is i itself.
-__device__ __forceinline__ int rr_partner(int i, int rd, int N) {
+__host__ __device__ constexpr int rr_partner(int i, int rd, int N) {
     if (i >= N) return i;
     const int n = N - 1;
     if (i == n) return rd;
@@ -508,6 +525,24 @@ __device__ __forceinline__ int rr_partner(int i, int rd, int N) {
     if (j < 0) j += n;
     return j == i ? n : j;
 }
+
+// Partner tables of the CTA one-sided kernels, [round][player] for every even order N (32 x 32 for
+// N <= 32, 64 x 64 up to 64), evaluated by the compiler: computing them in every CTA (a modulo by
+// N - 1 per entry) cost about 1.5 us per projection; a CTA now copies its table with one or two
+// 8-byte loads per thread.
+struct PartnerTables {
+    unsigned char t32[16][32 * 32];
+    unsigned char t64[32][64 * 64];
+};
+constexpr PartnerTables make_partner_tables() {
+    PartnerTables p{};
+    for (int t = 0; t < 16; ++t)
+        for (int q = 0; q < 32 * 32; ++q) p.t32[t][q] = (unsigned char)rr_partner(q & 31, q >> 5, 2 * (t + 1));
+    for (int t = 0; t < 32; ++t)
+        for (int q = 0; q < 64 * 64; ++q) p.t64[t][q] = (unsigned char)rr_partner(q & 63, q >> 6, 2 * (t + 1));
+    return p;
+}
+__device__ __align__(16) const PartnerTables g_partner = make_partner_tables();
 
 template <int CPL>
 struct OSLayout {
@@ -546,7 +581,11 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     // Warm start whenever eigenvectors are kept (they are the identity right after a reset).
     const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
-    for (int q = tid; q < NP * NP; q += NT) s_partner[q] = (unsigned char)rr_partner(q % NP, q / NP, N);
+    {
+        const unsigned char* gp = CPL == 1 ? g_partner.t32[N / 2 - 1] : g_partner.t64[N / 2 - 1];
+        for (int q = 8 * tid; q < NP * NP; q += 8 * NT)
+            *reinterpret_cast<uint2*>(s_partner + q) = *reinterpret_cast<const uint2*>(gp + q);
+    }
 
     // ---- W scaled by 2^-e2 into Ws (both triangles), zero outside s x s. Each thread reads its
     // entries once, all loads in flight, and keeps them until the scale is known.
@@ -563,6 +602,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     for (int k = 0; k < KQ; ++k) wmax = fmax(wmax, fabs(wv[k]));
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    const Pow2 p2 = pow2_of(e2);
     for (int q = tid; q < NP * NP; q += NT) {
         const int i = q / NP, j = q % NP;
         if (i >= s || j >= s) Ws[i * LD + j] = 0.f;
@@ -573,7 +613,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         const int q = tid + k * NT;
         const int ra = q % s, cb = q / s;
         if (q < s * s && ra >= cb) {
-            const float wt = (float)ldexp(wv[k], -e2);
+            const float wt = (float)scale_down(p2, wv[k]);
             Ws[ra * LD + cb] = wt;
             Ws[cb * LD + ra] = wt;
         }
@@ -770,12 +810,18 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
-    for (int q = tid; q < s * s; q += NT) {
-        const int ra = q % s, cb = q / s;
-        if (ra < cb) continue;
+    // warp w takes columns w, w + NW, ...; lane j row cb + j (+ 32 h): no division, and the FP64
+    // results of a column go out as consecutive stores
+    for (int cb = w; cb < s; cb += NW)
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) {
+        const int ra = cb + lane + 32 * h;
+        if (ra >= s) continue;
+        const float* Va = Vs + ra * LD;
+        const float* Wb = Ws + cb * LD;
         float acc = 0.f;
-        for (int i = 0; i < N; ++i) acc = fmaf(Vs[ra * LD + i], Ws[cb * LD + i], acc);
-        const double xv = ldexp((double)acc, e2);
+        for (int i = 0; i < N; ++i) acc = fmaf(Va[i], Wb[i], acc);
+        const double xv = scale_up(p2, (double)acc);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
             const double u = a.x[a.gather_idx[off + pos]];
@@ -892,7 +938,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
     }
     wmax = seg_maxd<NR>(wmax);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
+    const Pow2 p2 = pow2_of(e2);
 #pragma unroll
     for (int r = 0; r < NR; ++r) Ws[r * LD + c] = 0.f;
     __syncwarp();
@@ -900,14 +946,14 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (r >= c && r < s) {
-                const float wt = (float)(wc[r] * down);
+                const float wt = (float)scale_down(p2, wc[r]);
                 Ws[r * LD + c] = wt;
                 Ws[c * LD + r] = wt;
             }
     } else {
         if (c < s)
             for (int r = c; r < s; ++r) {
-                const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
+                const float wt = (float)scale_down(p2, load_w<MODE>(a, off, packed_pos(r, c, s), rinv));
                 Ws[r * LD + c] = wt;
                 Ws[c * LD + r] = wt;
             }
@@ -1017,7 +1063,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
             float acc = 0.f;
 #pragma unroll 8
             for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = (double)acc * up;
+            const double xv = scale_up(p2, (double)acc);
             const int pos = packed_pos(ra, cb, s);
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
@@ -1095,11 +1141,11 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
     pair_sync(pair);
     wmax = fmax(redd[0], redd[1]);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
+    const Pow2 p2 = pow2_of(e2);
     pair_sync(pair);
     if (c < s)
         for (int r = c; r < s; ++r) {
-            const float wt = (float)(load_w<MODE>(a, off, packed_pos(r, c, s), rinv) * down);
+            const float wt = (float)scale_down(p2, load_w<MODE>(a, off, packed_pos(r, c, s), rinv));
             Ts[r * LD + c] = wt;
             Ts[c * LD + r] = wt;
         }
@@ -1223,7 +1269,7 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
             const float* Qa = Ts + ra * LD;
             float acc = 0.f;
             for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = (double)acc * up;
+            const double xv = scale_up(p2, (double)acc);
             const int pos = packed_pos(ra, cb, s);
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
@@ -1352,6 +1398,7 @@ size_t project_vstore_elems(int s) {
 
 cudaError_t project_prepare() {
     cudaError_t e;
+
     if ((e = prepare_mode<float, PROJ_PLAIN>()) != cudaSuccess) return e;
     if ((e = prepare_mode<float, PROJ_PRIMAL>()) != cudaSuccess) return e;
     if ((e = prepare_mode<float, PROJ_DUAL>()) != cudaSuccess) return e;
