@@ -202,7 +202,10 @@ struct Pow2 {
 };
 __device__ __forceinline__ Pow2 pow2_of(int e2) {
     const bool plain = e2 >= -1000 && e2 <= 1000;
-    return Pow2{plain, e2, plain ? ldexp(1.0, -e2) : 0.0, plain ? ldexp(1.0, e2) : 0.0};
+    // 2^k for |k| <= 1000 straight from its exponent field (integer operations only)
+    const double down = __longlong_as_double((long long)(1023 - (plain ? e2 : 0)) << 52);
+    const double up = __longlong_as_double((long long)(1023 + (plain ? e2 : 0)) << 52);
+    return Pow2{plain, e2, down, up};
 }
 __device__ __forceinline__ double scale_down(const Pow2& p, double x) { return p.plain ? x * p.down : ldexp(x, -p.e); }
 __device__ __forceinline__ double scale_up(const Pow2& p, double x) { return p.plain ? x * p.up : ldexp(x, p.e); }
@@ -591,22 +594,27 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     // entries once, all loads in flight, and keeps them until the scale is known.
     constexpr int KQ = NP * NP / (32 * NW);
     double wv[KQ];
+    float vp[KQ];          // the previous eigenvectors, loaded alongside W
     double wmax = 0.0;
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int q = tid + k * NT;
         const int ra = q % s, cb = q / s;
         wv[k] = (q < s * s && ra >= cb) ? load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv) : 0.0;
+        const int i = q / NP, j = q % NP;
+        vp[k] = !warm ? 0.f : (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) wmax = fmax(wmax, fabs(wv[k]));
     wmax = block_max(wmax, red_d);
     const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
     const Pow2 p2 = pow2_of(e2);
-    for (int q = tid; q < NP * NP; q += NT) {
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+        const int q = tid + k * NT;
         const int i = q / NP, j = q % NP;
         if (i >= s || j >= s) Ws[i * LD + j] = 0.f;
-        if (warm) Vs[i * LD + j] = (i < N && j < N) ? vglob[i * N + j] : (i == j ? 1.f : 0.f);
+        if (warm) Vs[i * LD + j] = vp[k];
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
