@@ -697,11 +697,20 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         for (int rd = 0; rd < N - 1; ++rd) {
             int p[CPL];
             float gp[CPL][kOSRows];
+            float beta[CPL];
             const int buf = rd & 1;
 #pragma unroll
             for (int h = 0; h < CPL; ++h) {
                 p[h] = s_partner[rd * NP + lane + 32 * h];
                 const int pl = p[h] & 31, ph = p[h] >> 5;
+                // the partner's alpha (lane p & 31 holds it in slot p >> 5), fetched before the
+                // barrier so that it is off the round's critical path
+                beta[h] = 0.f;
+#pragma unroll
+                for (int hs = 0; hs < CPL; ++hs) {
+                    const float t = __shfl_sync(0xffffffffu, alpha[hs], pl);
+                    if (hs == ph) beta[h] = t;
+                }
                 float pg = 0.f;
 #pragma unroll
                 for (int k = 0; k < kOSRows; ++k) {
@@ -725,18 +734,10 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
                 float gsum = 0.f;
                 for (int ww = 0; ww < NW; ++ww) gsum += s_gam[buf][ww][lane + 32 * h];
                 gam[h] = gsum;
-                // the partner's alpha: lane p & 31 holds it in slot p >> 5
-                const int pl = p[h] & 31, ph = p[h] >> 5;
-                float beta = 0.f;
-#pragma unroll
-                for (int hs = 0; hs < CPL; ++hs) {
-                    const float t = __shfl_sync(0xffffffffu, alpha[hs], pl);
-                    if (hs == ph) beta = t;
-                }
                 const int me = lane + 32 * h;
                 first[h] = me < p[h];
-                ai[h] = first[h] ? alpha[h] : beta;
-                aj[h] = first[h] ? beta : alpha[h];
+                ai[h] = first[h] ? alpha[h] : beta[h];
+                aj[h] = first[h] ? beta[h] : alpha[h];
                 float cc = 1.f, sn = 0.f, t = 0.f;
                 if (p[h] != me && fabsf(gsum) > 1.0e-30f) {
                     worst = fmaxf(worst, __fdividef(gsum * gsum, fmaxf(ai[h] * aj[h], 1.0e-30f)));
