@@ -191,24 +191,18 @@ __device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int p
     return __dsub_rn(a.v[off + pos], __dmul_rn(rinv, a.lam[off + pos]));
 }
 
-// Scaling of a block by the exact power of two 2^-e2 and back. A multiplication by 2^k rounds like
-// ldexp(x, k) (both are correctly rounded), but on GB300 ldexp is a sequence of FP64 operations
-// per element where the multiplication is one; 2^k is formed once per block, as a double while
-// |k| <= 1000, and ldexp itself scales the rare block whose exponent lies beyond that.
-struct Pow2 {
-    bool plain;
-    int e;
-    double down, up;
-};
-__device__ __forceinline__ Pow2 pow2_of(int e2) {
-    const bool plain = e2 >= -1000 && e2 <= 1000;
-    // 2^k for |k| <= 1000 straight from its exponent field (integer operations only)
-    const double down = __longlong_as_double((long long)(1023 - (plain ? e2 : 0)) << 52);
-    const double up = __longlong_as_double((long long)(1023 + (plain ? e2 : 0)) << 52);
-    return Pow2{plain, e2, down, up};
+// Scaling of a block by an exact power of two, 2^-e2 before the eigensolve and 2^e2 after, with
+// e2 = ilogb(max |W_ij|) clamped to [-1000, 1000] so that both factors are normal doubles built
+// from their exponent bits (on GB300 ldexp per element is a sequence of FP64 operations, the
+// multiplication is one, and rounds the same). A block beyond that range is scaled by 2^-+1000:
+// above, its FP32 values stay finite; below, its entries are under 2^-1000 and so is the error.
+__device__ __forceinline__ int block_exponent(double wmax) {
+    const int e = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+    return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
 }
-__device__ __forceinline__ double scale_down(const Pow2& p, double x) { return p.plain ? x * p.down : ldexp(x, -p.e); }
-__device__ __forceinline__ double scale_up(const Pow2& p, double x) { return p.plain ? x * p.up : ldexp(x, p.e); }
+__device__ __forceinline__ double pow2_exact(int k) {       // 2^k for |k| <= 1000, from its exponent bits
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
 
 // Batches: true when clique blk belongs to a problem that has stopped, so the CTA must return.
 // In the primal form the iteration right after the stop copies the block's current x_k to the
@@ -268,8 +262,8 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
         wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv)));
     }
     wmax = block_max(wmax, red_d);
-    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const Pow2 p2 = pow2_of(e2);
+    const int e2 = block_exponent(wmax);
+    const double down = pow2_exact(-e2), up = pow2_exact(e2);
     T* Wt = warm ? Wb : Ax;
     for (int q = tid; q < N * N; q += NT) {
         const int i = q / N, j = q - (q / N) * N;
@@ -278,7 +272,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     for (int q = tid; q < s * s; q += NT) {
         const int ra = q % s, cb = q / s;
         if (ra < cb) continue;
-        const T wt = (T)scale_down(p2, load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv));
+        const T wt = (T)((load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv)) * down);
         Wt[ra * LD + cb] = wt;
         Wt[cb * LD + ra] = wt;
     }
@@ -465,7 +459,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
         const T* Vb = Vx + cb * LD;
         T acc = T(0);
         for (int i = 0; i < N; ++i) acc = fma(Va[i] * dp[i], Vb[i], acc);
-        const double xv = scale_up(p2, (double)acc);
+        const double xv = ((double)acc) * up;
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
             const double u = a.x[a.gather_idx[off + pos]];
@@ -607,8 +601,8 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 #pragma unroll
     for (int k = 0; k < KQ; ++k) wmax = fmax(wmax, fabs(wv[k]));
     wmax = block_max(wmax, red_d);
-    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const Pow2 p2 = pow2_of(e2);
+    const int e2 = block_exponent(wmax);
+    const double down = pow2_exact(-e2), up = pow2_exact(e2);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int q = tid + k * NT;
@@ -621,7 +615,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         const int q = tid + k * NT;
         const int ra = q % s, cb = q / s;
         if (q < s * s && ra >= cb) {
-            const float wt = (float)scale_down(p2, wv[k]);
+            const float wt = (float)((wv[k]) * down);
             Ws[ra * LD + cb] = wt;
             Ws[cb * LD + ra] = wt;
         }
@@ -830,7 +824,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
         const float* Wb = Ws + cb * LD;
         float acc = 0.f;
         for (int i = 0; i < N; ++i) acc = fmaf(Va[i], Wb[i], acc);
-        const double xv = scale_up(p2, (double)acc);
+        const double xv = ((double)acc) * up;
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
             const double u = a.x[a.gather_idx[off + pos]];
@@ -946,8 +940,8 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
             for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
     }
     wmax = seg_maxd<NR>(wmax);
-    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const Pow2 p2 = pow2_of(e2);
+    const int e2 = block_exponent(wmax);
+    const double down = pow2_exact(-e2), up = pow2_exact(e2);
 #pragma unroll
     for (int r = 0; r < NR; ++r) Ws[r * LD + c] = 0.f;
     __syncwarp();
@@ -955,14 +949,14 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (r >= c && r < s) {
-                const float wt = (float)scale_down(p2, wc[r]);
+                const float wt = (float)((wc[r]) * down);
                 Ws[r * LD + c] = wt;
                 Ws[c * LD + r] = wt;
             }
     } else {
         if (c < s)
             for (int r = c; r < s; ++r) {
-                const float wt = (float)scale_down(p2, load_w<MODE>(a, off, packed_pos(r, c, s), rinv));
+                const float wt = (float)((load_w<MODE>(a, off, packed_pos(r, c, s), rinv)) * down);
                 Ws[r * LD + c] = wt;
                 Ws[c * LD + r] = wt;
             }
@@ -1072,7 +1066,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
             float acc = 0.f;
 #pragma unroll 8
             for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = scale_up(p2, (double)acc);
+            const double xv = ((double)acc) * up;
             const int pos = packed_pos(ra, cb, s);
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
@@ -1149,12 +1143,12 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
     for (int r = 0; r < 64; ++r) Ts[r * LD + c] = 0.f;
     pair_sync(pair);
     wmax = fmax(redd[0], redd[1]);
-    const int e2 = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
-    const Pow2 p2 = pow2_of(e2);
+    const int e2 = block_exponent(wmax);
+    const double down = pow2_exact(-e2), up = pow2_exact(e2);
     pair_sync(pair);
     if (c < s)
         for (int r = c; r < s; ++r) {
-            const float wt = (float)scale_down(p2, load_w<MODE>(a, off, packed_pos(r, c, s), rinv));
+            const float wt = (float)((load_w<MODE>(a, off, packed_pos(r, c, s), rinv)) * down);
             Ts[r * LD + c] = wt;
             Ts[c * LD + r] = wt;
         }
@@ -1278,7 +1272,7 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
             const float* Qa = Ts + ra * LD;
             float acc = 0.f;
             for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = scale_up(p2, (double)acc);
+            const double xv = ((double)acc) * up;
             const int pos = packed_pos(ra, cb, s);
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
