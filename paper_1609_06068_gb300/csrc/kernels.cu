@@ -294,15 +294,15 @@ __device__ __forceinline__ void finish_and_maybe_finalize(const IterPtrs& P, int
 __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, double rinv, double rho, int use_current) {
     __shared__ double red[2 * kEntThreads + 2];
     pdl_wait();
-    if (P.ctrl->done) return;
+    const bool light = (int)blockIdx.x < P.ent_ctas;
+    const Sched sc = light ? P.ent_sched[blockIdx.x] : P.heavy_sched[blockIdx.x - P.ent_ctas];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
     const bool odd = (P.ctrl->iter & 1) != 0;
     const double* cur = odd ? P.xk[1] : P.xk[0];
     const double* nxt = odd ? P.xk[0] : P.xk[1];
     const double* xn_buf = use_current ? cur : nxt;
     const double* xo_buf = cur;
     double v[2] = {0.0, 0.0};
-    const bool light = (int)blockIdx.x < P.ent_ctas;
-    const Sched sc = light ? P.ent_sched[blockIdx.x] : P.heavy_sched[blockIdx.x - P.ent_ctas];
     if (!use_current && stopped(P, sc.q)) return;
     if (light) {
         const int e = sc.lo + threadIdx.x;
@@ -370,10 +370,10 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_primal(IterPtrs P, doub
 // lane-strided partial sums and a fixed shuffle tree).
 __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double rinv) {
     pdl_wait();
-    if (P.ctrl->done) return;
-    const double* z = P.xk[0];
     const bool light = (int)blockIdx.x < P.ent_ctas;
     const Sched sc = light ? P.ent_sched[blockIdx.x] : P.heavy_sched[blockIdx.x - P.ent_ctas];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
+    const double* z = P.xk[0];
     if (stopped(P, sc.q)) return;
     if (light) {
         const int e = sc.lo + threadIdx.x;
@@ -414,11 +414,11 @@ __global__ void __launch_bounds__(kEntThreads) k_scatter_dual(IterPtrs P, double
 // One warp per chunk of a row (no block-wide reduction); four loads in flight per lane.
 __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
     pdl_wait();
-    if (P.ctrl->done) return;
     const int lane = threadIdx.x & 31;
     const int ch = blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5);
     if (ch >= P.row_chunks) return;
     const Sched sc = P.row_sched[ch];
+    if (P.ctrl->done) return;         // the chunk above is read alongside the flag
     if (stopped(P, sc.q)) return;
     const int hi = sc.hi;
     double a0 = 0.0, a1 = 0.0;
@@ -445,8 +445,8 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_rows(IterPtrs P) {
 __global__ void __launch_bounds__(kTriThreads) k_solve_y(IterPtrs P, double rinv, int form) {
     extern __shared__ double u[];
     pdl_wait();
-    if (P.ctrl->done) return;
     const Sched sc = P.tri_sched[blockIdx.x];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
     if (stopped(P, sc.q)) return;
     const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -485,8 +485,8 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols(IterPtrs P) {
     extern __shared__ double ys[];
     __shared__ double red[33];
     pdl_wait();
-    if (P.ctrl->done) return;
     const Sched sc = P.col_sched[blockIdx.x];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
     if (stopped(P, sc.q)) return;
     const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = P.y[r0 + i];
@@ -541,9 +541,9 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols_split(IterPtrs P) {
     constexpr int NW = kColThreads / 32;
     __shared__ double part[NW][32];
     pdl_wait();
-    if (P.ctrl->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Sched sc = P.col_sched[blockIdx.x];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
     if (stopped(P, sc.q)) return;
     const int sl = sc.lo, len = P.sell_len[sl];
     const int k0 = (int)((long long)len * w / NW), k1 = (int)((long long)len * (w + 1) / NW);
@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(kColThreads) k_spmv_cols_split(IterPtrs P) {
 __global__ void __launch_bounds__(kEntThreads) k_update_dual(IterPtrs P, double rho, double rinv) {
     __shared__ double red[5 * kEntThreads + 5];
     pdl_wait();
-    if (P.ctrl->done) return;
     const Sched sc = P.pos_sched[blockIdx.x];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
     if (stopped(P, sc.q)) return;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     // Four positions per step, all of their loads issued before any arithmetic (one step when a
@@ -777,9 +777,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kConeThreads) k_project_cones(IterPtrs P, double rho, double rinv) {
     __shared__ double red[33 * 3];
     pdl_wait();
-    if (P.ctrl->done) return;
     const int sg = blockIdx.x;
     const int lo = P.cone_lo[sg], hi = P.cone_hi[sg], kind = P.cone_kind[sg];
+    if (P.ctrl->done) return;         // the segment above is read alongside the flag
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (P.ctrl->iter & 1) ? P.xk[0] : P.xk[1];

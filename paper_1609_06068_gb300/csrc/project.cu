@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     __shared__ double red_d[33 * 4];
 
     pdl_wait();
+    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
     if (a.ctrl != nullptr && a.ctrl->done) return;
 
-    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
     const int s = a.size[blk];
     const long long off = a.off[blk];
     if (block_stopped<MODE>(a, blk, s, off)) return;
@@ -566,10 +566,10 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     __shared__ float red_f[33 * 2];
 
     pdl_wait();
+    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
     if (a.ctrl != nullptr && a.ctrl->done) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int NT = 32 * NW;
-    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
     const int s = a.size[blk];
     const long long off = a.off[blk];
     if (block_stopped<MODE>(a, blk, s, off)) return;
