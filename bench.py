@@ -593,7 +593,7 @@ def run_conic(args):
             peaks = json.load(f)
     except (OSError, ValueError):
         pass
-    out = dict(workload=cfg["name"], form=cfg["form"], prec=cfg["prec"], rho=cfg["rho"])
+    out = dict(workload=cfg["name"], form=cfg["form"], prec=cfg["prec"])
     stream = torch.cuda.current_stream()
     if args.profile_iters > 0:
         # a short, fixed sequence of launches for a profiler: reset, then K iterations
@@ -604,9 +604,11 @@ def run_conic(args):
             s.iterate(args.profile_iters)
             torch.cuda.synchronize()
         return
-    for label, a in (("sdp_only", dict(arrs, b=inst.b, cones=None)), ("conic", arrs)):
+    from sdp_inputs import CONFIGS
+    for label, a, rho in (("sdp_only", dict(arrs, b=inst.b, cones=None), CONFIGS[cfg["base"]]["rho"]),
+                          ("conic", arrs, cfg["rho"])):
         t0 = time.perf_counter()
-        opts = cadmm.make_opts(rho=cfg["rho"], tol=0.0, max_iter=cfg["iters"], form=cfg["form"], prec=cfg["prec"])
+        opts = cadmm.make_opts(rho=rho, tol=0.0, max_iter=cfg["iters"], form=cfg["form"], prec=cfg["prec"])
         s = cadmm.ChordalADMM(a, opts)
         torch.cuda.synchronize()
         setup_ms = 1e3 * (time.perf_counter() - t0)
@@ -626,11 +628,17 @@ def run_conic(args):
         phases = cadmm.sdp_time_phases(s.h, reps=20, stream=stream)
         s.set_opts(tol=1e-4, max_iter=2000)
         s.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         r = s.solve()
-        entry = dict(setup_ms=setup_ms, iters_per_s=cfg["iters"] / (med * 1e-3), ms_per_iter=med / cfg["iters"],
+        e1.record(stream)
+        e1.synchronize()
+        entry = dict(rho=rho, setup_ms=setup_ms, iters_per_s=cfg["iters"] / (med * 1e-3), ms_per_iter=med / cfg["iters"],
                      n_cone=s.sizes["n_cone"], nE_lower=s.sizes["nE_lower"], S_lower=s.sizes["S_lower"],
                      nnz_A=s.sizes["nnz_A"], phases_ms=phases,
-                     solve_to_tol=dict(tol=1e-4, iters=r["iters"], status=r["status"], obj_dual=r["obj_dual"],
+                     solve_to_tol=dict(tol=1e-4, iters=r["iters"], status=r["status"], ms=e0.elapsed_time(e1),
+                                       obj_dual=r["obj_dual"],
                                         obj_primal=r["obj_primal"], eps_p=r["eps_p"], eps_d=r["eps_d"]))
         if label == "conic" and "project_cones" in phases:
             nbytes = 24.0 * s.sizes["n_cone"]
