@@ -176,3 +176,39 @@ def test_setup_conic_validates_cones_on_host(lib):
     empty.update(A_ptr=np.zeros(2, np.int64), b=np.ones(1))
     empty["cones"] = sdp_cases.cones_from_dense(np.zeros((1, 0)), np.zeros(0))
     assert _conic_rc(empty)[0] == cadmm.SDP_ERR_ARG
+
+
+def test_concurrent_setups_share_the_worker_pool(lib):
+    """Host setup runs its loops on a process-wide worker pool; a second caller while the pool is
+    busy runs on threads of its own. Concurrent setups (here stopped by the missing GPU after the
+    host build, or completed where a GPU exists) must all return, with the same outcome as a
+    serial one."""
+    import threading
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the host path up to the first CUDA call")
+    arrs = sdp_cases.instance_arrays(__import__("sdp_inputs").config_instance(0))
+
+    def outcome():
+        try:
+            cadmm.ChordalADMM(arrs, cadmm.make_opts())
+            return "ok"
+        except cadmm.SDPError as exc:
+            return exc.code
+    serial = outcome()
+    results = [None] * 6
+    threads = [threading.Thread(target=lambda i=i: results.__setitem__(i, outcome())) for i in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    assert not any(t.is_alive() for t in threads)
+    assert results == [serial] * 6 and serial == cadmm.SDP_ERR_CUDA
+
+
+def test_handle_calls_reject_null_on_host(lib):
+    P = ctypes.c_void_p
+    buf = (ctypes.c_int * 4)()
+    assert lib.sdp_proj_sweeps(None, buf) == cadmm.SDP_ERR_ARG
+    assert lib.sdp_get_sizes(None, None) == cadmm.SDP_ERR_ARG
+    assert lib.sdp_setup_conic(None, None, None, ctypes.byref(P())) == cadmm.SDP_ERR_ARG
