@@ -58,12 +58,14 @@ int worker_count() { return t_serial ? 1 : (int)std::max(1u, std::thread::hardwa
 // loop cost about as much as the loop. One caller at a time runs tasks on it (a concurrent caller,
 // or a process forked from this one, which has no workers, starts threads of its own). The calling
 // thread takes tasks too; the call returns once every task has run and no worker is inside the
-// task loop, so the next call cannot mix with it.
+// task loop, so the next call cannot mix with it. The pool is never destroyed: process exit ends
+// its idle workers, and a forked child, whose copy of the pool has no threads behind it, has
+// nothing to join at its exit.
 class WorkerPool {
 public:
     static WorkerPool& get() {
-        static WorkerPool pool;
-        return pool;
+        static WorkerPool* pool = new WorkerPool();
+        return *pool;
     }
     int threads() const { return (int)th_.size() + 1; }
     // Runs task(t) for t in [0, n); false (nothing run) when another caller holds the pool.
@@ -86,15 +88,6 @@ public:
         task_ = nullptr;
         return true;
     }
-    ~WorkerPool() {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-        }
-        cv_.notify_all();
-        for (auto& t : th_) t.join();
-    }
-
 private:
     WorkerPool() : pid_(getpid()) {
         const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -114,8 +107,7 @@ private:
         for (;;) {
             {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
-                if (stop_) return;
+                cv_.wait(lk, [&] { return gen_ != seen; });
                 seen = gen_;
                 ++active_;
             }
@@ -132,7 +124,6 @@ private:
     int n_ = 0, done_ = 0, active_ = 0;
     std::atomic<int> next_{0};
     unsigned long long gen_ = 0;
-    bool stop_ = false;
 };
 
 // Runs f(i) for i in [0, n) in up to hardware_concurrency contiguous slices.

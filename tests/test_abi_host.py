@@ -212,3 +212,32 @@ def test_handle_calls_reject_null_on_host(lib):
     assert lib.sdp_proj_sweeps(None, buf) == cadmm.SDP_ERR_ARG
     assert lib.sdp_get_sizes(None, None) == cadmm.SDP_ERR_ARG
     assert lib.sdp_setup_conic(None, None, None, ctypes.byref(P())) == cadmm.SDP_ERR_ARG
+
+
+def _fork_child(q):
+    arrs = sdp_cases.instance_arrays(__import__("sdp_inputs").config_instance(0))
+    try:
+        cadmm.ChordalADMM(arrs, cadmm.make_opts())
+        q.put("ok")
+    except cadmm.SDPError as exc:
+        q.put(exc.code)
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")      # fork of a threaded process is the case tested
+def test_forked_child_builds_and_exits_cleanly(lib):
+    """A process forked after the worker pool started (the pool's threads do not exist in it) runs
+    the host build on threads of its own and exits normally."""
+    import multiprocessing as mp
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("forking after CUDA initialisation is not supported")
+    arrs = sdp_cases.instance_arrays(__import__("sdp_inputs").config_instance(0))
+    with pytest.raises(cadmm.SDPError):
+        cadmm.ChordalADMM(arrs, cadmm.make_opts())          # starts the pool in this process
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_fork_child, args=(q,))
+    p.start()
+    p.join(timeout=120)
+    assert p.exitcode == 0
+    assert q.get(timeout=5) == cadmm.SDP_ERR_CUDA
