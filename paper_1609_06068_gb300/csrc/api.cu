@@ -317,7 +317,7 @@ Schedules build_schedules(const sdp_ctx::SchedSource& hp, const std::vector<char
             }
             S.row_chunk[i + 1] = (int)S.row.size();
         }
-    // L^-1 / L^-T products: 8 rows (one per warp) per CTA.
+    // The M^-1 product (k_solve_y): 8 rows (one per warp) per CTA.
     for (int q = 0; q < Q; ++q)
         for (int r = hp.inst_row[q]; r < hp.inst_row[q + 1] && act[q]; r += 8)
             S.tri.push_back({q, r, std::min(r + 8, hp.inst_row[q + 1]), 0});
