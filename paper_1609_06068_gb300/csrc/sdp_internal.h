@@ -155,7 +155,7 @@ struct IterPtrs {
     // Work schedules. The two passes over A are split into warp-sized chunks (8 per CTA); the
     // other kernels give one Sched per CTA.
     const Sched* row_sched; int row_chunks; const int* row_chunk;  // CSR chunks; row_chunk[m+1]
-    const Sched* tri_sched; int tri_ctas;                          // <= 8 rows of L^-1 per CTA
+    const Sched* tri_sched; int tri_ctas;                          // <= 8 rows of M^-1 per CTA (y solve)
     const Sched* col_sched; int col_chunks;                        // slice ranges of A^T
     int col_split;                                                 // 1: one slice per CTA, warps split it
     const Sched* pos_sched; int pos_ctas;                          // packed positions
