@@ -17,7 +17,11 @@ full s×s clique blocks), where all maps are plain Euclidean linear maps:
   (r, b) ↦ x is one more KKT solve with right-hand side [x̄; 0], returning r̄ = x and b̄ = y;
 * the derivative of P₊ at a symmetric W = V diag(λ) Vᵀ is the Daleckii–Krein formula
   DP₊(W)[E] = V (Γ ∘ (Vᵀ E V)) Vᵀ with Γ_ij = (f(λ_i) − f(λ_j)) / (λ_i − λ_j), f = max(·, 0), and
-  f' of the pair's mean where |λ_i − λ_j| ≤ 1e-12 max|λ| (f'(0) taken as 0). It is self-adjoint.
+  f' of the pair's mean where |λ_i − λ_j| ≤ 1e-12 max|λ| (f'(0) taken as 0). It is self-adjoint;
+* cone blocks (Section V's other cones, projected in the primal form onto the cone itself): the
+  free block's projection is the identity, the nonnegative one's derivative is the 0/1 mask of
+  w > 0, and the second-order one's (for ‖u‖ > |t|) is ½[[1, ûᵀ], [û, (1 + t/‖u‖)I − (t/‖u‖)ûûᵀ]]
+  with û = u/‖u‖ (the identity inside the cone, zero inside its polar); all are symmetric.
 
 A full-representation gradient ḡ (∂L/∂ each ordered-pair entry) of a symmetric quantity relates
 to the gradient with respect to its lower-triangle parameters (an off-diagonal parameter moves
@@ -53,6 +57,33 @@ def proj_psd_vjp(W: np.ndarray, Xbar: np.ndarray) -> np.ndarray:
     return V @ (dk_gamma(lam) * Y) @ V.T
 
 
+def proj_soc_vjp(w: np.ndarray, gbar: np.ndarray) -> np.ndarray:
+    """The derivative of the second-order projection at w applied to ḡ (it is symmetric)."""
+    t, u = float(w[0]), np.asarray(w[1:], dtype=np.float64)
+    nu = float(np.sqrt(np.dot(u, u)))
+    if nu <= t:
+        return np.array(gbar, dtype=np.float64)
+    if nu <= -t:
+        return np.zeros(len(w))
+    uh = u / nu
+    gt, gu = float(gbar[0]), np.asarray(gbar[1:], dtype=np.float64)
+    r = t / nu
+    out_t = 0.5 * (gt + float(np.dot(uh, gu)))
+    out_u = 0.5 * gt * uh + 0.5 * ((1.0 + r) * gu - r * float(np.dot(uh, gu)) * uh)
+    return np.concatenate([[out_t], out_u])
+
+
+def proj_cone_vjp(kind: str, w: np.ndarray, gbar: np.ndarray) -> np.ndarray:
+    """The derivative of a cone block's (primal-form) projection at w applied to ḡ."""
+    if kind == "free":
+        return np.array(gbar, dtype=np.float64)
+    if kind == "nonneg":
+        return np.where(np.asarray(w) > 0.0, gbar, 0.0)
+    if kind == "soc":
+        return proj_soc_vjp(w, gbar)
+    raise ValueError(f"unknown cone {kind!r}")
+
+
 def with_data(sdp: ChordalSDP, c_full: np.ndarray | None = None, b: np.ndarray | None = None) -> ChordalSDP:
     """A copy of the problem with a new cost and/or right-hand side (the KKT factor is unchanged:
     it depends on A and D only)."""
@@ -80,19 +111,23 @@ def unrolled_backward(sdp: ChordalSDP, rho: float, states: list, xbar_T: np.ndar
     itself) and ∂L/∂b."""
     rinv = 1.0 / rho
     T = len(states) - 1
-    sizes = [len(c) for c in sdp.cliques]
-    Xb = [np.zeros(s * s) for s in sizes]
-    Lb = [np.zeros(s * s) for s in sizes]
+    K = range(sdp.nblk)
+    Xb = [np.zeros(sdp.block_len(k)) for k in K]
+    Lb = [np.zeros(sdp.block_len(k)) for k in K]
     cbar = np.zeros(sdp.nE)
     bbar = np.zeros(sdp.m)
     for t in range(T, 0, -1):
         prev, cur = states[t - 1], states[t]
         ub, Lpart = [], []
-        for k, s in enumerate(sizes):
-            # λ_k⁺ = λ_k + ρ(x_k⁺ − u_k);  x_k⁺ = P₊(W_k);  W_k = u_k − ρ⁻¹λ_k
+        for k in K:
+            # λ_k⁺ = λ_k + ρ(x_k⁺ − u_k);  x_k⁺ = P(W_k);  W_k = u_k − ρ⁻¹λ_k
             Xt = Xb[k] + rho * Lb[k]
             W = cur["u"][k] - rinv * prev["lam"][k]
-            Wb = _vec(proj_psd_vjp(_mat(W, s), _mat(Xt, s)))
+            if sdp.kinds[k] == "psd":
+                s = len(sdp.cliques[k])
+                Wb = _vec(proj_psd_vjp(_mat(W, s), _mat(Xt, s)))
+            else:
+                Wb = proj_cone_vjp(sdp.kinds[k], W, Xt)
             ub.append(Wb - rho * Lb[k])
             Lpart.append(Lb[k] - rinv * Wb)
         # u_k = H_k x (plus the loss term at the last iteration)
@@ -104,8 +139,8 @@ def unrolled_backward(sdp: ChordalSDP, rho: float, states: list, xbar_T: np.ndar
         bbar += ybar
         # r = Σ H_kᵀ(x_k + ρ⁻¹λ_k) − ρ⁻¹c
         cbar += -rinv * rbar
-        Xb = [sdp.H(k, rbar) for k in range(sdp.p)]
-        Lb = [Lpart[k] + rinv * sdp.H(k, rbar) for k in range(sdp.p)]
+        Xb = [sdp.H(k, rbar) for k in K]
+        Lb = [Lpart[k] + rinv * sdp.H(k, rbar) for k in K]
     return cbar, bbar
 
 

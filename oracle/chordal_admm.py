@@ -255,7 +255,15 @@ class ChordalSDP:
         return x_full[self.lower_mask()]
 
     def from_lower(self, rows, cols, vals) -> np.ndarray:
-        return self._full_from_lower(rows, cols, vals)
+        """Full vector from lower-pattern values; rows n + j (cone variable j, listed as the
+        diagonal pair of a virtual vertex) go to the cone variables."""
+        rows = np.asarray(rows, dtype=np.int64)
+        cols = np.asarray(cols, dtype=np.int64)
+        vals = np.asarray(vals, dtype=np.float64)
+        cone = rows >= self.n
+        full = self._full_from_lower(rows[~cone], cols[~cone], vals[~cone])
+        full[self.nE_mat + (rows[cone] - self.n)] += vals[cone]
+        return full
 
     def block_sizes(self):
         return [len(c) for c in self.cliques]

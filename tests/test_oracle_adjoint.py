@@ -6,7 +6,10 @@ What fixes it, independently of its own code:
   - the whole reverse pass against central differences of the forward iterations, for C (lower
     parameters, perturbed symmetrically) and b, on a small block-arrow problem;
   - planted mistakes in the reverse pass (a dropped b̄ term, a wrong multiplier scaling) that the
-    finite-difference check must catch.
+    finite-difference check must catch;
+  - the cone blocks' derivatives (free, nonnegative, second-order) against central differences
+    of their projections and closed forms, and the reverse pass through a problem with every cone
+    kind against central differences of its forward iterations.
 """
 
 import numpy as np
@@ -147,3 +150,60 @@ def test_planted_mistakes_are_caught(small, monkeypatch):
     # a reverse pass run with the wrong ρ (as if ρ⁻¹ and ρ were swapped) disagrees
     _, gb_rho = adj.unrolled_backward(sdp, 1.0 / 3.0, states, sdp.c + 2 * d)
     assert not np.allclose(gb_rho, fb, rtol=1e-3, atol=1e-6)
+
+
+def test_cone_vjps_match_central_differences():
+    """The cone blocks' derivatives: second-order (off the cone's boundary, where it is smooth)
+    against central differences of the projection; inside the cone the identity, inside its polar
+    zero; the nonnegative mask."""
+    rng = np.random.default_rng(12)
+    h = 1e-6
+    for trial in range(40):
+        q = int(rng.integers(2, 7))
+        w = rng.standard_normal(q)
+        w[0] = rng.uniform(-0.9, 0.9) * np.linalg.norm(w[1:])          # |t| < ||u||: smooth part
+        E, gbar = rng.standard_normal(q), rng.standard_normal(q)
+        fd = np.dot(gbar, orc.proj_soc(w + h * E) - orc.proj_soc(w - h * E)) / (2 * h)
+        an = np.dot(adj.proj_soc_vjp(w, gbar), E)
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (trial, fd, an)
+    w = np.array([3.0, 1.0, -1.0])
+    g = rng.standard_normal(3)
+    np.testing.assert_array_equal(adj.proj_soc_vjp(w, g), g)                        # inside
+    np.testing.assert_array_equal(adj.proj_soc_vjp(-w, g), np.zeros(3))             # polar
+    np.testing.assert_array_equal(adj.proj_cone_vjp("nonneg", np.array([1.0, -1.0]), np.array([2.0, 3.0])), [2.0, 0.0])
+    np.testing.assert_array_equal(adj.proj_cone_vjp("free", np.array([1.0, -1.0]), np.array([2.0, 3.0])), [2.0, 3.0])
+
+
+def test_unrolled_gradient_with_cones_matches_central_differences():
+    """The reverse pass through cone blocks (free, nonnegative, second-order) on a mixed problem,
+    for the cost of matrix entries and of cone variables, and for b."""
+    arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=4, soc_dims=(3, 4), m=6, seed=21)
+    sdp = make_oracle(arrs)
+    rng = np.random.default_rng(13)
+    lower = sdp.lower_mask()
+    x_ref = sdp.from_lower(sdp.E_row[lower], sdp.E_col[lower], rng.standard_normal(int(lower.sum())))
+    rho, T = 0.8, 15
+    L, gc, gb, _ = adj.loss_and_grad(sdp, rho, T, x_ref)
+    n_mat = int(lower.sum()) - sdp.n_cone
+    ic = np.concatenate([rng.choice(n_mat, size=4, replace=False), n_mat + np.arange(sdp.n_cone)])
+    ib = np.arange(sdp.m)
+    fc, fb = fd_grads(sdp, rho, T, x_ref, ic, ib)
+    scale = max(np.abs(gc).max(), np.abs(gb).max())
+    np.testing.assert_allclose(gc[ic], fc, rtol=1e-5, atol=1e-6 * scale)
+    np.testing.assert_allclose(gb, fb, rtol=1e-5, atol=1e-6 * scale)
+
+
+def test_planted_soc_derivative_mistake_is_caught(monkeypatch):
+    """A dropped ûûᵀ term in the second-order derivative fails the difference check."""
+    def wrong(w, gbar):
+        t, u = float(w[0]), np.asarray(w[1:])
+        nu = float(np.linalg.norm(u))
+        if nu <= t:
+            return np.array(gbar, float)
+        if nu <= -t:
+            return np.zeros(len(w))
+        uh, gt, gu = u / nu, float(gbar[0]), np.asarray(gbar[1:])
+        return np.concatenate([[0.5 * (gt + uh @ gu)], 0.5 * gt * uh + 0.5 * (1 + t / nu) * gu])
+    monkeypatch.setattr(adj, "proj_soc_vjp", wrong)
+    with pytest.raises(AssertionError):
+        test_cone_vjps_match_central_differences()
