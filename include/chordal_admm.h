@@ -201,8 +201,9 @@ typedef struct {
 
 /* sdp_setup for a problem with cone variables beside the PSD matrix. `problem` holds the matrix
  * part as in sdp_setup (n = 0 with p = 0 and no matrix data: no PSD part at all); `cones` may be
- * NULL (then this is sdp_setup). Host pointers, copied. Not available for batches or
- * sdp_unrolled_forward / sdp_unrolled_backward (SDP_ERR_UNSUPPORTED there).
+ * NULL (then this is sdp_setup). Host pointers, copied. Not available for batches;
+ * sdp_unrolled_forward / sdp_unrolled_backward take the cone blocks too (their projections'
+ * derivatives: identity, the mask of w > 0, the second-order closed form).
  * Errors: as sdp_setup; SDP_ERR_ARG for negative cone sizes, a second-order cone of dimension
  * < 1, no variables at all, or a cone variable index out of range. */
 int sdp_setup_conic(const sdp_problem* problem, const sdp_cones* cones, const admm_opts* opts,

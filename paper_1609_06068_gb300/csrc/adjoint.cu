@@ -189,6 +189,92 @@ cudaError_t adjoint_prepare() {
     return cudaFuncSetAttribute(k_dk_vjp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VjpLayout<32>::kBytes);
 }
 
+// Cone blocks (free, nonnegative, second-order; projected onto the cone itself in the primal
+// form): the derivative of the projection is the identity (free), the mask of W > 0 (nonnegative),
+// and for a second-order cone (t, u) with ||u|| > |t| the symmetric
+// 1/2 [[1, uh^T], [uh, (1 + t/||u||) I - (t/||u||) uh uh^T]], uh = u / ||u|| (the identity inside
+// the cone, zero inside its polar). Same epilogue as the cliques. One CTA per forward segment: a
+// run of free or nonnegative positions, one large second-order cone, or up to 256 small ones (a
+// thread each). Every position's X~ is read before its Lb is written.
+__device__ __forceinline__ void cone_vjp_out(int pos, double wbar, double* Lb, double* ub, double rho, double rinv) {
+    const double lb = Lb[pos];
+    ub[pos] = wbar - rho * lb;
+    Lb[pos] = lb - rinv * wbar;
+}
+
+__device__ __forceinline__ double soc_vjp_elem(bool first, double w, double g, double gt, double t, double nu,
+                                               double dot) {
+    if (nu <= t) return g;                      // inside the cone: identity
+    if (nu <= -t) return 0.0;                   // inside the polar cone: zero
+    if (first) return 0.5 * (gt + dot);
+    const double r = t / nu, uh = w / nu;
+    return 0.5 * gt * uh + 0.5 * ((1.0 + r) * g - r * dot * uh);
+}
+
+__global__ void __launch_bounds__(256) k_cone_vjp(IterPtrs P, const double* __restrict__ W,
+                                                  const double* __restrict__ Xb, double* __restrict__ Lb,
+                                                  double* __restrict__ ub, double rho, double rinv) {
+    __shared__ double red[2][8];
+    const int sg = blockIdx.x;
+    const int lo = P.cone_lo[sg], hi = P.cone_hi[sg], kind = P.cone_kind[sg];
+    if (kind == kConeSocSmall) {
+        const int c = lo + (int)threadIdx.x;
+        if (c >= hi) return;
+        const int p0 = P.soc_pos[c], q = P.soc_q[c];
+        const double t = W[p0], gt = Xb[p0] + rho * Lb[p0];
+        double nn = 0.0, ug = 0.0;
+        for (int j = 1; j < q; ++j) {
+            const double u = W[p0 + j];
+            nn = fma(u, u, nn);
+            ug = fma(u, Xb[p0 + j] + rho * Lb[p0 + j], ug);
+        }
+        const double nu = sqrt(nn), dot = nu > 0.0 ? ug / nu : 0.0;
+        cone_vjp_out(p0, soc_vjp_elem(true, t, gt, gt, t, nu, dot), Lb, ub, rho, rinv);
+        for (int j = 1; j < q; ++j) {
+            const double g = Xb[p0 + j] + rho * Lb[p0 + j];
+            cone_vjp_out(p0 + j, soc_vjp_elem(false, W[p0 + j], g, gt, t, nu, dot), Lb, ub, rho, rinv);
+        }
+        return;
+    }
+    if (kind == kConeSoc) {
+        // both sums over the cone in a fixed order: a strided partial per thread, then the warps'
+        // shuffle trees and the warps in order
+        double nn = 0.0, ug = 0.0;
+        for (int pos = lo + 1 + (int)threadIdx.x; pos < hi; pos += blockDim.x) {
+            const double u = W[pos];
+            nn = fma(u, u, nn);
+            ug = fma(u, Xb[pos] + rho * Lb[pos], ug);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            nn += __shfl_xor_sync(0xffffffffu, nn, o);
+            ug += __shfl_xor_sync(0xffffffffu, ug, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = nn;
+            red[1][threadIdx.x >> 5] = ug;
+        }
+        __syncthreads();
+        nn = 0.0;
+        ug = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            nn += red[0][w];
+            ug += red[1][w];
+        }
+        const double t = W[lo], gt = Xb[lo] + rho * Lb[lo];
+        const double nu = sqrt(nn), dot = nu > 0.0 ? ug / nu : 0.0;
+        __syncthreads();                        // every thread has read X~ at lo before it changes
+        for (int pos = lo + (int)threadIdx.x; pos < hi; pos += blockDim.x) {
+            const double g = Xb[pos] + rho * Lb[pos];
+            cone_vjp_out(pos, soc_vjp_elem(pos == lo, W[pos], g, gt, t, nu, dot), Lb, ub, rho, rinv);
+        }
+        return;
+    }
+    for (int pos = lo + (int)threadIdx.x; pos < hi; pos += blockDim.x) {
+        const double g = Xb[pos] + rho * Lb[pos];
+        cone_vjp_out(pos, kind == kConeFree ? g : (W[pos] > 0.0 ? g : 0.0), Lb, ub, rho, rinv);
+    }
+}
+
 cudaError_t launch_form_w(const IterPtrs& P, const double* lam_prev, double rinv, double* W, cudaStream_t st) {
     k_form_w<<<grid_for(P.SL), 256, 0, st>>>(P, lam_prev, rinv, W);
     return cudaGetLastError();
@@ -209,6 +295,7 @@ cudaError_t launch_dk_vjp(const IterPtrs& P, int n_large, const double* W, const
         k_dk_vjp<16><<<(rest + L::BPC - 1) / L::BPC, 128, L::kBytes, st>>>(P, P.order + n_large, rest, W, V, Xb, Lb,
                                                                           ub, rho, rinv);
     }
+    if (P.ncs > 0) k_cone_vjp<<<P.ncs, 256, 0, st>>>(P, W, Xb, Lb, ub, rho, rinv);
     return cudaGetLastError();
 }
 

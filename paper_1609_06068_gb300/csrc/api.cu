@@ -1120,7 +1120,6 @@ int sdp_unrolled_forward(sdp_handle h, int T, int ckpt_every, double* x_out, voi
     if (h->opts.form != SDP_PRIMAL || h->opts.prec != SDP_PROJ_FP64)
         return set_err(SDP_ERR_ARG, "unrolled differentiation needs form SDP_PRIMAL and prec SDP_PROJ_FP64");
     if (h->smax > 32) return set_err(SDP_ERR_UNSUPPORTED, "unrolled differentiation takes cliques of order <= 32");
-    if (h->n_cone > 0) return set_err(SDP_ERR_UNSUPPORTED, "unrolled differentiation takes PSD cones only");
     CK(cudaSetDevice(h->device));
     cudaStream_t st = as_stream(cuda_stream);
     try {

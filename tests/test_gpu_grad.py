@@ -137,3 +137,24 @@ def test_workload_gradient_matches_oracle_and_differences(workload4, capsys):
     with capsys.disabled():
         print(f"\nunrolled T={T}, 64 problems: loss {L:.6e}, forward {t_fwd * 1e3:.1f} ms, forward+backward "
               f"{t_grad * 1e3:.1f} ms, worst finite-difference disagreement {worst:.2e}")
+
+
+@pytest.mark.parametrize("T,K", [(12, 5)])
+def test_gradient_with_cones_matches_oracle(T, K):
+    """Reverse mode through a problem with free, nonnegative and second-order variables (small
+    and large second-order cones) against the oracle's reference gradient."""
+    torch, cadmm = require_gpu()
+    arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=5, soc_dims=(3, 1, 300), m=6, seed=31)
+    sdp = make_oracle(arrs)
+    rng = np.random.default_rng(17)
+    lower = sdp.lower_mask()
+    xr = rng.standard_normal(int(lower.sum()))
+    x_ref = sdp.from_lower(sdp.E_row[lower], sdp.E_col[lower], xr)
+    rho = 0.8
+    L0, gc0, gb0, _ = adj.loss_and_grad(sdp, rho, T, x_ref)
+    with primal_handle(cadmm, arrs, rho) as s:
+        L, gc, gb = gpu_grad(cadmm, torch, s.h, sdp.to_lower(sdp.c), sdp.b, xr, T, K)
+    assert abs(L - L0) <= 1e-10 * abs(L0)
+    scale = max(np.abs(gc0).max(), np.abs(gb0).max())
+    np.testing.assert_allclose(gc, gc0, rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(gb, gb0, rtol=0, atol=1e-9 * scale)
