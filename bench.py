@@ -202,6 +202,9 @@ def kernel_model(name, inst_sizes, cfg, prec):
     with vectors, Golub & Van Loan) plus 2 s^3 for the rebuild V diag(lambda+) V^T."""
     s, p = inst_sizes["s_list"], inst_sizes["p"]
     nEL, SL, m, nnz = inst_sizes["nEL"], inst_sizes["SL"], inst_sizes["m"], inst_sizes["nnz"]
+    if name == "project_cones":
+        # read v_k (or x at the gather index) and lambda_k, write z_k (dual form): 24 B a position
+        return "hbm", 24.0 * inst_sizes.get("n_cone", 0), "byte"
     if name.startswith("project"):
         flops = sum(11.0 * si ** 3 for si in s)
         return "alu", flops, "flop"
@@ -343,7 +346,7 @@ def run_ours(args):
     sz = solver.sizes
     insts = inst if batch else [inst]
     s_list = [len(c) for x in insts for c in x.cliques]
-    inst_sizes = dict(s_list=s_list, p=sz["p"], nEL=sz["nE_lower"], SL=sz["S_lower"], m=sz["m"],
+    inst_sizes = dict(s_list=s_list, p=sz["p"], nEL=sz["nE_lower"], SL=sz["S_lower"], m=sz["m"], n_cone=sz["n_cone"],
                       nnz=sz["nnz_A"])
     stream = torch.cuda.current_stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")

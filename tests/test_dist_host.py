@@ -64,3 +64,18 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_model_covers_every_phase():
+    """Every phase name the library reports gets a nonzero algorithmic-work model in bench.py (a
+    missing name would put a zero into the roofline line)."""
+    import bench
+    sizes = dict(s_list=[30] * 100, p=100, nEL=25710, SL=46500, m=200, nnz=1542600, n_cone=1000)
+    names = ["project_dual", "project_primal", "project_cones", "scatter_dual", "scatter_primal",
+             "scatter_primal+finalize", "spmv_rows", "solve_y", "spmv_cols", "update_dual",
+             "update_dual+finalize"]
+    for name in names:
+        bound, amount, unit = bench.kernel_model(name, sizes, {}, "fp32")
+        assert amount > 0, name
+        assert (bound, unit) in (("alu", "flop"), ("hbm", "byte")), name
+    assert bench.kernel_model("project_cones", sizes, {}, "fp32")[0] == "hbm"
