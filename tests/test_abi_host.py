@@ -241,3 +241,34 @@ def test_forked_child_builds_and_exits_cleanly(lib):
     p.join(timeout=120)
     assert p.exitcode == 0
     assert q.get(timeout=5) == cadmm.SDP_ERR_CUDA
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structs of the binding have the C header's sizes and field offsets (a mismatch
+    would pass garbage through the ABI silently). gcc compiles a probe that prints them."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"admm_opts": cadmm.admm_opts, "admm_result": cadmm.admm_result, "sdp_sizes": cadmm.sdp_sizes,
+               "sdp_problem": cadmm.sdp_problem, "sdp_cones": cadmm.sdp_cones}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chordal_admm.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for line in out:
+        if line:
+            name, field, value = line.split()
+            c_layout[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert c_layout[(name, field)] == getattr(cls, field).offset, (name, field)
