@@ -209,6 +209,12 @@ typedef struct {
 int sdp_setup_conic(const sdp_problem* problem, const sdp_cones* cones, const admm_opts* opts,
                     sdp_handle* out);
 
+/* Host-only planning of a problem (needs no GPU): runs sdp_setup_conic's host work (validation,
+ * chordal extension when p = 0, index maps, A D^-1 A^T and its factorization) and reports the sizes
+ * a handle would have (batch = 1), so a caller can check a problem and size its device memory
+ * first. cones may be NULL. Errors: as sdp_setup_conic, except SDP_ERR_CUDA. */
+int sdp_plan(const sdp_problem* problem, const sdp_cones* cones, sdp_sizes* out);
+
 /* Chordal extension of a sparse symmetric pattern (Section II.A: a non-chordal aggregate pattern is
  * first extended to a chordal one; the paper leaves the extension to heuristics) and the maximal
  * cliques of the extension. Ordering by maximum cardinality search (ties: smallest vertex index),

@@ -43,7 +43,7 @@ EXPORTS = [
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
     "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_set_cost",
-    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_proj_sweeps", "sdp_free",
+    "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_proj_sweeps", "sdp_plan", "sdp_free",
     "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
@@ -137,6 +137,7 @@ def load_library(path: str = LIB_PATH):
         "sdp_set_cost": (_I, [_P, _P, _P]),
         "sdp_set_rhs": (_I, [_P, _P, _P]),
         "sdp_proj_sweeps": (_I, [_P, _P]),
+        "sdp_plan": (_I, [ctypes.POINTER(sdp_problem), ctypes.POINTER(sdp_cones), ctypes.POINTER(sdp_sizes)]),
         "sdp_unrolled_forward": (_I, [_P, _I, _I, _P, _P]),
         "sdp_unrolled_backward": (_I, [_P, _P, _P, _P, _P]),
         "sdp_free": (None, [_P]),
@@ -285,6 +286,21 @@ def sdp_setup_conic(problem: dict, cones: dict | None, opts=None):
     _check(lib.sdp_setup_conic(ctypes.byref(pr), ctypes.byref(cs) if cs is not None else None,
                                ctypes.byref(opts), ctypes.byref(h)), "sdp_setup_conic")
     return h
+
+
+def sdp_plan(problem: dict, cones: dict | None = None) -> dict:
+    """Host-only check and sizes of a problem (sdp_setup's arguments as a dict; cones as for
+    sdp_setup_conic): the sizes a handle would have, without a GPU."""
+    lib = load_library()
+    d = _problem_arrays(**{k: v for k, v in problem.items() if k in _PROBLEM_KEYS})
+    pr = _problem_struct(d)
+    cd = _cone_arrays(cones) if cones is not None else None
+    cs = None if cd is None else sdp_cones(cd["n_free"], cd["n_lin"], len(cd["soc_dims"]), _ptr(cd["soc_dims"]),
+                                           _ptr(cd["A_ptr"]), _ptr(cd["A_var"]), _ptr(cd["A_val"]), _ptr(cd["c"]))
+    out = sdp_sizes()
+    _check(lib.sdp_plan(ctypes.byref(pr), ctypes.byref(cs) if cs is not None else None, ctypes.byref(out)),
+           "sdp_plan")
+    return {f: getattr(out, f) for f, _ in sdp_sizes._fields_}
 
 
 _PROBLEM_KEYS = ("n", "A_ptr", "A_row", "A_col", "A_val", "b", "C_row", "C_col", "C_val", "cliques",

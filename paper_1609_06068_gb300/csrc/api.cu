@@ -741,6 +741,33 @@ int sdp_setup_conic(const sdp_problem* pr, const sdp_cones* cones, const admm_op
     }
 }
 
+int sdp_plan(const sdp_problem* pr, const sdp_cones* cones, sdp_sizes* out) {
+    try {
+        if (!pr || !out) return set_err(SDP_ERR_ARG, "NULL argument");
+        HostProblem hp;
+        std::string err;
+        const int rc = cadmm::build_host_problem(pr->n, pr->m, pr->A_ptr, pr->A_row, pr->A_col, pr->A_val, pr->b,
+                                                 pr->C_nnz, pr->C_row, pr->C_col, pr->C_val, pr->pat_nnz,
+                                                 pr->pat_row, pr->pat_col, pr->p, pr->clique_ptr, pr->clique_vtx,
+                                                 cones, hp, err);
+        if (rc) return set_err(rc, err);
+        out->n = hp.n;
+        out->m = hp.m;
+        out->p = hp.p;
+        out->max_clique = hp.smax;
+        out->nE_lower = hp.nEL;
+        out->S_lower = hp.SL;
+        out->nnz_A = hp.nnz;
+        out->batch = 1;
+        out->n_cone = hp.n_cone;
+        return SDP_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(SDP_ERR_ARG, "host out of memory");
+    } catch (...) {
+        return set_err(SDP_ERR_ARG, "unexpected exception in sdp_plan");
+    }
+}
+
 int sdp_setup_batch(int count, const sdp_problem* problems, const admm_opts* opts, sdp_handle* out) {
     try {
         if (!out) return set_err(SDP_ERR_ARG, "out is NULL");

@@ -272,3 +272,53 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert c_layout[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def _oracle_of(arrs):
+    from tests.gpu_support import make_oracle
+    return make_oracle(arrs)
+
+
+@pytest.mark.parametrize("name", ["config0", "block_arrow", "conic", "pure_cones", "theta", "non_chordal"])
+def test_plan_sizes_match_the_oracle(lib, name):
+    """sdp_plan (the host build alone, no GPU) against the oracle's representation: lower pattern
+    entries (cone variables included), packed positions, cliques, largest clique and the stored
+    nonzeros of A on the lower pattern after duplicates merge."""
+    from oracle import chordal as och
+    if name == "config0":
+        arrs = sdp_cases.instance_arrays(__import__("sdp_inputs").config_instance(0))
+    elif name == "block_arrow":
+        arrs = sdp_cases.random_block_arrow(l=4, d=3, h=2, m=6, seed=2)
+    elif name == "conic":
+        arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=4, soc_dims=(3, 1, 40), m=6, seed=21)
+    elif name == "pure_cones":
+        arrs = sdp_cases.random_conic(l=0, n_free=2, n_lin=7, soc_dims=(4, 2), m=5, seed=22)
+    elif name == "theta":
+        arrs = sdp_cases.theta_c5()[0]
+    else:
+        arrs = sdp_cases.random_sparse_sdp(n=24, m=8, seed=5)
+        rows = np.concatenate([arrs["A_row"], arrs["C_row"]])
+        cols = np.concatenate([arrs["A_col"], arrs["C_col"]])
+        cliques, _ = och.chordal_extension(arrs["n"], rows, cols)
+        ref_arrs = dict(arrs, cliques=[np.array(c, np.int32) for c in cliques])
+    sz = cadmm.sdp_plan(arrs, arrs.get("cones"))
+    sdp = _oracle_of(ref_arrs if name == "non_chordal" else arrs)
+    lower = sdp.lower_mask()
+    assert sz["p"] == sdp.p and sz["n_cone"] == sdp.n_cone and sz["batch"] == 1
+    assert sz["nE_lower"] == int(lower.sum())
+    assert sz["S_lower"] == sum(len(c) * (len(c) + 1) // 2 for c in sdp.cliques) + sdp.n_cone
+    assert sz["max_clique"] == max([len(c) for c in sdp.cliques], default=0)
+    assert sz["nnz_A"] == int((sdp.A[:, np.flatnonzero(lower)] != 0).sum())
+
+
+def test_plan_reports_host_errors(lib):
+    arrs = sdp_cases.random_block_arrow(l=3, d=2, h=2, m=4)
+    bad = dict(arrs)
+    bad["b"] = np.concatenate([arrs["b"], arrs["b"][:1]])
+    bad["A_ptr"] = np.concatenate([arrs["A_ptr"], arrs["A_ptr"][-1:] + 0])    # an empty constraint
+    with pytest.raises(cadmm.SDPError) as exc:
+        cadmm.sdp_plan(bad)
+    assert exc.value.code == cadmm.SDP_ERR_NOT_PD
+    with pytest.raises(cadmm.SDPError) as exc:
+        cadmm.sdp_plan(dict(arrs, cliques=[np.array([1, 0], np.int32)]))
+    assert exc.value.code == cadmm.SDP_ERR_CLIQUE
