@@ -21,7 +21,9 @@ Readings where the paper is silent (each one also listed in the design notes):
   ``ε_d = ρ‖Σ H_kᵀ(x_k⁺ − x_k)‖ / max(‖Σ H_kᵀ λ_k⁺‖, 1e-12)``; dual form
   ``ε_p = ‖[z_k − v_k]‖ / max(‖[z_k]‖, ‖[v_k]‖, 1e-12)`` and
   ``ε_d = ρ‖[v_k⁺ − v_k]‖ / max(‖[λ_k⁺]‖, 1e-12)``. Norms are Euclidean over the stacked vectors.
-  Iteration ``n`` stops the loop when ``max(ε_p, ε_d) < tol``.
+  Iteration ``n`` stops the loop when ``max(ε_p, ε_d) < tol``. Each iteration also returns the
+  four norms (``res_p``/``res_p_den``, ``res_d``/``res_d_den``) so that the tests can compare them
+  with Boyd's residuals of the splitting, built from explicit matrices.
 * Initial iterates are zero; the paper leaves them to the user.
 * The affine step is solved by block elimination (the paper's "e.g."), with ``A D⁻¹ Aᵀ`` factored once.
 * Eq. (DualMultUpdate) is printed as ``λ_k = ρ H_k x``; substituting Eq. (vkEqn) into
@@ -362,9 +364,11 @@ def primal_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     pri_den = max(_norm_blocks(xk_new), _norm_blocks(u), 1e-12)
     dres = sdp.HT_sum([xk_new[k] - st["xk"][k] for k in K])
     dual_den = max(float(np.linalg.norm(sdp.HT_sum(lam_new))), 1e-12)
+    dual_num = rho * float(np.linalg.norm(dres))
     out = dict(st)
     out.update(iter=st["iter"] + 1, x=x, y=y, xk=xk_new, lam=lam_new, r=r, u=u,
-               eps_p=pri / pri_den, eps_d=rho * float(np.linalg.norm(dres)) / dual_den,
+               eps_p=pri / pri_den, eps_d=dual_num / dual_den,
+               res_p=pri, res_p_den=pri_den, res_d=dual_num, res_d_den=dual_den,
                obj_primal=float(np.dot(sdp.c, x)), obj_dual=float(np.dot(sdp.b, -rho * y)))
     return out
 
@@ -393,6 +397,7 @@ def dual_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     out.update(iter=st["iter"] + 1, x=x, y=y, zk=zk, vk=vk_new, lam=lam_new, r=r, u=u,
                lam_general=lam_general,
                eps_p=pri / pri_den, eps_d=rho * dres / dual_den,
+               res_p=pri, res_p_den=pri_den, res_d=rho * dres, res_d_den=dual_den,
                obj_dual=float(np.dot(sdp.b, y)), obj_primal=float(np.dot(sdp.c, -rho * x)))
     return out
 

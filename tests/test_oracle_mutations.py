@@ -82,3 +82,40 @@ def test_dropped_cost_term_is_caught(monkeypatch):
     orig = orc.primal_iteration
     monkeypatch.setattr(orc, "primal_iteration", no_cost)
     _expect_pin_failure(pins.test_lovasz_theta_c5)
+
+
+def test_dropped_rho_in_dual_residual_is_caught(monkeypatch):
+    orig = orc.primal_iteration
+
+    def no_rho(sdp, st, rho):
+        out = orig(sdp, st, rho)
+        out["res_d"] = out["res_d"] / rho
+        out["eps_d"] = out["res_d"] / out["res_d_den"]
+        return out
+    monkeypatch.setattr(orc, "primal_iteration", no_rho)
+    _expect_pin_failure(pins.test_stopping_measures_match_boyd_residuals, "primal")
+
+
+def test_old_multiplier_in_dual_denominator_is_caught(monkeypatch):
+    orig = orc.dual_iteration
+
+    def old_lam(sdp, st, rho):
+        out = orig(sdp, st, rho)
+        out["res_d_den"] = max(float(np.sqrt(sum(float(np.dot(v, v)) for v in st["lam"]))), 1e-12)
+        out["eps_d"] = out["res_d"] / out["res_d_den"]
+        return out
+    monkeypatch.setattr(orc, "dual_iteration", old_lam)
+    _expect_pin_failure(pins.test_stopping_measures_match_boyd_residuals, "dual")
+
+
+def test_primal_residual_against_wrong_iterate_is_caught(monkeypatch):
+    orig = orc.dual_iteration
+
+    def stale_v(sdp, st, rho):
+        out = orig(sdp, st, rho)
+        # z_k − v_k against the previous v_k instead of the one just computed
+        out["res_p"] = float(np.sqrt(sum(float(np.dot(z - v, z - v)) for z, v in zip(out["zk"], st["vk"]))))
+        out["eps_p"] = out["res_p"] / out["res_p_den"]
+        return out
+    monkeypatch.setattr(orc, "dual_iteration", stale_v)
+    _expect_pin_failure(pins.test_stopping_measures_match_boyd_residuals, "dual")

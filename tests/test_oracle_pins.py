@@ -297,3 +297,62 @@ def test_primal_dual_are_scaled_versions(cfg0):
     rd = orc.admm_solve(sdp, "dual", rho=0.1, tol=1e-4, max_iter=2000)
     assert abs(rp["iters"] - rd["iters"]) <= 1
     assert abs(rp["obj_primal"] - rd["obj_primal"]) <= 1e-6 * abs(rp["obj_primal"])
+
+
+# ------------------------------------------------- stopping measures (Sec. III.B, Sec. IV.B)
+
+def _stacked_selector(sdp):
+    """[H_1; …; H_p] restricted to the pattern pairs E, built from E_k ⊗ E_k (dense)."""
+    n = sdp.n
+    on_E = sdp.E_col * n + sdp.E_row
+    return np.vstack([explicit_H(n, c)[:, on_E] for c in sdp.cliques])
+
+
+def _boyd_measures(A_B, B_B, c_B, xB, zB, zB_prev, yB, rho):
+    """Relative primal and dual residuals of ADMM for min f(x) + g(z) s.t. A x + B z = c
+    (Boyd et al. 2011, Sec. 3.3): r = A x⁺ + B z⁺ − c over max(‖A x⁺‖, ‖B z⁺‖, ‖c‖), and
+    s = ρ Aᵀ B (z⁺ − z) over ‖Aᵀ y⁺‖, y the unscaled multiplier."""
+    r = A_B @ xB + B_B @ zB - c_B
+    s = rho * (A_B.T @ (B_B @ (zB - zB_prev)))
+    return (np.linalg.norm(r), max(np.linalg.norm(A_B @ xB), np.linalg.norm(B_B @ zB), np.linalg.norm(c_B)),
+            np.linalg.norm(s), np.linalg.norm(A_B.T @ yB))
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_stopping_measures_match_boyd_residuals(form):
+    """ε_p and ε_d are Boyd's relative residuals of the paper's splitting, assembled here from
+    explicit matrices rather than from the oracle's helpers.
+
+    Primal form (Eq. AugLagrPrimal): the first block is x, the second the stacked x_k, and the
+    constraint x_k − H_k x = 0 carries λ_k, so A = −[H_k], B = I, c = 0, y = [λ_k].
+    Dual form (Eq. AugLagrDual, Algorithm 2 minimising over 𝒴 before 𝒳): the first block is the
+    stacked z_k, the second (y, v_k), and z_k − v_k = 0 carries λ_k, so A = I, B = [0, −I], c = 0.
+    """
+    arrs = sdp_cases.random_block_arrow(l=3, d=2, h=2, m=4)
+    sdp = make_sdp(arrs)
+    rho = 0.7                          # ≠ 1, so that a lost factor ρ shows
+    H = _stacked_selector(sdp)
+    nS = H.shape[0]
+    st = orc.admm_init(sdp, form)
+    step = orc.primal_iteration if form == "primal" else orc.dual_iteration
+    for it in range(4):
+        prev = st
+        st = step(sdp, st, rho)
+        if form == "primal":
+            A_B, B_B = -H, np.eye(nS)
+            xB = st["x"]
+            zB, zB_prev = np.concatenate(st["xk"]), np.concatenate(prev["xk"])
+        else:
+            A_B = np.eye(nS)
+            B_B = np.hstack([np.zeros((nS, sdp.m)), -np.eye(nS)])
+            xB = np.concatenate(st["zk"])
+            zB = np.concatenate([st["y"], np.concatenate(st["vk"])])
+            zB_prev = np.concatenate([prev["y"], np.concatenate(prev["vk"])])
+        yB = np.concatenate(st["lam"])
+        rp, rp_den, rd, rd_den = _boyd_measures(A_B, B_B, np.zeros(nS), xB, zB, zB_prev, yB, rho)
+        assert rp > 0 and rd > 0
+        for got, want in ((st["res_p"], rp), (st["res_p_den"], rp_den), (st["res_d"], rd),
+                          (st["res_d_den"], rd_den)):
+            assert abs(got - want) <= 1e-13 * want, (form, it, got, want)
+        assert st["eps_p"] == st["res_p"] / st["res_p_den"]
+        assert st["eps_d"] == st["res_d"] / st["res_d_den"]
