@@ -215,6 +215,8 @@ def kernel_model(name, inst_sizes, cfg, prec):
 
     if name == "solve_y":
         return "hbm", m * m * 8.0 + 2 * m * 8.0, "byte"
+    if name in ("tri_lower", "tri_upper"):
+        return "hbm", m * (m + 1) / 2 * 8.0 + 2 * m * 8.0, "byte"
     if name.startswith("scatter_dual"):
         return "hbm", SL * (8 * 2 + 4) + nEL * (4 + 8 + 8 * 2 + 8 + 1), "byte"
     if name.startswith("scatter_primal"):

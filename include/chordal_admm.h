@@ -287,8 +287,9 @@ int sdp_scatter(sdp_handle h, const double* blocks, double* out, void* cuda_stre
  * in and out are DEVICE pointers to packed lower blocks (FP64); sizes[count] and offsets[count]
  * are HOST arrays giving each block's order (1 <= s <= SDP_MAX_CLIQUE) and its element offset in
  * in/out. prec selects FP64 or FP32 eigensolves (results are FP64 either way). Blocks run in one
- * launch, largest first. The call allocates a small stream-ordered device schedule. in == out is
- * allowed; blocks must not overlap otherwise. */
+ * launch, largest first. The call allocates a small stream-ordered device schedule, copied from a
+ * host buffer of the call, so it cannot be captured in a CUDA graph: on a capturing stream it
+ * returns SDP_ERR_UNSUPPORTED. in == out is allowed; blocks must not overlap otherwise. */
 int project_psd_batched(const double* in, double* out, const int* sizes, const long long* offsets,
                         int count, int prec, void* cuda_stream);
 
@@ -363,10 +364,14 @@ const char* sdp_phase_name(sdp_handle h, int i);
  *   - count > SDP_NOALLOC_MAX_BLOCKS returns SDP_ERR_UNSUPPORTED; other errors as for
  *     project_psd_batched.
  *   - The first call on each device looks up the array's device address and prepares the kernels;
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture. After cudaDeviceReset the next call on that
+ *     device repeats this set-up (every call checks the address).
+ *   - sizes and offsets are host arrays (pageable or pinned), copied before the call returns:
+ *     the caller may change or free them as soon as it has returned.
  *   - Every call reuses the same array, which keeps the last call's schedule. Each call
  *     overwrites every entry it reads, so nothing needs clearing, but calls that overlap on the
  *     GPU (e.g. on two streams) race on the array: order them on one stream or synchronize.
+ *   - in == out is allowed (each block is read before it is written, by the same CTA).
  *   - Blocks run in the caller's order rather than largest first. */
 #define SDP_NOALLOC_MAX_BLOCKS 32768
 int project_psd_batched_noalloc(const double* in, double* out, const int* sizes,

@@ -467,6 +467,12 @@ int run_project_batched(const double* in, double* out, const int* sizes, const l
     for (int k = 0; k < count; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
     cudaStream_t st = as_stream(cuda_stream);
+    // The schedule is copied from a host buffer that lives for this call only: a captured copy
+    // would read it again at every replay, after it is gone. Capture is refused.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_err(SDP_ERR_UNSUPPORTED, "project_psd_batched cannot be captured in a CUDA graph");
     CK(cadmm::project_prepare());
     // One stream-ordered device buffer holds offsets, sizes and order.
     const size_t bytes = (size_t)count * (2 * sizeof(int) + sizeof(long long));
@@ -648,7 +654,14 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(sell_off, hp.sell_off);
     UP(sell_row, hp.sell_row);
     UP(sell_val, hp.sell_val);
-    UP(Minv, hp.Minv);
+    P.kkt_tri = hp.kkt_tri ? 1 : 0;
+    if (hp.kkt_tri) {
+        UP(Linv, hp.Linv);
+        UP(LinvT, hp.LinvT);
+        if ((rc = h->dalloc(&P.z1, (size_t)std::max(1, hp.m)))) return rc;
+    } else {
+        UP(Minv, hp.Minv);
+    }
     UP(cone_lo, hp.cone_lo);
     UP(cone_hi, hp.cone_hi);
     UP(cone_kind, hp.cone_kind);
@@ -1033,7 +1046,7 @@ int project_variant_count(void) { return cadmm::PV_COUNT; }
 
 const char* project_variant_name(int v) {
     static const char* names[cadmm::PV_COUNT] = {"os32", "os64", "ts16", "ts32", "ts64", "ts96",
-                                                 "ow8", "ow16", "ow32", "ow64"};
+                                                 "ow8", "ow16", "ow32", "ow64", "ws32"};
     return (v >= 0 && v < cadmm::PV_COUNT) ? names[v] : nullptr;
 }
 
@@ -1258,7 +1271,7 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
 
 const char* sdp_phase_name(sdp_handle h, int i) {
     if (!h) return nullptr;
-    return cadmm::phase_name(h->opts.form, h->ninst > 1, h->P.ncs > 0, i);
+    return cadmm::phase_name(h->opts.form, h->ninst > 1, h->P.ncs > 0, h->P.kkt_tri != 0, i);
 }
 
 void sdp_free(sdp_handle h) { delete h; }

@@ -473,6 +473,70 @@ __global__ void __launch_bounds__(kTriThreads) k_solve_y(IterPtrs P, double rinv
     }
 }
 
+// ---------------------------------------------------------------- y = L^-T (L^-1 (t - rhs2))
+// The same solve for an ill-conditioned M: with the explicit M^-1, x = D^-1 (r - A^T y) misses
+// A x = rhs2 by about kappa(M) eps; with the two triangular factors (the inverse of the cached
+// Cholesky factor, formed by substitution at setup) by about eps. z1 = L^-1 (t - rhs2): one warp
+// per row of L^-1, t - rhs2 staged in shared memory as in k_solve_y.
+__global__ void __launch_bounds__(kTriThreads) k_tri_lower(IterPtrs P, double rinv, int form) {
+    extern __shared__ double u[];
+    pdl_wait();
+    const Sched sc = P.tri_sched[blockIdx.x];
+    if (P.ctrl->done) return;         // the schedule entry above is read alongside the flag
+    if (stopped(P, sc.q)) return;
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double t = 0.0;
+        for (int c = P.row_chunk[r0 + i]; c < P.row_chunk[r0 + i + 1]; ++c) t += P.tpart[c];
+        const double bi = P.b[r0 + i];
+        const double rhs2 = form == SDP_PRIMAL ? bi : (form == SDP_DUAL ? -__dmul_rn(rinv, bi) : 0.0);
+        u[i] = t - rhs2;
+    }
+    __syncthreads();
+    const double* Lb = P.Linv + P.mblk_off[sc.q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
+        const int row = grow - r0;
+        const double* Lr = Lb + (size_t)row * m;
+        double a0 = 0.0, a1 = 0.0;
+        int j = lane;
+        for (; j + 32 <= row; j += 64) {
+            a0 = fma(Lr[j], u[j], a0);
+            a1 = fma(Lr[j + 32], u[j + 32], a1);
+        }
+        if (j <= row) a0 = fma(Lr[j], u[j], a0);
+        const double acc = warp_sum(a0 + a1);
+        if (lane == 0) P.z1[grow] = acc;
+    }
+}
+
+// y = L^-T z1: row i of L^-T is column i of L^-1, read as row i of (L^-1)^T (entries i .. m-1).
+__global__ void __launch_bounds__(kTriThreads) k_tri_upper(IterPtrs P) {
+    extern __shared__ double zs[];
+    pdl_wait();
+    const Sched sc = P.tri_sched[blockIdx.x];
+    if (P.ctrl->done) return;
+    if (stopped(P, sc.q)) return;
+    const int r0 = P.inst_row[sc.q], m = P.inst_row[sc.q + 1] - r0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = P.z1[r0 + i];
+    __syncthreads();
+    const double* Lb = P.LinvT + P.mblk_off[sc.q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int grow = sc.lo + warp; grow < sc.hi; grow += nw) {
+        const int row = grow - r0;
+        const double* Lr = Lb + (size_t)row * m;
+        double a0 = 0.0, a1 = 0.0;
+        int i = row + lane;
+        for (; i + 32 < m; i += 64) {
+            a0 = fma(Lr[i], zs[i], a0);
+            a1 = fma(Lr[i + 32], zs[i + 32], a1);
+        }
+        if (i < m) a0 = fma(Lr[i], zs[i], a0);
+        const double acc = warp_sum(a0 + a1);
+        if (lane == 0) P.y[grow] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- x = (r - A^T y) / D
 // A^T in sliced ELL form (columns ordered by length within windows of 256, so slices pad
 // little): one CTA per chunk of slices of one problem, its warps taking the slices in turn, one
@@ -879,7 +943,14 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
         return e;
     const size_t mbytes = (size_t)P.mmax * sizeof(double);   // the largest problem's y, staged
     mk.mark();
-    if ((e = launch_pdl(k_solve_y, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) return e;
+    if (P.kkt_tri) {
+        if ((e = launch_pdl(k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess)
+            return e;
+        mk.mark();
+        if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
+    } else if ((e = launch_pdl(k_solve_y, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) {
+        return e;
+    }
     mk.mark();
     if (P.col_split)
         e = launch_pdl(k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
@@ -896,11 +967,12 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
 }  // namespace
 
 int iteration_kernel_count(const IterPtrs& P, const ProjPlan& plan, int form) {
-    return (form == SDP_PRIMAL ? 4 : 5) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
+    return (form == SDP_PRIMAL ? 4 : 5) + plan.runs + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0) +
+           (P.kkt_tri ? 1 : 0);
 }
 
 int phase_count(const IterPtrs& P, int form) {
-    return (form == SDP_PRIMAL ? 5 : 6) + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0);
+    return (form == SDP_PRIMAL ? 5 : 6) + (P.ncs > 0 ? 1 : 0) + (P.ninst > 1 ? 1 : 0) + (P.kkt_tri ? 1 : 0);
 }
 
 cudaError_t iteration_prepare() {
@@ -908,6 +980,8 @@ cudaError_t iteration_prepare() {
     const int bytes = SDP_MAX_CONSTRAINTS * (int)sizeof(double);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tri_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_spmv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -948,15 +1022,23 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
     return cudaGetLastError();
 }
 
-const char* phase_name(int form, bool batch, bool cones, int i) {
+const char* phase_name(int form, bool batch, bool cones, bool tri, int i) {
     static const char* primal[] = {"spmv_rows", "solve_y", "spmv_cols", "project_primal", "project_cones",
                                    "scatter_primal+finalize", "finalize_batch"};
     static const char* dual[] = {"project_dual", "project_cones", "scatter_dual", "spmv_rows", "solve_y",
                                  "spmv_cols", "update_dual+finalize", "finalize_batch"};
     const char** list = form == SDP_PRIMAL ? primal : dual;
     const int cone_at = form == SDP_PRIMAL ? 4 : 1;
-    const int n = (form == SDP_PRIMAL ? 5 : 6) + (cones ? 1 : 0) + (batch ? 1 : 0);
+    const int solve_at = form == SDP_PRIMAL ? 1 : 4;
+    const int n = (form == SDP_PRIMAL ? 5 : 6) + (cones ? 1 : 0) + (batch ? 1 : 0) + (tri ? 1 : 0);
     if (i < 0 || i >= n) return nullptr;
+    // the triangular path has two phases in the slot of solve_y
+    const int solve_pos = solve_at - (!cones && cone_at < solve_at ? 1 : 0);
+    if (tri) {
+        if (i == solve_pos) return "tri_lower";
+        if (i == solve_pos + 1) return "tri_upper";
+        if (i > solve_pos + 1) --i;
+    }
     if (!cones && i >= cone_at) ++i;                    // no cone phase: skip its slot
     if (batch && i == (form == SDP_PRIMAL ? 5 : 6)) return form == SDP_PRIMAL ? "scatter_primal" : "update_dual";
     return list[i];

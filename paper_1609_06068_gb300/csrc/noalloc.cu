@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "sdp_internal.h"
 
@@ -20,10 +21,18 @@ constexpr size_t kSchedBytes = (size_t)SDP_NOALLOC_MAX_BLOCKS * (sizeof(long lon
 static __device__ __align__(256) unsigned char g_noalloc_sched[kSchedBytes];
 
 // Host-side view: the symbol above is only a host stand-in, so its device address is looked up
-// once per device (with that device current) and cached here.
+// with the device current and cached here. Every call looks it up again (a table lookup in the
+// runtime, no device work) and repeats the set-up when it has changed, which happens when the
+// device's context was destroyed (cudaDeviceReset) and a new one created.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_sched_dev[kMaxDevices] = {};
+
+// Host staging copy of the caller's schedule: the caller's arrays may be pinned, and a copy from
+// pinned memory runs asynchronously, so they are first copied here (pageable memory: the copy
+// below returns once the runtime has staged it, and this buffer may be reused at once). Host
+// memory only, one buffer per calling thread.
+thread_local std::vector<unsigned char> t_stage;
 
 // Errors go to the same per-thread message that sdp_last_error() reports.
 int fail(int code, const std::string& msg) { return cadmm::record_error(code, msg); }
@@ -54,33 +63,37 @@ extern "C" int project_psd_batched_noalloc(const double* in, double* out, const 
     if (dev < 0 || dev >= kMaxDevices) return fail(SDP_ERR_UNSUPPORTED, "device index beyond 63");
     void* sched = nullptr;
     {
-        // First call on this device: find the array's device address and raise the kernels'
-        // shared-memory limit. This must happen outside any stream capture.
+        // The array's device address in the current context. The first call on a device (and the
+        // first after its context was reset) also raises the kernels' shared-memory limit; that
+        // call must happen outside any stream capture.
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_sched);
+        if (e != cudaSuccess)
+            return fail(SDP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         std::lock_guard<std::mutex> lock(g_mu);
-        if (g_sched_dev[dev] == nullptr) {
-            void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_sched);
-            if (e != cudaSuccess)
-                return fail(SDP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        if (g_sched_dev[dev] != ptr) {
             e = cadmm::project_prepare();
             if (e != cudaSuccess)
                 return fail(SDP_ERR_CUDA, std::string("project_prepare: ") + cudaGetErrorString(e));
             g_sched_dev[dev] = ptr;
         }
-        sched = g_sched_dev[dev];
+        sched = ptr;
     }
 
-    // The caller's host arrays are copied straight into the shared schedule (pageable copies
-    // return once staged, so the caller may reuse them). Every entry the kernel reads is
-    // overwritten here, so nothing in the array has to start at zero; a call that overlaps another
-    // one on the GPU would overwrite its schedule.
+    // The schedule goes into the shared array as [offsets (count) | sizes (count)], through the
+    // host staging buffer, in one copy. Every entry the kernel reads is overwritten here, so
+    // nothing in the array has to start at zero; a call that overlaps another one on the GPU
+    // would overwrite its schedule.
+    const size_t off_bytes = (size_t)count * sizeof(long long);
+    const size_t bytes = off_bytes + (size_t)count * sizeof(int);
+    if (t_stage.size() < bytes) t_stage.resize(bytes);
+    std::memcpy(t_stage.data(), offsets, off_bytes);
+    std::memcpy(t_stage.data() + off_bytes, sizes, (size_t)count * sizeof(int));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     unsigned char* base = static_cast<unsigned char*>(sched);
     long long* d_off = reinterpret_cast<long long*>(base);
-    int* d_size = reinterpret_cast<int*>(base + (size_t)SDP_NOALLOC_MAX_BLOCKS * sizeof(long long));
-    e = cudaMemcpyAsync(d_off, offsets, (size_t)count * sizeof(long long), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_size, sizes, (size_t)count * sizeof(int), cudaMemcpyHostToDevice, st);
+    int* d_size = reinterpret_cast<int*>(base + off_bytes);
+    e = cudaMemcpyAsync(base, t_stage.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail(SDP_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
 
     cadmm::ProjArgs a{};

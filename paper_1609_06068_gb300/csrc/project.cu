@@ -852,6 +852,271 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 }
 
 // ---------------------------------------------------------------------------------------------
+// FP32, padded order N <= 32, one CTA of four warps per clique, for launches with few cliques
+// (fewer than the GPU holds warps), where a projection's time is the length of its dependent
+// chain rather than its operation count. The whole CTA loads W, forms G = B V_prev and rebuilds
+// the projection; the Jacobi sweeps run in warp 0 alone, lane c holding column c of G (rows
+// 0..31) in registers. A round is then 32 shuffles, a Gram entry, the 2x2 rotation and the column
+// update, with no barrier and no shared-memory exchange (k_project_os spends both on every round).
+//
+// The method is k_project_ow's (one-sided Jacobi on G = B V, B = W + sigma I, sigma = 2 ||W||_F,
+// V never formed: v_j = g_j / mu_j, lambda_j = mu_j - sigma with mu_j = ||g_j||), with three
+// changes on the round's critical path:
+//   - the partner of round rd is updated incrementally (no division, no table lookup);
+//   - the rotation takes r = sqrt(d^2 + 4 gamma^2) once, t = sign(d) 2 gamma / (|d| + r) with
+//     d = alpha_j - alpha_i, which is the same t as the textbook sign(zeta) / (|zeta| + sqrt(1 +
+//     zeta^2)), zeta = d / (2 gamma), with one reciprocal fewer; c = 1/sqrt(1 + t^2) from the
+//     hardware estimate and one Newton-Raphson step (error about one ulp, as for a correctly
+//     rounded one);
+//   - a pair whose columns are already orthogonal to kWSSkip (relative) is not rotated, and a
+//     round in which no pair rotates skips the column update altogether; below kWSSkip the Gram
+//     entry is at the level of FP32 rounding of a 32-term dot product, where a rotation cannot
+//     improve the columns;
+//   - each column carries a scale factor that takes the rotations' cosines, so a row of the
+//     update is one FMA (fast Givens style); the factors are folded back at every sweep start.
+// The sweeps stop after one in which every pair started within kOneSidedStop of orthogonal, as in
+// the other one-sided kernels.
+constexpr int kWSLD = 36;                 // row stride (floats): 16-byte rows for float4 access
+constexpr float kWSSkip = 1.0e-6f;
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
+    constexpr int LD = kWSLD;
+    __shared__ __align__(16) float Ws[32 * LD];   // W (scaled), later Q = V diag(lambda+)^(1/2)
+    __shared__ __align__(16) float Vs[32 * LD];   // previous eigenvectors (warm start)
+    __shared__ __align__(16) float Gs[32 * LD];   // G = B V_prev
+    __shared__ int s_exp[4];
+    __shared__ float s_sq[4];
+    __shared__ double red_d[33 * 3];
+
+    pdl_wait();
+    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
+    if (a.ctrl != nullptr && a.ctrl->done) return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int s = a.size[blk];
+    const long long off = a.off[blk];
+    if (block_stopped<MODE>(a, blk, s, off)) return;
+    const int N = s + (s & 1);
+    const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
+    float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+
+    // ---- W: warp w reads columns w, w + 4, ... of the packed lower triangle, lane j row cb + j
+    // (each column a contiguous run), all loads in flight. The block's scale comes from the
+    // largest exponent field, taken with integer operations.
+    double wv[8];
+    int emax = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int cb = w + 4 * k, ra = cb + lane;
+        wv[k] = (cb < s && ra < s) ? load_w<MODE>(a, off, packed_pos(ra, cb, s), rinv) : 0.0;
+    }
+    float vp[8];           // previous eigenvectors: warp w rows w, w + 4, ..., lane j column j
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int r = w + 4 * k;
+        vp[k] = !warm ? 0.f : (r < N && lane < N) ? vglob[r * N + lane] : (r == lane ? 1.f : 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int ex = (__double2hiint(wv[k]) >> 20) & 0x7ff;
+        emax = ex > emax ? ex : emax;
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) s_exp[w] = emax;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int r = w + 4 * k;
+        if (warm) Vs[r * LD + lane] = vp[k];
+        // zero the padding of W: rows and columns s .. 31
+        const int cb = w + 4 * k;
+        if (cb >= s || lane >= s) { Ws[lane * LD + cb] = 0.f; Ws[cb * LD + lane] = 0.f; }
+    }
+    __syncthreads();
+    emax = max(max(s_exp[0], s_exp[1]), max(s_exp[2], s_exp[3]));
+    // ilogb of max |W_ij| from the biased exponent, clamped to [-1000, 1000] as in block_exponent
+    // (a block whose entries are all zero or subnormal is scaled by 2^1000; a block holding an
+    // infinity or a NaN goes through unscaled and shows as such in the residuals)
+    const int e2 = emax == 0 ? -1000 : emax == 0x7ff ? 0 : min(max(emax - 1023, -1000), 1000);
+    const double down = pow2_exact(-e2), up = pow2_exact(e2);
+    float sq = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int cb = w + 4 * k, ra = cb + lane;
+        if (cb < s && ra < s) {
+            const float wt = (float)(wv[k] * down);
+            Ws[ra * LD + cb] = wt;
+            Ws[cb * LD + ra] = wt;
+            sq = fmaf(ra == cb ? wt : 2.f * wt, wt, sq);
+        }
+    }
+    sq = warp_sum_t(sq);
+    if (lane == 0) s_sq[w] = sq;
+    __syncthreads();
+    const float sigma = 2.f * sqrtf((s_sq[0] + s_sq[1]) + (s_sq[2] + s_sq[3]));
+
+    // ---- G = B V_prev (warm) by all four warps, warp w rows 8w .. 8w + 7, lane j column j
+    if (warm) {
+        const int r0 = 8 * w;
+        float g[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = sigma * Vs[(r0 + k) * LD + lane];
+#pragma unroll 2
+        for (int m = 0; m < 32; m += 4) {
+            const float v0 = Vs[m * LD + lane], v1 = Vs[(m + 1) * LD + lane];
+            const float v2 = Vs[(m + 2) * LD + lane], v3 = Vs[(m + 3) * LD + lane];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float4 wr = *reinterpret_cast<const float4*>(Ws + (r0 + k) * LD + m);
+                g[k] = fmaf(wr.x, v0, g[k]);
+                g[k] = fmaf(wr.y, v1, g[k]);
+                g[k] = fmaf(wr.z, v2, g[k]);
+                g[k] = fmaf(wr.w, v3, g[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Gs[(r0 + k) * LD + lane] = lane < N ? g[k] : 0.f;
+        __syncthreads();
+    }
+
+    // ---- sweeps: warp 0, lane c = column c. The column is kept as kap * gh: a rotation scales
+    // both columns of its pair by c, which goes into kap, so the rows take one FMA each
+    // (gh' = gh -+ t (kap_partner / kap) gh_partner); every sweep starts from kap = 1.
+    int sweeps = 0;
+    if (w == 0) {
+        __syncwarp();
+        const int c = lane;
+        float g[32];
+        if (warm) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) g[r] = Gs[r * LD + c];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) g[r] = c < N ? Ws[r * LD + c] + ((r == c) ? sigma : 0.f) : 0.f;
+        }
+        const int n = N - 1;                      // rounds per sweep (odd)
+        float kap = 1.f, kinv = 1.f;
+        for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
+            float alpha = 0.f;                    // ||g_c||^2 (true scale)
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                g[r] *= kap;
+                alpha = fmaf(g[r], g[r], alpha);
+            }
+            kap = 1.f;
+            kinv = 1.f;
+            bool big = false;                     // some pair started this sweep beyond the stop
+            // round-robin partner: player n meets player rd; player i < n meets (2 rd - i) mod n,
+            // or player n when that is i itself. j tracks (2 rd - c) mod n.
+            int j = (c == 0 || c >= n) ? 0 : n - c;
+            for (int rd = 0; rd < n; ++rd) {
+                const int p = c >= N ? c : (c == n ? rd : (j == c ? n : j));
+                j += 2;
+                if (j >= n) j -= n;
+                float gp[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) gp[r] = __shfl_sync(0xffffffffu, g[r], p);
+                const float beta = __shfl_sync(0xffffffffu, alpha, p);
+                const float kp = __shfl_sync(0xffffffffu, kap, p);
+                float ga[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < 32; ++r) ga[r & 3] = fmaf(g[r], gp[r], ga[r & 3]);
+                // both ends form the same product (kap * kp in the same order at both ends)
+                const bool first = c < p;
+                const float kk = first ? kap * kp : kp * kap;
+                const float gam = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * kk;
+                const float g2 = gam * gam, ab = alpha * beta;
+                const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
+                big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
+                if (!__any_sync(0xffffffffu, rot)) continue;
+                const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
+                const float gg = 2.f * gam;
+                const float x = fmaf(d, d, gg * gg);
+                const float rr = x * rsqrtf(x);
+                float t = __fdividef(gg, fabsf(d) + rr);
+                t = d < 0.f ? -t : t;
+                const float u = fmaf(t, t, 1.f);
+                float cc = rsqrtf(u);
+                cc = fmaf(0.5f * cc, fmaf(-u * cc, cc, 1.f), cc);    // Newton-Raphson step
+                // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j), with s = t c
+                const float f = rot ? (first ? -t : t) * (kp * kinv) : 0.f;
+#pragma unroll
+                for (int r = 0; r < 32; ++r) g[r] = fmaf(f, gp[r], g[r]);
+                if (rot) {
+                    kap *= cc;
+                    kinv *= u * cc;                                   // 1 / c = sqrt(1 + t^2)
+                    alpha = first ? alpha - t * gam : alpha + t * gam;
+                }
+            }
+            ++sweeps;
+            if (!__any_sync(0xffffffffu, big)) break;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) g[r] *= kap;
+        // lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into Ws
+        float mu2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) mu2 = fmaf(g[r], g[r], mu2);
+        const float mu = sqrtf(mu2);
+        const float inv = mu > 0.f ? 1.f / mu : 0.f;
+        const float lam = mu - sigma;
+        const float qs = (c < N && lam > 0.f) ? sqrtf(lam) * inv : 0.f;
+        if (vglob != nullptr && c < N) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (r < N) vglob[r * N + c] = mu > 0.f ? g[r] * inv : (r == c ? 1.f : 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) Ws[r * LD + c] = g[r] * qs;
+    }
+    __syncthreads();
+
+    // ---- rebuild the lower triangle of Q Q^T: warp w columns w, w + 4, ..., lane j row cb + j
+    pdl_trigger();
+    double pv[3] = {0.0, 0.0, 0.0};
+    double* xk_new = nullptr;
+    if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
+    for (int cb = w; cb < s; cb += 4) {
+        const int ra = cb + lane;
+        if (ra >= s) continue;
+        const float4* Qa = reinterpret_cast<const float4*>(Ws + ra * LD);
+        const float4* Qb = reinterpret_cast<const float4*>(Ws + cb * LD);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 qa = Qa[i], qb = Qb[i];
+            acc[0] = fmaf(qa.x, qb.x, acc[0]);
+            acc[1] = fmaf(qa.y, qb.y, acc[1]);
+            acc[2] = fmaf(qa.z, qb.z, acc[2]);
+            acc[3] = fmaf(qa.w, qb.w, acc[3]);
+        }
+        const double xv = ((double)((acc[0] + acc[1]) + (acc[2] + acc[3]))) * up;
+        const int pos = packed_pos(ra, cb, s);
+        if (MODE == PROJ_PRIMAL) {
+            const double u = a.x[a.gather_idx[off + pos]];
+            const double l = a.lam[off + pos];
+            const double d = xv - u;
+            xk_new[off + pos] = xv;
+            a.lam[off + pos] = l + a.rho * d;                  // Eq. LambdakUpdate
+            const double wgt = (ra == cb) ? 1.0 : 2.0;
+            pv[0] += wgt * d * d;
+            pv[1] += wgt * xv * xv;
+            pv[2] += wgt * u * u;
+        } else {
+            a.out[off + pos] = xv;
+        }
+    }
+    if (MODE == PROJ_PRIMAL) {
+        block_sum_t<double, 3>(pv, red_d);
+        if (tid == 0) {
+            a.part[blk * 4 + 0] = pv[0];
+            a.part[blk * 4 + 1] = pv[1];
+            a.part[blk * 4 + 2] = pv[2];
+        }
+    }
+    if (a.part != nullptr && w == 0 && lane == 0) a.part[blk * 4 + 3] = (double)sweeps;
+}
+
+// ---------------------------------------------------------------------------------------------
 // FP32, padded order N <= NR (NR = 8, 16, 32): one warp segment of NR lanes per clique (32 / NR
 // cliques per warp, 4 warps per CTA), lane c holding column c of G = B V in registers, so a round
 // of the one-sided Jacobi iteration needs no barrier and no shared memory: the partner column
@@ -1355,6 +1620,8 @@ cudaError_t launch_mode(const ProjArgs& a, int variant, int smax, cudaStream_t s
             return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
         case PV_OS2:
             return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
+        case PV_WS32:
+            return launch_pdl(k_project_ws<MODE>, dim3(a.count), dim3(128), 0, st, a, rinv);
         case PV_OW8:
             return launch_pdl(k_project_ow<MODE, 8>, dim3((a.count + OWLayout<8>::BPC - 1) / OWLayout<8>::BPC),
                               dim3(128), OWLayout<8>::kBytes, st, a, rinv);
@@ -1426,6 +1693,7 @@ bool project_variant_valid(int variant, int s, int prec) {
     const int N = s + (s & 1);
     switch (variant) {
         case PV_OS1: return prec == SDP_PROJ_FP32 && N <= 32;
+        case PV_WS32: return prec == SDP_PROJ_FP32 && N <= 32;
         case PV_OW8: return prec == SDP_PROJ_FP32 && N <= 8;
         case PV_OW16: return prec == SDP_PROJ_FP32 && N <= 16;
         case PV_OW32: return prec == SDP_PROJ_FP32 && N <= 32;
@@ -1442,7 +1710,8 @@ bool project_variant_valid(int variant, int s, int prec) {
 ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& size, int prec, const int* table,
                         int ow_min_blocks) {
     // A warp segment per block pays off when there are enough blocks to fill the GPU with warps;
-    // with fewer, a CTA per block finishes each block sooner.
+    // with fewer, a CTA per block finishes each block sooner (the CTA shares the load, the warm
+    // start and the rebuild; the sweeps stay in one warp up to order 32).
     long long small = 0;
     for (int k : order) small += (size[k] + (size[k] & 1)) <= 64;
     const bool use_ow = small >= ow_min_blocks;
@@ -1452,7 +1721,7 @@ ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& s
         const int s = size[order[i]];
         const int N = s + (s & 1);
         int v = project_default_variant(s, prec);
-        if (!use_ow && (v == PV_OW8 || v == PV_OW16 || v == PV_OW32)) v = PV_OS1;
+        if (!use_ow && (v == PV_OW8 || v == PV_OW16 || v == PV_OW32)) v = PV_WS32;
         if (!use_ow && v == PV_OW64) v = PV_OS2;
         if (table != nullptr && project_variant_valid(table[N], s, prec)) v = table[N];
         if (pl.runs > 0 && pl.variant[pl.runs - 1] == v) {

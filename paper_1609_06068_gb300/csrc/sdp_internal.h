@@ -55,6 +55,11 @@ struct HostProblem {
     std::vector<unsigned short> sell_row;
     std::vector<double> sell_val;
     std::vector<double> Minv;                   // (A D^-1 A^T)^-1: per instance an m_q x m_q row-major block
+    // L^-1 (lower, row-major, per instance at the same offsets as M^-1), kept for the affine
+    // step of ill-conditioned problems; LinvT = (L^-1)^T row-major, filled when kkt_tri is set.
+    std::vector<double> Linv, LinvT;
+    double kkt_cond = 1.0;                      // kappa_1(A D^-1 A^T) (largest over a batch)
+    bool kkt_tri = false;                       // affine step by the two triangular factors
     // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
     int ninst = 1;
     std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
@@ -136,7 +141,7 @@ struct Sched {
 // Projection launches: the cliques in processing order (largest first) split into runs that use
 // the same kernel variant. A run [start, start + count) of `order` goes to one launch.
 enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_OW8, PV_OW16, PV_OW32, PV_OW64,
-                   PV_COUNT };
+                   PV_WS32, PV_COUNT };
 constexpr int kMaxProjRuns = 64;
 struct ProjPlan {
     int runs;
@@ -176,6 +181,10 @@ struct IterPtrs {
     const int* sell_col; const int* sell_len; const long long* sell_off;    // A^T, sliced ELL
     const unsigned short* sell_row; const double* sell_val;                  // rows within the problem
     const double* Minv;                            // (A D^-1 A^T)^-1 blocks at mblk_off
+    // kkt_tri: y = L^-T (L^-1 (t - rhs2)) by two triangular products with the cached factor's
+    // inverse (blocks at mblk_off), z1 the intermediate; otherwise y = M^-1 (t - rhs2).
+    int kkt_tri;
+    const double* Linv; const double* LinvT; double* z1;
     // state
     double* x; double* y; double* r; double* rsw;
     double* xk[2]; double* lam; double* vk;
@@ -242,7 +251,10 @@ cudaError_t launch_vstore_identity(const IterPtrs& P, int prec, cudaStream_t st)
 cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, int prec, double rho,
                              cudaStream_t st, cudaEvent_t* ev = nullptr);
 int phase_count(const IterPtrs& P, int form);
-const char* phase_name(int form, bool batch, bool cones, int i);
+const char* phase_name(int form, bool batch, bool cones, bool tri, int i);
+// Condition number (1-norm) of A D^-1 A^T above which the affine step applies the Cholesky
+// factor as two triangular products instead of the explicit inverse.
+constexpr double kKktTriCond = 1.0e5;
 cudaError_t launch_primal_rebuild_r(const IterPtrs& P, double rho, cudaStream_t st);
 cudaError_t launch_gather(const IterPtrs& P, const double* x, double* blocks, cudaStream_t st);
 cudaError_t launch_scatter(const IterPtrs& P, const double* blocks, double* out, cudaStream_t st);

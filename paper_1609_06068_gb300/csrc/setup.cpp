@@ -147,6 +147,18 @@ void parallel_for(int n, F f) {
 
 }  // namespace
 
+// (L^-1)^T of every problem's block, row-major at the same offsets: the upper triangular product
+// then reads rows, as the lower one does.
+void fill_linv_t(HostProblem& hp) {
+    hp.LinvT.assign(hp.Linv.size(), 0.0);
+    parallel_for(hp.ninst, [&](int q) {
+        const long long off = hp.mblk_off[q];
+        const int mq = hp.inst_row[q + 1] - hp.inst_row[q];
+        for (int i = 0; i < mq; ++i)
+            for (int j = 0; j <= i; ++j) hp.LinvT[off + (size_t)j * mq + i] = hp.Linv[off + (size_t)i * mq + j];
+    });
+}
+
 int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
                        const double* A_val, const double* b, long long C_nnz, const int* C_row,
                        const int* C_col, const double* C_val, long long pat_nnz,
@@ -574,6 +586,25 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     });
     for (int i = 0; i < m; ++i)
         for (int j = i + 1; j < m; ++j) hp.Minv[(size_t)i * m + j] = hp.Minv[(size_t)j * m + i];
+    // kappa_1(M) = ||M||_1 ||M^-1||_1 (both symmetric: largest absolute row sums). With the
+    // explicit inverse, x = D^-1 (r - A^T y) misses A x = rhs2 by about kappa eps; with the two
+    // triangular factors by about eps, as with substitution. Above kKktTriCond the affine step
+    // takes the factors (one more launch per iteration).
+    {
+        double nm = 0.0, ni = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double a = 0.0, bsum = 0.0;
+            for (int j = 0; j < m; ++j) {
+                a += std::fabs(M[(size_t)i * m + j]);
+                bsum += std::fabs(hp.Minv[(size_t)i * m + j]);
+            }
+            nm = std::max(nm, a);
+            ni = std::max(ni, bsum);
+        }
+        hp.kkt_cond = m > 0 ? nm * ni : 1.0;
+        hp.kkt_tri = hp.kkt_cond > kKktTriCond;
+    }
+    hp.Linv.swap(Linv);
 
     // ---- A^T as sliced ELL (32 columns per slice, one lane per column on the device). Within
     // each window of 256 consecutive columns the columns are ordered by length (longest first,
@@ -633,6 +664,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     hp.inst_pos = {0, hp.SL};
     hp.inst_row = {0, m};
     hp.mblk_off = {0, (long long)mm};
+    if (hp.kkt_tri) fill_linv_t(hp);
     return SDP_OK;
 }
 
@@ -706,8 +738,13 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         hp.b.reserve(m); hp.a_rowptr.reserve(m + 1);
         hp.a_col.reserve(nnz); hp.a_val.reserve(nnz);
         hp.Minv.reserve(mm);
+        hp.Linv.reserve(mm);
     };
     reserve_all();
+    for (const HostProblem& h : parts) {
+        hp.kkt_cond = std::max(hp.kkt_cond, h.kkt_cond);
+        hp.kkt_tri = hp.kkt_tri || h.kkt_tri;
+    }
     hp.sc_ptr.push_back(0);
     hp.a_rowptr.push_back(0);
     // Concatenate: indices into E_L, positions, vertices and nonzeros are shifted by the totals of
@@ -749,6 +786,7 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
         for (int c : h.a_col) hp.a_col.push_back(c + e0);
         hp.a_val.insert(hp.a_val.end(), h.a_val.begin(), h.a_val.end());
         hp.Minv.insert(hp.Minv.end(), h.Minv.begin(), h.Minv.end());
+        hp.Linv.insert(hp.Linv.end(), h.Linv.begin(), h.Linv.end());
         h = HostProblem();   // release the part as soon as it is copied
     }
     hp.blk_off.push_back((int)SL);
@@ -762,6 +800,8 @@ int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& out,
     std::iota(hp.order.begin(), hp.order.end(), 0);
     std::stable_sort(hp.order.begin(), hp.order.end(),
                      [&](int x, int y) { return hp.blk_size[x] > hp.blk_size[y]; });
+    // one affine-step method for the whole batch: the triangular factors if any problem needs them
+    if (hp.kkt_tri) fill_linv_t(hp);
     return SDP_OK;
 }
 

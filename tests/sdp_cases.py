@@ -298,3 +298,31 @@ def socp_as_arrow_sdp(Ac: np.ndarray, b, c, n_lin: int, soc_dims) -> dict:
     bb += [0.0] * len(extra)
     d = problem_from_dense(cost, As, bb, cliques)
     return d
+
+
+def near_dependent_block_arrow(l=4, d=3, h=2, m=8, delta=1e-4, seed=17) -> dict:
+    """A feasible block-arrow SDP whose last constraint is the first one plus delta times a
+    random matrix on the pattern: two nearly dependent rows of A, so that A D⁻¹ Aᵀ has condition
+    number of order 1/delta²."""
+    rng = np.random.default_rng(seed)
+    P = block_arrow_dense_pattern(l, d, h)
+    n = P.shape[0]
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    X0 = G @ G.T
+    As = []
+    for _ in range(m - 1):
+        A = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.5)
+        A = np.tril(A) + np.tril(A, -1).T
+        As.append(A * P)
+    R = rng.standard_normal((n, n))
+    R = (np.tril(R) + np.tril(R, -1).T) * P
+    As.append(As[0] + delta * R)
+    b = [float(np.sum(A * X0)) for A in As]
+    Z = rng.standard_normal((n, n))
+    Z = np.tril(Z, -1)
+    Z = (Z + Z.T) * P
+    Z += np.diag(np.abs(Z).sum(axis=1) + 1.0)
+    y0 = rng.standard_normal(m)
+    C = Z + sum(y * A for y, A in zip(y0, As))
+    C[P & (C == 0)] = 1e-3
+    return problem_from_dense(C, As, b, block_arrow_cliques(l, d, h))

@@ -51,8 +51,13 @@ def batch(rng):
     return blocks
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_project_matches_oracle(prec, tol):
+def entry_err(P, ref, W):
+    """Largest entry error relative to the largest entry of W."""
+    return float(np.max(np.abs(P - ref)) / max(np.max(np.abs(W)), 1e-300))
+
+
+@pytest.mark.parametrize("prec,tol,ent_tol", [("fp64", 1e-12, 1e-12), ("fp32", 2e-5, 1e-4)])
+def test_project_matches_oracle(prec, tol, ent_tol):
     torch, cadmm = require_gpu()
     rng = np.random.default_rng(42)
     blocks = batch(rng)
@@ -72,6 +77,7 @@ def test_project_matches_oracle(prec, tol):
         nW = max(np.linalg.norm(W), 1e-300)
         err = np.linalg.norm(P - ref) / nW
         assert err <= tol, (k, s, prec, err)
+        assert entry_err(P, ref, W) <= ent_tol, (k, s, prec, entry_err(P, ref, W))
         if np.linalg.norm(W) > 0:
             assert np.linalg.eigvalsh(P)[0] >= -tol * nW
 
@@ -92,13 +98,15 @@ def test_project_in_place_and_empty():
     cadmm.project_psd_batched(v, v, np.zeros(0, np.int32), np.zeros(0, np.int64))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
-def test_every_variant_matches_oracle(prec, tol, capsys):
+@pytest.mark.parametrize("prec,tol,ent_tol", [("fp64", 1e-12, 1e-12), ("fp32", 1e-4, 4e-4)])
+def test_every_variant_matches_oracle(prec, tol, ent_tol, capsys):
     """Each eigensolver kernel variant, forced on every order it accepts (random blocks, several
     per order so warp segments and CTAs hold more than one, plus the special blocks that fit),
-    against the oracle's projection. The FP32 bound is the one-sided variants' stopping rule
-    (columns orthogonal to 1e-4 relative): from a cold start on a block with four 5-fold
-    eigenvalue clusters they come within about 7.5e-5 of ||W||."""
+    against the oracle's projection, in the Frobenius norm relative to ||W||_F and entry by entry
+    relative to max |W_ij|. The FP32 bound is the one-sided variants' stopping rule (columns
+    orthogonal to 1e-4 relative): from a cold start on a block with four 5-fold eigenvalue
+    clusters they come within about 7.5e-5 of ||W||_F. On that block ||W||_F is about four times
+    max |W_ij|, so its entry bound is four times the Frobenius one."""
     torch, cadmm = require_gpu()
     names = cadmm.project_variants()
     rng = np.random.default_rng(11)
@@ -109,7 +117,7 @@ def test_every_variant_matches_oracle(prec, tol, capsys):
             base.append((W + W.T) / 2)
     base += special_blocks(rng)
     tested = 0
-    worst = {}
+    worst, worst_ent = {}, {}
     for v, name in enumerate(names):
         blocks = [W for W in base if cadmm.project_variant_fits(v, W.shape[0], prec)]
         if not blocks:
@@ -124,11 +132,38 @@ def test_every_variant_matches_oracle(prec, tol, capsys):
         got = out.cpu().numpy()
         for k, W in enumerate(blocks):
             s = W.shape[0]
-            err = np.linalg.norm(unpacked(got[offs[k]:offs[k] + lens[k]], s) - orc.proj_psd(W)) / max(
-                np.linalg.norm(W), 1e-300)
-            assert err <= tol, (name, k, s, err)
+            P, ref = unpacked(got[offs[k]:offs[k] + lens[k]], s), orc.proj_psd(W)
+            err = np.linalg.norm(P - ref) / max(np.linalg.norm(W), 1e-300)
+            ent = entry_err(P, ref, W)
+            assert err <= tol and ent <= ent_tol, (name, k, s, err, ent)
             worst[name] = max(worst.get(name, 0.0), float(err))
+            worst_ent[name] = max(worst_ent.get(name, 0.0), ent)
         tested += 1
     assert tested >= (4 if prec == "fp64" else 8)
     with capsys.disabled():
         print(f"\n{prec} projection variants, worst error / ||W||:", {k: f"{v:.1e}" for k, v in worst.items()})
+        print(f"{prec} projection variants, worst entry error / max|W|:",
+              {k: f"{v:.1e}" for k, v in worst_ent.items()})
+
+
+def test_project_refuses_stream_capture():
+    """project_psd_batched copies its schedule from a host buffer that lives for the call only, so
+    on a capturing stream it returns SDP_ERR_UNSUPPORTED instead of recording that copy."""
+    torch, cadmm = require_gpu()
+    rng = np.random.default_rng(9)
+    W = rng.standard_normal((12, 12)); W = W + W.T
+    v = torch.tensor(packed(W), device="cuda")
+    sizes, offs = np.array([12], np.int32), np.array([0], np.int64)
+    cadmm.project_psd_batched(v, v, sizes, offs)          # prepares the kernels outside the capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        g.capture_begin()
+        try:
+            with pytest.raises(cadmm.SDPError) as e:
+                cadmm.project_psd_batched(v, v, sizes, offs, stream=stream)
+        finally:
+            g.capture_end()
+    assert e.value.code == cadmm.SDP_ERR_UNSUPPORTED
+    assert "captured" in str(e.value)
