@@ -43,6 +43,9 @@ NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
 FP32_MEASURED_TFLOPS = 73.3      # FMA-chain probe on this GB300 pool (8 independent chains/thread)
+# FP64 FMA, multiply, add and FP64-to-FP32 conversion each issue at 1.68 per clock per SM on this
+# pool's GB300s (a throughput probe, 8 independent chains per thread, 152 x 256 threads)
+FP64_OPS_PER_CLK_SM = 1.68
 
 
 def parse_args():
@@ -62,8 +65,12 @@ def parse_args():
                     help="time the conic workload (the n = 1020 SDP plus nonnegative and second-order cones)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="for profilers: set up, run this many iterations from a reset, exit (no JSON)")
+    ap.add_argument("--l", type=int, default=0,
+                    help="single-instance workloads: use this many diagonal blocks instead of the workload's "
+                         "(smaller captures for profilers; the line then names the reduced workload)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-iters", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-procs", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -74,14 +81,20 @@ def _arrays(inst):
                 A_val=inst.A_val, b=inst.b, C_row=inst.C_row, C_col=inst.C_col, C_val=inst.C_val)
 
 
-def workload(config: int):
-    """(cfg, instances, arrays): one instance and its arrays, or lists of them for a batch."""
+def workload(config: int, l_override: int = 0):
+    """(cfg, instances, arrays): one instance and its arrays, or lists of them for a batch. A block
+    count override gives a smaller instance of a single-instance workload (renamed accordingly)."""
     from sdp_inputs import CONFIGS, config_instance
     cfg = dict(CONFIGS[config])
     if cfg["count"] > 1:
         insts = [config_instance(config, i) for i in range(cfg["count"])]
         return cfg, insts, [_arrays(x) for x in insts]
-    inst = config_instance(config)
+    if l_override > 0:
+        cfg["l"] = l_override
+        cfg["name"] = cfg["name"].replace(f"_l{CONFIGS[config]['l']}_", f"_l{l_override}_")
+        inst = config_instance(config, l=l_override)
+    else:
+        inst = config_instance(config)
     return cfg, inst, _arrays(inst)
 
 
@@ -95,11 +108,22 @@ def oracle_worker(args):
     cfg = dict(CONFIGS[args.config])
     batch = cfg["count"] > 1
     step = orc.primal_iteration if cfg["form"] == "primal" else orc.dual_iteration
+    pool = None
+    if args.oracle_procs > 1:
+        # every host core for the clique projections (independent within an iteration): one
+        # contiguous share of the blocks per thread, its clique blocks of one order stacked into a
+        # single eigensolver call (LAPACK, one BLAS thread each, outside the interpreter lock)
+        from concurrent.futures import ThreadPoolExecutor
+        pool = ThreadPoolExecutor(args.oracle_procs)
+        orc.set_block_map(lambda f, items: _parallel_projections(pool, args.oracle_procs, orc, list(items)))
     limit = args.oracle_iters if args.oracle_iters > 0 else 10 ** 9
     iters, setup_s, run_s, problems, q = 0, 0.0, 0.0, 0, 0
     t_all = time.perf_counter()
     while iters < limit and (args.oracle_iters > 0 or run_s < args.cpu_seconds):
-        inst = config_instance(args.config, q % cfg["count"])
+        if args.l > 0 and not batch:
+            inst = config_instance(args.config, l=args.l)
+        else:
+            inst = config_instance(args.config, q % cfg["count"])
         t0 = time.perf_counter()
         sdp = orc.ChordalSDP(inst.n, inst.cliques, inst.A_ptr, inst.A_row, inst.A_col, inst.A_val,
                              inst.b, inst.C_row, inst.C_col, inst.C_val)
@@ -119,22 +143,75 @@ def oracle_worker(args):
             break
         if time.perf_counter() - t_all > 4 * max(args.cpu_seconds, 1.0) + 60:
             break
-    print(json.dumps(dict(iters=iters, seconds=run_s, setup_seconds=setup_s, problems=problems)))
+    if pool is not None:
+        pool.shutdown()
+    print(json.dumps(dict(iters=iters, seconds=run_s, setup_seconds=setup_s, problems=problems,
+                          procs=args.oracle_procs)))
 
 
-def run_oracle(args, iters=0, seconds=None):
+# The oracle cannot hold the largest single instance (2000 blocks, 2e8 nonzeros of A) in a bounded
+# CPU sample; its baseline runs the same workload with this many blocks and scales the time per
+# iteration by the block ratio (the projections and both passes over A grow with the block count).
+ORACLE_MAX_BLOCKS = 100
+
+
+def _project_share(orc, items):
+    """The oracle's block projections for one thread's share: clique blocks of one order go to
+    one stacked eigendecomposition, the rest one by one as the oracle does them."""
+    import numpy as np
+    out = [None] * len(items)
+    groups = {}
+    for i, (kind, s, w, dual) in enumerate(items):
+        if kind == "psd":
+            groups.setdefault(s, []).append(i)
+        else:
+            out[i] = orc._project_item(items[i])
+    for s, idx in groups.items():
+        W = np.stack([items[i][2].reshape(s, s, order="F") for i in idx])
+        W = 0.5 * (W + W.transpose(0, 2, 1))
+        lam, V = np.linalg.eigh(W)
+        X = (V * np.maximum(lam, 0.0)[:, None, :]) @ V.transpose(0, 2, 1)
+        X = 0.5 * (X + X.transpose(0, 2, 1))
+        for j, i in enumerate(idx):
+            out[i] = X[j].reshape(-1, order="F")
+    return out
+
+
+def _parallel_projections(pool, nthreads, orc, items):
+    k = max(1, -(-len(items) // nthreads))
+    shares = [items[i:i + k] for i in range(0, len(items), k)]
+    res = []
+    for r in pool.map(lambda sh: _project_share(orc, sh), shares):
+        res.extend(r)
+    return res
+
+
+def run_oracle(args, iters=0, seconds=None, l_override=0, procs=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", str(args.config),
            "--cpu-seconds", str(seconds if seconds is not None else args.cpu_seconds),
-           "--oracle-iters", str(iters)]
+           "--oracle-iters", str(iters), "--l", str(l_override), "--oracle-procs", str(procs)]
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
         raise RuntimeError("oracle worker failed: " + res.stderr[-2000:])
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_entry(args, cfg, unit=UNIT):
-    r = run_oracle(args)
+def cpu_baseline_entry(args, cfg, unit=UNIT, procs=1):
+    """The oracle on the host cores: one thread (one BLAS thread), or with procs > 1 its clique
+    projections spread over that many threads, each stacking its blocks of one order into one
+    eigensolver call (the rest of each iteration stays in one thread)."""
+    l_cfg = cfg.get("l") or 0
+    if cfg["count"] == 1 and l_cfg > ORACLE_MAX_BLOCKS:
+        r = run_oracle(args, l_override=ORACLE_MAX_BLOCKS, procs=procs)
+        scale = l_cfg / ORACLE_MAX_BLOCKS
+        sample = (f"{r['iters']} oracle {cfg['form']}-form iterations from a cold start on the same workload with "
+                  f"{ORACLE_MAX_BLOCKS} of its {l_cfg} diagonal blocks (setup {r['setup_seconds']:.2f} s excluded), "
+                  f"time per iteration scaled by {scale:g}; one BLAS thread")
+        if procs > 1:
+            sample += f"; clique projections over {procs} threads (stacked eigensolves)"
+        return dict(value=r["iters"] / (r["seconds"] * scale), unit=unit, cores=procs, kind="oracle", sample=sample)
+    r = run_oracle(args, procs=procs)
     if cfg["count"] > 1:
         sample = (f"{r['iters']} oracle {cfg['form']}-form iterations over the first {r['problems']} problems "
                   f"of {cfg['name']} (50 from a cold start each; setup {r['setup_seconds']:.2f} s excluded), "
@@ -142,7 +219,9 @@ def cpu_baseline_entry(args, cfg, unit=UNIT):
     else:
         sample = (f"{r['iters']} oracle {cfg['form']}-form iterations from a cold start on "
                   f"{cfg['name']} (setup {r['setup_seconds']:.2f} s excluded), one BLAS thread")
-    return dict(value=r["iters"] / r["seconds"], unit=unit, cores=1, kind="oracle", sample=sample)
+    if procs > 1:
+        sample = sample.replace("one BLAS thread", f"clique projections over {procs} threads (stacked eigensolves), one BLAS thread each")
+    return dict(value=r["iters"] / r["seconds"], unit=unit, cores=procs, kind="oracle", sample=sample)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -261,6 +340,31 @@ def roofline(phases, inst_sizes, cfg, prec, peaks, clocks):
                 traffic=traffic, peak_source="of measured (MEASURED_PEAKS.json hbm_gbs)", ms=ms)
 
 
+def affine_roofline(phases, inst_sizes, peaks, clocks):
+    """The two passes over A: algorithmic bytes against the HBM copy rate, and FP64 FMAs (one per
+    stored nonzero; the A^T pass counts its padded sliced-ELL slots) against the FP64 issue rate,
+    which bounds these kernels on GB300 before HBM does."""
+    mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = NUM_SMS * FP64_OPS_PER_CLK_SM * mhz * 1e6      # FP64 operations per second
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for name in ("spmv_rows", "spmv_cols"):
+        if name not in phases:
+            continue
+        ms = phases[name]
+        _, nbytes, _ = kernel_model(name, inst_sizes, None, "fp32")
+        fma = float(inst_sizes["nnz"]) if name == "spmv_rows" else float(inst_sizes.get("nnz_padded", inst_sizes["nnz"]))
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        gops = fma / (ms * 1e-3) / 1e9
+        out[name] = dict(ms=ms, bytes=nbytes, achieved_gbs=gbs, hbm_peak_gbs=hbm, hbm_frac=gbs / hbm,
+                         fp64_fma=fma, achieved_fp64_gops=gops, fp64_peak_gops=fp64_peak / 1e9,
+                         fp64_frac=gops * 1e9 / fp64_peak,
+                         peak_source=("HBM: of measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
+                                      else "HBM: of fallback 6.8 TB/s") +
+                                     f"; FP64: {FP64_OPS_PER_CLK_SM} ops/clock/SM measured x 152 SMs x max SM clock")
+    return out
+
+
 def source_sha():
     import hashlib
     h = hashlib.sha1()
@@ -339,7 +443,7 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     cadmm.load_library()
-    cfg, inst, arrs = workload(args.config)
+    cfg, inst, arrs = workload(args.config, args.l)
     batch = cfg["count"] > 1
     unit = "problem-iter/s" if batch else UNIT
     opts = cadmm.make_opts(rho=cfg["rho"], tol=cfg["tol"] if cfg["tol"] > 0 else 1e-4,
@@ -408,17 +512,34 @@ def run_ours(args):
     ms_per_step = total_ms_max / args.steps
     fp32_iters_per_solve = iters / args.steps
 
+    # A workload with an iteration cap below the usual 2000 (the large instance): also the time to
+    # the tolerance without the cap, FP32 here and FP64 below
+    capped = (not batch) and cfg["max_iter"] < 2000
+    to_tol = None
+    if capped:
+        solver.set_opts(max_iter=3000)
+        it_u, ms_u, _, last_u = timed_solves(1)
+        to_tol = dict(time_to_tol_ms=ms_u[0], iters=it_u, status=last_u["status"], eps_p=last_u["eps_p"],
+                      eps_d=last_u["eps_d"], obj_dual=last_u["obj_dual"], obj_primal=last_u["obj_primal"],
+                      iter_cap=3000)
+        solver.set_opts(max_iter=cfg["max_iter"])
+
     # FP64 eigensolves on the same instance (the plain baseline of the metric)
     fp64, phases64 = None, None
-    fp64_steps = min(args.fp64_steps, 1) if batch else args.fp64_steps
+    fp64_steps = min(args.fp64_steps, 1) if (batch or capped) else args.fp64_steps
     if fp64_steps > 0:
         solver.set_opts(prec="fp64")
+        if capped:
+            solver.set_opts(max_iter=3000)
         it64, ms64, _, last64 = timed_solves(fp64_steps)
         fp64 = dict(value=it64 / (sum(ms64) * 1e-3), unit=unit, time_to_tol_ms=sum(ms64) / fp64_steps,
                     iters_per_solve=it64 / fp64_steps, obj_dual=last64["obj_dual"],
                     obj_primal=last64["obj_primal"], status=last64["status"])
         if batch:
             fp64["batch_iters_per_solve"] = last64["iters"]
+        if capped:
+            fp64["iter_cap"] = 3000
+            solver.set_opts(max_iter=cfg["max_iter"])
         solver.reset(stream)
         solver.iterate(20, stream)          # warm-started eigensolves, every problem still active
         phases64 = cadmm.sdp_time_phases(solver.h, reps=5, stream=stream)
@@ -434,6 +555,7 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     roof = roofline(phases, inst_sizes, cfg, "fp32", peaks, clocks)
+    roof_affine = affine_roofline(phases, inst_sizes, peaks, clocks)
 
     # end to end through the C ABI from pinned host arrays: setup, solve, read the solution
     h2d = 0
@@ -474,9 +596,12 @@ def run_ours(args):
                    includes="sdp_setup (host maps, A D^-1 A^T, Cholesky, upload) + admm_solve + "
                             "sdp_get_solution")
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_entry(args, cfg, unit)
+        ncores = os.cpu_count() or 1
+        if ncores > 1:
+            cpu_all = cpu_baseline_entry(args, cfg, unit, procs=ncores)
 
     if rank == 0:
         conf = dict(workload=cfg["name"], n=sz["n"], m=sz["m"], p=sz["p"], clique=sz["max_clique"],
@@ -497,8 +622,12 @@ def run_ours(args):
             fp64_plain=fp64,
             speedup_fp32_vs_fp64_time_to_tol=(fp64["time_to_tol_ms"] / ms_per_step) if fp64 else None,
             phases_ms_fp32=phases, phases_ms_fp64=phases64,
-            roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks,
-            gpu=torch.cuda.get_device_name(local))
+            roofline=roof, roofline_affine=roof_affine, cpu_baseline=cpu, cpu_baseline_all_cores=cpu_all,
+            e2e=e2e, gpu_launches=launches,
+            clocks=clocks, gpu=torch.cuda.get_device_name(local))
+        if capped:
+            line["fp32_to_tol"] = to_tol
+            line["eps_at_cap"] = dict(eps_p=last["eps_p"], eps_d=last["eps_d"], iter_cap=cfg["max_iter"])
         if batch:
             line["batch_iters_per_solve"] = last["iters"]
         print(json.dumps(line))

@@ -92,6 +92,32 @@ def proj_cone(kind: str, w: np.ndarray, dual: bool) -> np.ndarray:
     raise OracleError(-1, f"unknown cone {kind!r}")
 
 
+def _project_item(item):
+    """One block of an iteration's projections (Eqs. XkUpdate / zkUpdate): (kind, order, w, dual)."""
+    kind, s, w, dual = item
+    if kind == "psd":
+        return _vec(proj_psd(_mat(w, s)))
+    return proj_cone(kind, w, dual)
+
+
+# The blocks' projections within an iteration are independent (Section III.B.2: "in parallel").
+# They go through this order-preserving map, the builtin one unless a caller installs another
+# (a process pool, for a timing baseline on every host core); the results do not depend on it.
+_block_map = map
+
+
+def set_block_map(fn) -> None:
+    """Install an order-preserving map(fn, items) for the block projections (None: the builtin)."""
+    global _block_map
+    _block_map = map if fn is None else fn
+
+
+def _project_blocks(sdp, ws, dual: bool = False) -> list:
+    items = [(sdp.kinds[k], len(sdp.cliques[k]) if sdp.kinds[k] == "psd" else 0, ws[k], dual)
+             for k in range(sdp.nblk)]
+    return list(_block_map(_project_item, items))
+
+
 def _mat(v: np.ndarray, s: int) -> np.ndarray:
     """vec⁻¹: column-major s×s matrix from its stacked columns."""
     return v.reshape(s, s, order="F")
@@ -356,7 +382,7 @@ def primal_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     x, y = sdp.kkt_solve(r, sdp.b)
     # Eq. (XkUpdate): x_k = vec P_k[vec⁻¹(H_k x − ρ⁻¹λ_k)].
     u = [sdp.H(k, x) for k in K]
-    xk_new = [sdp.project(k, u[k] - rinv * st["lam"][k]) for k in K]
+    xk_new = _project_blocks(sdp, [u[k] - rinv * st["lam"][k] for k in K])
     # Eq. (LambdakUpdate): λ_k += ρ (x_k − H_k x).
     lam_new = [st["lam"][k] + rho * (xk_new[k] - u[k]) for k in K]
     # Residuals (reading of Section III.B's stopping test, see module docstring).
@@ -378,7 +404,7 @@ def dual_iteration(sdp: ChordalSDP, st: dict, rho: float) -> dict:
     rinv = 1.0 / rho
     # Eq. (zkUpdate): z_k = vec P_k[vec⁻¹(v_k − ρ⁻¹λ_k)].
     K = range(sdp.nblk)
-    zk = [sdp.project(k, st["vk"][k] - rinv * st["lam"][k], dual=True) for k in K]
+    zk = _project_blocks(sdp, [st["vk"][k] - rinv * st["lam"][k] for k in K], dual=True)
     # Eq. (OptCondMinYDual): right-hand side c − Σ H_kᵀ(z_k + ρ⁻¹λ_k) and −ρ⁻¹b.
     r = sdp.c - sdp.HT_sum([zk[k] + rinv * st["lam"][k] for k in K])
     x, y = sdp.kkt_solve(r, -(rinv * sdp.b))

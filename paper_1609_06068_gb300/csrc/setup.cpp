@@ -455,58 +455,49 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         });
     }
     hp.nnz = (long long)hp.a_col.size();
-    // CSC by a parallel transpose: thread t counts the columns of its contiguous block of rows;
-    // exclusive sums over (column, thread) give every thread its write offsets, so each column
-    // lists its rows in increasing order as a serial transpose would.
+    // CSC by a parallel transpose over column ranges: every row of the CSR lists its columns in
+    // increasing order, so the entries of row i in columns [e0, e1) are one contiguous run found
+    // by binary search. Each worker owns a range of columns and walks the rows in order, so every
+    // column lists its rows in increasing order (as a serial transpose would) and each worker
+    // writes only its own part of the output.
     hp.c_colptr.assign(nEL + 1, 0);
     hp.c_row.resize(hp.nnz);
     hp.c_val.resize(hp.nnz);
     {
-        const int nt = std::max(1, std::min(worker_count(), std::max(1, m / 8)));
-        std::vector<std::vector<int>> cnt_t(nt, std::vector<int>(nEL, 0));
-        auto rows_of = [&](int t, int& lo, int& hi) {
-            lo = (int)((long long)m * t / nt);
-            hi = (int)((long long)m * (t + 1) / nt);
+        const int nt = std::max(1, std::min(4 * worker_count(), nEL / 256 + 1));
+        auto cols_of = [&](int t, int& e0, int& e1) {
+            e0 = (int)((long long)nEL * t / nt);
+            e1 = (int)((long long)nEL * (t + 1) / nt);
+        };
+        auto run_of = [&](int i, int e0, int e1, int& lo, int& hi) {
+            const int* c0 = hp.a_col.data() + hp.a_rowptr[i];
+            const int* c1 = hp.a_col.data() + hp.a_rowptr[i + 1];
+            lo = (int)(std::lower_bound(c0, c1, e0) - hp.a_col.data());
+            hi = (int)(std::lower_bound(c0 + (lo - hp.a_rowptr[i]), c1, e1) - hp.a_col.data());
         };
         parallel_for(nt, [&](int t) {
-            int lo, hi;
-            rows_of(t, lo, hi);
-            for (int tt = hp.a_rowptr[lo]; tt < hp.a_rowptr[hi]; ++tt) cnt_t[t][hp.a_col[tt]]++;
-        });
-        // exclusive offsets, column-major over (column, thread): column totals, their prefix sum,
-        // then each column's per-thread offsets (columns in parallel)
-        const int nchunk = std::max(1, std::min(worker_count(), nEL / 4096 + 1));
-        parallel_for(nchunk, [&](int k) {
-            const int e0 = (int)((long long)nEL * k / nchunk), e1 = (int)((long long)nEL * (k + 1) / nchunk);
-            for (int e = e0; e < e1; ++e) {
-                int tot = 0;
-                for (int t = 0; t < nt; ++t) tot += cnt_t[t][e];
-                hp.c_colptr[e + 1] = tot;
+            int e0, e1;
+            cols_of(t, e0, e1);
+            for (int i = 0; i < m; ++i) {
+                int lo, hi;
+                run_of(i, e0, e1, lo, hi);
+                for (int q = lo; q < hi; ++q) hp.c_colptr[hp.a_col[q] + 1]++;
             }
         });
-        hp.c_colptr[0] = 0;
         for (int e = 0; e < nEL; ++e) hp.c_colptr[e + 1] += hp.c_colptr[e];
-        parallel_for(nchunk, [&](int k) {
-            const int e0 = (int)((long long)nEL * k / nchunk), e1 = (int)((long long)nEL * (k + 1) / nchunk);
-            for (int e = e0; e < e1; ++e) {
-                int run = hp.c_colptr[e];
-                for (int t = 0; t < nt; ++t) {
-                    const int c0 = cnt_t[t][e];
-                    cnt_t[t][e] = run;
-                    run += c0;
+        parallel_for(nt, [&](int t) {
+            int e0, e1;
+            cols_of(t, e0, e1);
+            std::vector<int> fillp(hp.c_colptr.begin() + e0, hp.c_colptr.begin() + e1);
+            for (int i = 0; i < m; ++i) {
+                int lo, hi;
+                run_of(i, e0, e1, lo, hi);
+                for (int q = lo; q < hi; ++q) {
+                    const int at = fillp[hp.a_col[q] - e0]++;
+                    hp.c_row[at] = (unsigned short)i;
+                    hp.c_val[at] = hp.a_val[q];
                 }
             }
-        });
-        parallel_for(nt, [&](int t) {
-            int lo, hi;
-            rows_of(t, lo, hi);
-            std::vector<int>& fillp = cnt_t[t];
-            for (int i = lo; i < hi; ++i)
-                for (int tt = hp.a_rowptr[i]; tt < hp.a_rowptr[i + 1]; ++tt) {
-                    const int q = fillp[hp.a_col[tt]]++;
-                    hp.c_row[q] = (unsigned short)i;
-                    hp.c_val[q] = hp.a_val[tt];
-                }
         });
     }
 
@@ -576,11 +567,18 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         }
         for (int i = j; i < m; ++i) Linv[(size_t)i * m + j] = xcol[i];
     });
+    // (L^-1)^T row-major, so that the products below read rows
+    std::vector<double> LinvTr(mm, 0.0);
+    parallel_for(m, [&](int i) {
+        for (int k = i; k < m; ++k) LinvTr[(size_t)i * m + k] = Linv[(size_t)k * m + i];
+    });
     hp.Minv.assign(mm, 0.0);
     parallel_for(m, [&](int i) {
+        const double* Ti = LinvTr.data() + (size_t)i * m;
         for (int j = 0; j <= i; ++j) {
+            const double* Tj = LinvTr.data() + (size_t)j * m;
             double s = 0.0;
-            for (int k = i; k < m; ++k) s += Linv[(size_t)k * m + i] * Linv[(size_t)k * m + j];
+            for (int k = i; k < m; ++k) s += Ti[k] * Tj[k];
             hp.Minv[(size_t)i * m + j] = s;
         }
     });
@@ -642,15 +640,22 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         hp.sell_val.assign(off, 0.0);
         hp.sell_row.assign(off, 0);
         parallel_for(ns, [&](int sl) {
+            // in storage order (element k of the 32 slots, then k + 1, ...): the writes are
+            // contiguous and the reads are 32 forward streams
+            int beg[32], len[32];
             for (int t = 0; t < 32; ++t) {
                 const int c = slot_col[32LL * sl + t];
-                if (c < 0) continue;
-                for (int j = hp.c_colptr[c]; j < hp.c_colptr[c + 1]; ++j) {
-                    const long long q = hp.sell_off[sl] + 32LL * (j - hp.c_colptr[c]) + t;
-                    hp.sell_val[q] = hp.c_val[j];
-                    hp.sell_row[q] = hp.c_row[j];
-                }
+                beg[t] = c < 0 ? 0 : hp.c_colptr[c];
+                len[t] = c < 0 ? 0 : hp.c_colptr[c + 1] - hp.c_colptr[c];
             }
+            const long long base = hp.sell_off[sl];
+            for (int k = 0; k < hp.sell_len[sl]; ++k)
+                for (int t = 0; t < 32; ++t)
+                    if (k < len[t]) {
+                        const long long q = base + 32LL * k + t;
+                        hp.sell_val[q] = hp.c_val[beg[t] + k];
+                        hp.sell_row[q] = hp.c_row[beg[t] + k];
+                    }
         });
         std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
         std::vector<unsigned short>().swap(hp.c_row);
