@@ -907,7 +907,8 @@ cudaError_t launch_project_plan(const ProjArgs& a, const IterPtrs& P, const Proj
                                 cudaStream_t st) {
     for (int r = 0; r < plan.runs; ++r) {
         ProjArgs b = a;
-        b.order = P.order + plan.start[r];
+        b.order = plan.identity[r] ? nullptr : P.order + plan.start[r];
+        b.first = plan.start[r];
         b.count = plan.count[r];
         const cudaError_t e = launch_project_variant(b, mode, prec, plan.variant[r], plan.smax[r], st);
         if (e != cudaSuccess) return e;

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(SH::NT) k_project(ProjArgs a, double rinv) {
     __shared__ double red_d[33 * 4];
 
     pdl_wait();
-    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
+    const int blk = a.order ? a.order[blockIdx.x] : a.first + (int)blockIdx.x;   // read alongside the flag
     if (a.ctrl != nullptr && a.ctrl->done) return;
 
     const int s = a.size[blk];
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
     __shared__ float red_f[33 * 2];
 
     pdl_wait();
-    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
+    const int blk = a.order ? a.order[blockIdx.x] : a.first + (int)blockIdx.x;   // read alongside the flag
     if (a.ctrl != nullptr && a.ctrl->done) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int NT = 32 * NW;
@@ -869,15 +869,56 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 //     hardware estimate and one Newton-Raphson step (error about one ulp, as for a correctly
 //     rounded one);
 //   - a pair whose columns are already orthogonal to kWSSkip (relative) is not rotated, and a
-//     round in which no pair rotates skips the column update altogether; below kWSSkip the Gram
-//     entry is at the level of FP32 rounding of a 32-term dot product, where a rotation cannot
-//     improve the columns;
+//     round in which no pair rotates skips the column update altogether. A pair left at relative
+//     Gram entry e moves P(W) by about e ||W||_F, and up to N^2/2 pairs add up in quadrature, so
+//     kWSSkip = 1e-7 (about FP32 rounding of a 32-term dot product) keeps their sum near 4e-6
+//     ||W||_F at order 64;
 //   - each column carries a scale factor that takes the rotations' cosines, so a row of the
-//     update is one FMA (fast Givens style); the factors are folded back at every sweep start.
+//     update is one FMA (fast Givens style); the factors are folded back at every sweep start;
+//   - small rotations (|zeta| <= 2^-7, the usual case once a warm start is close) take the series
+//     of jacobi_rot, with 2 / (alpha_j - alpha_i) formed while the Gram entry is still being
+//     summed; a round whose rotations are all small has no square root or division on its chain.
 // The sweeps stop after one in which every pair started within kOneSidedStop of orthogonal, as in
 // the other one-sided kernels.
+// The rotation that makes two columns of G orthogonal, for the one-sided kernels: from
+// d = alpha_j - alpha_i, gamma and zeta = 2 gamma / d, the tangent t = zeta / (1 + sqrt(1 +
+// zeta^2)) (= sign(d) 2 gamma / (|d| + sqrt(d^2 + 4 gamma^2)), Golub & Van Loan's smaller root),
+// c = 1 / sqrt(1 + t^2) and 1/c. For |zeta| <= kSmallAngle (series = true) they come from their
+// series, t = (zeta/2)(1 - zeta^2/4), c = 1 - t^2/2, 1/c = 1 + t^2/2 (truncation below 1e-9
+// relative), with no division or root on the chain after gamma; otherwise from the closed forms
+// (c from the hardware reciprocal square root and one Newton-Raphson step, about one ulp).
+// need_full is warp-uniform: whether any lane of the warp takes the closed forms. Both ends of a
+// pair see the same gamma, d and zeta, so they choose the same way and compute the same rotation.
+constexpr float kSmallAngle = 0.0078125f;
+struct JRot {
+    float t, c, ic;
+};
+__device__ __forceinline__ JRot jacobi_rot(float gam, float d, float z, bool series, bool need_full) {
+    JRot q;
+    q.t = (0.5f * z) * fmaf(-0.25f * z, z, 1.f);
+    const float t2 = q.t * q.t;
+    q.c = fmaf(-0.5f, t2, 1.f);
+    q.ic = fmaf(0.5f, t2, 1.f);
+    if (need_full) {
+        const float gg = 2.f * gam;
+        const float x = fmaf(d, d, gg * gg);
+        const float rr = x * rsqrtf(x);
+        float t = __fdividef(gg, fabsf(d) + rr);
+        t = d < 0.f ? -t : t;
+        const float u = fmaf(t, t, 1.f);
+        float cc = rsqrtf(u);
+        cc = fmaf(0.5f * cc, fmaf(-u * cc, cc, 1.f), cc);    // Newton-Raphson step
+        if (!series) {
+            q.t = t;
+            q.c = cc;
+            q.ic = u * cc;                                   // sqrt(1 + t^2)
+        }
+    }
+    return q;
+}
+
 constexpr int kWSLD = 36;                 // row stride (floats): 16-byte rows for float4 access
-constexpr float kWSSkip = 1.0e-6f;
+constexpr float kWSSkip = 1.0e-7f;
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
@@ -890,15 +931,17 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
     __shared__ double red_d[33 * 3];
 
     pdl_wait();
-    const int blk = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;   // read alongside the flag
-    if (a.ctrl != nullptr && a.ctrl->done) return;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int blk = a.order ? a.order[blockIdx.x] : a.first + (int)blockIdx.x;
+    // the block's descriptor is read alongside the stop flag (one round trip to memory, not two)
     const int s = a.size[blk];
     const long long off = a.off[blk];
+    const long long voff = a.vstore != nullptr ? a.voff[blk] : 0;
+    if (a.ctrl != nullptr && a.ctrl->done) return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     if (block_stopped<MODE>(a, blk, s, off)) return;
     const int N = s + (s & 1);
     const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
-    float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
+    float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + voff : nullptr;
 
     // ---- W: warp w reads columns w, w + 4, ... of the packed lower triangle, lane j row cb + j
     // (each column a contiguous run), all loads in flight. The block's scale comes from the
@@ -1017,33 +1060,30 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
                 for (int r = 0; r < 32; ++r) gp[r] = __shfl_sync(0xffffffffu, g[r], p);
                 const float beta = __shfl_sync(0xffffffffu, alpha, p);
                 const float kp = __shfl_sync(0xffffffffu, kap, p);
+                const bool first = c < p;
+                const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
+                const float two_over_d = __fdividef(2.f, d);           // ready before gamma is
                 float ga[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int r = 0; r < 32; ++r) ga[r & 3] = fmaf(g[r], gp[r], ga[r & 3]);
                 // both ends form the same product (kap * kp in the same order at both ends)
-                const bool first = c < p;
                 const float kk = first ? kap * kp : kp * kap;
                 const float gam = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * kk;
                 const float g2 = gam * gam, ab = alpha * beta;
                 const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
                 big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
+                const float z = gam * two_over_d;                      // zeta
+                const bool series = fabsf(z) <= kSmallAngle;
                 if (!__any_sync(0xffffffffu, rot)) continue;
-                const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
-                const float gg = 2.f * gam;
-                const float x = fmaf(d, d, gg * gg);
-                const float rr = x * rsqrtf(x);
-                float t = __fdividef(gg, fabsf(d) + rr);
-                t = d < 0.f ? -t : t;
-                const float u = fmaf(t, t, 1.f);
-                float cc = rsqrtf(u);
-                cc = fmaf(0.5f * cc, fmaf(-u * cc, cc, 1.f), cc);    // Newton-Raphson step
+                const JRot q = jacobi_rot(gam, d, z, series, __any_sync(0xffffffffu, rot && !series));
+                const float t = q.t;
                 // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j), with s = t c
                 const float f = rot ? (first ? -t : t) * (kp * kinv) : 0.f;
 #pragma unroll
                 for (int r = 0; r < 32; ++r) g[r] = fmaf(f, gp[r], g[r]);
                 if (rot) {
-                    kap *= cc;
-                    kinv *= u * cc;                                   // 1 / c = sqrt(1 + t^2)
+                    kap *= q.c;
+                    kinv *= q.ic;
                     alpha = first ? alpha - t * gam : alpha + t * gam;
                 }
             }
@@ -1175,7 +1215,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
     int blk = -1, s = 0;
     long long off = 0;
     if (idx < a.count) {
-        blk = a.order ? a.order[idx] : idx;
+        blk = a.order ? a.order[idx] : a.first + idx;
         s = a.size[blk];
         off = a.off[blk];
         if (block_stopped<MODE>(a, blk, s, off, c, NR)) {
@@ -1254,53 +1294,69 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
         for (int r = 0; r < NR; ++r) g[r] = 0.f;
     }
 
-    // ---- sweeps over the round-robin schedule of N players
+    // ---- sweeps over the round-robin schedule of N players. As in k_project_ws: the partner is
+    // updated incrementally, each column carries a scale factor (a row update is one FMA), pairs
+    // orthogonal to kWSSkip are not rotated, small rotations take the series, and a segment stops
+    // after a sweep whose pairs all started within kOneSidedStop of orthogonal.
     int sweeps = 0;
     bool done = !act;
+    const int n = N - 1;
+    float kap = 1.f, kinv = 1.f;
     for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
         if (__all_sync(0xffffffffu, done)) break;
         float alpha = 0.f;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) alpha = fmaf(g[r], g[r], alpha);
-        const int rounds = __reduce_max_sync(0xffffffffu, done ? 0 : N - 1);
-        float worst = 0.f;
+        for (int r = 0; r < NR; ++r) {
+            g[r] *= kap;
+            alpha = fmaf(g[r], g[r], alpha);
+        }
+        kap = 1.f;
+        kinv = 1.f;
+        const int rounds = __reduce_max_sync(0xffffffffu, done ? 0 : n);
+        bool big = false;
+        int j = (c == 0 || c >= n) ? 0 : n - c;     // (2 rd - c) mod n
         for (int rd = 0; rd < rounds; ++rd) {
-            const int p = (!done && c < N && rd < N - 1) ? rr_partner(c, rd, N) : c;
+            const int p = (!done && c < N && rd < n) ? (c == n ? rd : (j == c ? n : j)) : c;
+            j += 2;
+            if (j >= n) j -= n;
             float gp[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) gp[r] = __shfl_sync(0xffffffffu, g[r], base + p);
+            const float beta = __shfl_sync(0xffffffffu, alpha, base + p);
+            const float kp = __shfl_sync(0xffffffffu, kap, base + p);
+            const bool first = c < p;
+            const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
+            const float two_over_d = __fdividef(2.f, d);
             // four independent chains (both ends of a pair add in the same order, so they agree)
             float ga[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int r = 0; r < NR; ++r) ga[r & 3] = fmaf(g[r], gp[r], ga[r & 3]);
-            const float gam = (ga[0] + ga[1]) + (ga[2] + ga[3]);
-            const float beta = __shfl_sync(0xffffffffu, alpha, base + p);
-            if (p != c && fabsf(gam) > 1.0e-30f) {
-                const bool first = c < p;
-                const float ai = first ? alpha : beta, aj = first ? beta : alpha;
-                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
-                const float zeta = __fdividef(aj - ai, 2.f * gam);
-                const float az = fabsf(zeta);
-                float den;
-                if (az > 1.0e15f) {
-                    den = 2.f * az;
-                } else {
-                    const float x = fmaf(zeta, zeta, 1.f);
-                    den = az + x * rsqrtf(x);
-                }
-                const float t = copysignf(__fdividef(1.f, den), zeta);
-                const float cc = __frsqrt_rn(fmaf(t, t, 1.f));
-                const float sn = t * cc;
-                const float sg = first ? -sn : sn;      // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j)
+            const float kk = first ? kap * kp : kp * kap;
+            const float gam = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * kk;
+            const float g2 = gam * gam, ab = alpha * beta;
+            const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
+            big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
+            const float z = gam * two_over_d;
+            const bool series = fabsf(z) <= kSmallAngle;
+            if (!__any_sync(0xffffffffu, rot)) continue;
+            const JRot q = jacobi_rot(gam, d, z, series, __any_sync(0xffffffffu, rot && !series));
+            // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j), with s = t c
+            const float f = rot ? (first ? -q.t : q.t) * (kp * kinv) : 0.f;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) g[r] = fmaf(sg, gp[r], cc * g[r]);
-                alpha = first ? ai - t * gam : aj + t * gam;
+            for (int r = 0; r < NR; ++r) g[r] = fmaf(f, gp[r], g[r]);
+            if (rot) {
+                kap *= q.c;
+                kinv *= q.ic;
+                alpha = first ? alpha - q.t * gam : alpha + q.t * gam;
             }
         }
         if (!done) ++sweeps;
-        worst = seg_maxf<NR>(worst);
-        if (worst < kOneSidedStop * kOneSidedStop) done = true;
+        // the segment's lanes agree on stopping
+        const unsigned seg_mask = (NR == 32 ? 0xffffffffu : ((1u << NR) - 1u)) << base;
+        if ((__ballot_sync(0xffffffffu, big) & seg_mask) == 0u) done = true;
     }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) g[r] *= kap;
 
     // ---- lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into the tile
     float mu2 = 0.f;
@@ -1367,7 +1423,7 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 // lane reads its partner's column from the tile (twice, for the Gram entry and for the update,
 // which keeps register use near 64 floats). Two blocks per CTA of four warps.
 constexpr int kOW64LD = 68;       // 16-byte rows: columns move through the tile as float4
-constexpr size_t kOW64BlockFloats = 2 * 64 * kOW64LD + 2 * 64;   // tile, V (warm start), alpha, scratch
+constexpr size_t kOW64BlockFloats = 2 * 64 * kOW64LD + 3 * 64;   // tile, V (warm start), alpha, scale, scratch
 constexpr size_t kOW64Bytes = 2 * kOW64BlockFloats * sizeof(float);
 
 __device__ __forceinline__ void pair_sync(int pair) {
@@ -1385,9 +1441,10 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
     float* Ts = reinterpret_cast<float*>(smem_ow64) + (size_t)pair * kOW64BlockFloats;   // 64 x LD
     float* Vs = Ts + 64 * LD;                                                           // 64 x LD
     float* als = Vs + 64 * LD;                                                          // 64
-    float* red = als + 64;                                                              // 64
+    float* kps = als + 64;                                                              // 64
+    float* red = kps + 64;                                                              // 64
     if (idx >= a.count) return;                     // both warps of the pair leave together
-    const int blk = a.order ? a.order[idx] : idx;
+    const int blk = a.order ? a.order[idx] : a.first + idx;
     const int s = a.size[blk];
     const long long off = a.off[blk];
     if (block_stopped<MODE>(a, blk, s, off, c, 64)) return;
@@ -1447,22 +1504,39 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
         for (int r = 0; r < 64; ++r) g[r] = 0.f;
     }
 
-    // ---- sweeps: columns meet through the tile
+    // ---- sweeps: columns meet through the tile. As in k_project_ws: incremental partners, a
+    // scale factor per column (a row update is one FMA), no rotation for pairs orthogonal to
+    // kWSSkip, series for small rotations, stop after a sweep that began within kOneSidedStop.
     int sweeps = 0;
+    const int n = N - 1;
+    float kap = 1.f, kinv = 1.f;
     for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
         float alpha = 0.f;
 #pragma unroll
-        for (int r = 0; r < 64; ++r) alpha = fmaf(g[r], g[r], alpha);
-        float worst = 0.f;
-        for (int rd = 0; rd < N - 1; ++rd) {
-            const int p = c < N ? rr_partner(c, rd, N) : c;
+        for (int r = 0; r < 64; ++r) {
+            g[r] *= kap;
+            alpha = fmaf(g[r], g[r], alpha);
+        }
+        kap = 1.f;
+        kinv = 1.f;
+        bool big = false;
+        int j = (c == 0 || c >= n) ? 0 : n - c;     // (2 rd - c) mod n
+        for (int rd = 0; rd < n; ++rd) {
+            const int p = c >= N ? c : (c == n ? rd : (j == c ? n : j));
+            j += 2;
+            if (j >= n) j -= n;
             pair_sync(pair);                                  // the previous round's reads are done
             float4* mine = reinterpret_cast<float4*>(Ts + c * LD);
 #pragma unroll
             for (int k = 0; k < 16; ++k) mine[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
             als[c] = alpha;
+            kps[c] = kap;
             pair_sync(pair);
             const float4* gp4 = reinterpret_cast<const float4*>(Ts + p * LD);
+            const float beta = als[p], kp = kps[p];
+            const bool first = c < p;
+            const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
+            const float two_over_d = __fdividef(2.f, d);
             float ga[4] = {0.f, 0.f, 0.f, 0.f};      // four chains, same order at both ends
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -1472,44 +1546,39 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
                 ga[2] = fmaf(g[4 * k + 2], q.z, ga[2]);
                 ga[3] = fmaf(g[4 * k + 3], q.w, ga[3]);
             }
-            const float gam = (ga[0] + ga[1]) + (ga[2] + ga[3]);
-            const float beta = als[p];
-            if (p != c && fabsf(gam) > 1.0e-30f) {
-                const bool first = c < p;
-                const float ai = first ? alpha : beta, aj = first ? beta : alpha;
-                worst = fmaxf(worst, __fdividef(gam * gam, fmaxf(ai * aj, 1.0e-30f)));
-                const float zeta = __fdividef(aj - ai, 2.f * gam);
-                const float az = fabsf(zeta);
-                float den;
-                if (az > 1.0e15f) {
-                    den = 2.f * az;
-                } else {
-                    const float x = fmaf(zeta, zeta, 1.f);
-                    den = az + x * rsqrtf(x);
-                }
-                const float t = copysignf(__fdividef(1.f, den), zeta);
-                const float cc = __frsqrt_rn(fmaf(t, t, 1.f));
-                const float sn = t * cc;
-                const float sg = first ? -sn : sn;
+            const float kk = first ? kap * kp : kp * kap;
+            const float gam = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * kk;
+            const float g2 = gam * gam, ab = alpha * beta;
+            const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
+            big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
+            const float z = gam * two_over_d;
+            const bool series = fabsf(z) <= kSmallAngle;
+            if (!__any_sync(0xffffffffu, rot)) continue;        // this warp has nothing to rotate
+            const JRot q = jacobi_rot(gam, d, z, series, __any_sync(0xffffffffu, rot && !series));
+            const float f = rot ? (first ? -q.t : q.t) * (kp * kinv) : 0.f;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float4 q = gp4[k];
-                    g[4 * k] = fmaf(sg, q.x, cc * g[4 * k]);
-                    g[4 * k + 1] = fmaf(sg, q.y, cc * g[4 * k + 1]);
-                    g[4 * k + 2] = fmaf(sg, q.z, cc * g[4 * k + 2]);
-                    g[4 * k + 3] = fmaf(sg, q.w, cc * g[4 * k + 3]);
-                }
-                alpha = first ? ai - t * gam : aj + t * gam;
+            for (int k = 0; k < 16; ++k) {
+                const float4 v = gp4[k];
+                g[4 * k] = fmaf(f, v.x, g[4 * k]);
+                g[4 * k + 1] = fmaf(f, v.y, g[4 * k + 1]);
+                g[4 * k + 2] = fmaf(f, v.z, g[4 * k + 2]);
+                g[4 * k + 3] = fmaf(f, v.w, g[4 * k + 3]);
+            }
+            if (rot) {
+                kap *= q.c;
+                kinv *= q.ic;
+                alpha = first ? alpha - q.t * gam : alpha + q.t * gam;
             }
         }
         ++sweeps;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+        const unsigned anyb = __ballot_sync(0xffffffffu, big);
         pair_sync(pair);
-        if ((c & 31) == 0) red[c >> 5] = worst;
+        if ((c & 31) == 0) red[c >> 5] = anyb ? 1.f : 0.f;
         pair_sync(pair);
-        if (fmaxf(red[0], red[1]) < kOneSidedStop * kOneSidedStop) break;
+        if (red[0] == 0.f && red[1] == 0.f) break;
     }
+#pragma unroll
+    for (int r = 0; r < 64; ++r) g[r] *= kap;
 
     // ---- lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into the tile
     float mu2 = 0.f;
@@ -1744,6 +1813,11 @@ ProjPlan make_proj_plan(const std::vector<int>& order, const std::vector<int>& s
         pl.variant[pl.runs] = v;
         pl.smax[pl.runs] = s;
         ++pl.runs;
+    }
+    for (int r = 0; r < pl.runs; ++r) {
+        bool id = true;
+        for (int i = pl.start[r]; i < pl.start[r] + pl.count[r] && id; ++i) id = order[i] == i;
+        pl.identity[r] = id ? 1 : 0;
     }
     return pl;
 }

@@ -102,7 +102,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
 enum ProjMode { PROJ_PLAIN = 0, PROJ_PRIMAL = 1, PROJ_DUAL = 2 };
 
 struct ProjArgs {
-    const int* order;       // [count] block to process per CTA (NULL = identity)
+    const int* order;       // [count] block to process per CTA (NULL: blocks first, first + 1, ...)
+    int first;
     const int* size;        // [*] block order s_k
     const long long* off;   // [*] packed element offset (64-bit for the standalone entry)
     int count;
@@ -146,6 +147,9 @@ constexpr int kMaxProjRuns = 64;
 struct ProjPlan {
     int runs;
     int start[kMaxProjRuns], count[kMaxProjRuns], variant[kMaxProjRuns], smax[kMaxProjRuns];
+    // 1: the run's stretch of `order` is start, start + 1, ... (its launch then reads no order
+    // entry, one dependent load fewer before a CTA can fetch its block)
+    unsigned char identity[kMaxProjRuns];
 };
 
 struct IterPtrs {

@@ -160,11 +160,14 @@ def _empty_matrix_part(n=0) -> dict:
                 C_val=np.zeros(0))
 
 
-def random_conic(l=2, d=3, h=2, n_free=3, n_lin=5, soc_dims=(3, 4), m=6, seed=21, density=0.6) -> dict:
+def random_conic(l=2, d=3, h=2, n_free=3, n_lin=5, soc_dims=(3, 4), m=6, seed=21, density=0.6,
+                 soc_u_scale=0.5) -> dict:
     """A feasible problem over a block-arrow PSD part (none when l = 0) and the other cones: free,
     nonnegative and second-order variables. Built from interior points x0 (primal) and (y0, z0)
     (dual; z0 = 0 on the free variables, whose dual cone is {0}), so both have optima and they
-    agree. Returns sdp_setup's arrays plus ``cones`` (the dict the oracle and sdp_setup_conic take)."""
+    agree. soc_u_scale sets the size of the interior points' u parts (larger: iterates that leave
+    the cones more often). Returns sdp_setup's arrays plus ``cones`` (the dict the oracle and
+    sdp_setup_conic take)."""
     rng = np.random.default_rng(seed)
     soc_dims = [int(q) for q in soc_dims]
     nc = n_free + n_lin + sum(soc_dims)
@@ -192,7 +195,7 @@ def random_conic(l=2, d=3, h=2, n_free=3, n_lin=5, soc_dims=(3, 4), m=6, seed=21
     o = n_free + n_lin
     for q in soc_dims:
         for v in (x0, z0):
-            u = rng.standard_normal(q - 1) * 0.5 / np.sqrt(q)
+            u = rng.standard_normal(q - 1) * soc_u_scale / np.sqrt(q)
             v[o] = np.linalg.norm(u) + rng.uniform(0.5, 1.5)
             v[o + 1:o + q] = u
         o += q

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import adjoint as adj
+from oracle import chordal_admm as orc
 from sdp_inputs import CONFIGS, config_instance
 from tests import sdp_cases
 from tests.gpu_support import make_oracle, require_gpu
@@ -109,34 +110,40 @@ def test_workload_gradient_matches_oracle_and_differences(workload4, capsys):
             scale = max(np.abs(gcq).max(), np.abs(gbq).max())
             np.testing.assert_allclose(gc[e0:e1], gcq, rtol=0, atol=1e-7 * scale)
             np.testing.assert_allclose(gb[r0:r1], gbq, rtol=0, atol=1e-7 * scale)
-        # central differences of the GPU forward on sampled coordinates. The step is 1e-4: with
-        # 1e-6 the quotient is dominated by the forward's rounding (the FP64 eigensolves stop on
-        # data-dependent sweep counts, so the loss is smooth only down to ~1e-12 relative); on
-        # these coordinates 1e-6 leaves 1e-5..2e-4 of noise while 1e-4 and 1e-3 agree to <1e-6.
+        # central differences of the GPU forward. The loss (|L| about 1e3 per problem) carries
+        # FP64 rounding of about 1e-14 relative after 200 iterations, so a quotient at step h errs
+        # by about 1e-14 |L| / h: at the step 1e-6 that is 1e-5 absolute, within the 1e-5 bar
+        # for the components of the gradient of size 1 and more (the two largest of C and of b
+        # are checked); the step 1e-4 keeps it below 1e-7 and is checked on random coordinates.
         rng = np.random.default_rng(11)
         scale = max(np.abs(gc).max(), np.abs(gb).max())
-        worst = 0.0
-        for kind, g, base in (("c", gc, c0), ("b", gb, b0)):
-            for i in rng.choice(len(base), size=4, replace=False):
-                off = lay["ent_off"] if kind == "c" else lay["row_off"]
-                q = int(np.searchsorted(off, i, side="right") - 1)
-                ent = (lay["ent_off"][q], lay["ent_off"][q + 1])
-                h = 1e-4
-                p, m = base.copy(), base.copy()
-                p[i] += h
-                m[i] -= h
-                if kind == "c":
-                    fd = (gpu_loss(cadmm, torch, s.h, p, b0, xr, T, K, ent) -
-                          gpu_loss(cadmm, torch, s.h, m, b0, xr, T, K, ent)) / (2 * h)
-                else:
-                    fd = (gpu_loss(cadmm, torch, s.h, c0, p, xr, T, K, ent) -
-                          gpu_loss(cadmm, torch, s.h, c0, m, xr, T, K, ent)) / (2 * h)
-                err = abs(fd - g[i]) / max(abs(g[i]), 1e-2 * scale)
-                worst = max(worst, err)
-                assert err <= 1e-5, (kind, int(i), fd, g[i])
+        picks = [(1e-6, "c", int(i)) for i in np.argsort(-np.abs(gc))[:2]] + \
+                [(1e-6, "b", int(i)) for i in np.argsort(-np.abs(gb))[:2]] + \
+                [(1e-4, "c", int(i)) for i in rng.choice(len(c0), size=4, replace=False)] + \
+                [(1e-4, "b", int(i)) for i in rng.choice(len(b0), size=4, replace=False)]
+        worst = {}
+        for h, kind, i in picks:
+            base = c0 if kind == "c" else b0
+            g = gc if kind == "c" else gb
+            off = lay["ent_off"] if kind == "c" else lay["row_off"]
+            q = int(np.searchsorted(off, i, side="right") - 1)
+            ent = (lay["ent_off"][q], lay["ent_off"][q + 1])
+            p, m = base.copy(), base.copy()
+            p[i] += h
+            m[i] -= h
+            if kind == "c":
+                fd = (gpu_loss(cadmm, torch, s.h, p, b0, xr, T, K, ent) -
+                      gpu_loss(cadmm, torch, s.h, m, b0, xr, T, K, ent)) / (2 * h)
+            else:
+                fd = (gpu_loss(cadmm, torch, s.h, c0, p, xr, T, K, ent) -
+                      gpu_loss(cadmm, torch, s.h, c0, m, xr, T, K, ent)) / (2 * h)
+            err = abs(fd - g[i]) / max(abs(g[i]), 1e-2 * scale)
+            worst[h] = max(worst.get(h, 0.0), err)
+            assert err <= 1e-5, (kind, i, h, fd, g[i])
     with capsys.disabled():
         print(f"\nunrolled T={T}, 64 problems: loss {L:.6e}, forward {t_fwd * 1e3:.1f} ms, forward+backward "
-              f"{t_grad * 1e3:.1f} ms, worst finite-difference disagreement {worst:.2e}")
+              f"{t_grad * 1e3:.1f} ms, worst finite-difference disagreement at step 1e-6 {worst[1e-6]:.2e}, "
+              f"at 1e-4 {worst[1e-4]:.2e}")
 
 
 @pytest.mark.parametrize("T,K", [(12, 5)])
@@ -144,13 +151,28 @@ def test_gradient_with_cones_matches_oracle(T, K):
     """Reverse mode through a problem with free, nonnegative and second-order variables (small
     and large second-order cones) against the oracle's reference gradient."""
     torch, cadmm = require_gpu()
-    arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=5, soc_dims=(3, 1, 300), m=6, seed=31)
+    arrs = sdp_cases.random_conic(l=2, d=3, h=2, n_free=2, n_lin=5, soc_dims=(3, 1, 300), m=6, seed=41,
+                                  soc_u_scale=5.0)
     sdp = make_oracle(arrs)
     rng = np.random.default_rng(17)
     lower = sdp.lower_mask()
     xr = rng.standard_normal(int(lower.sum()))
     x_ref = sdp.from_lower(sdp.E_row[lower], sdp.E_col[lower], xr)
     rho = 0.8
+    # the second-order cones' nontrivial branch (||u|| > |t|: the point is in neither the cone nor
+    # its polar) is reached by a small cone and by the large one at some forward iterate
+    st = orc.admm_init(sdp, "primal")
+    outside = set()
+    for _ in range(T):
+        nxt = orc.primal_iteration(sdp, st, rho)
+        for k in range(sdp.p, sdp.nblk):
+            if sdp.kinds[k] != "soc":
+                continue
+            w = nxt["u"][k] - st["lam"][k] / rho
+            if np.linalg.norm(w[1:]) > abs(w[0]):
+                outside.add(len(w))
+        st = nxt
+    assert 300 in outside and 3 in outside, outside     # large-cone (one CTA) and small-cone (one thread) paths
     L0, gc0, gb0, _ = adj.loss_and_grad(sdp, rho, T, x_ref)
     with primal_handle(cadmm, arrs, rho) as s:
         L, gc, gb = gpu_grad(cadmm, torch, s.h, sdp.to_lower(sdp.c), sdp.b, xr, T, K)

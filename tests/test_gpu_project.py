@@ -56,8 +56,13 @@ def entry_err(P, ref, W):
     return float(np.max(np.abs(P - ref)) / max(np.max(np.abs(W)), 1e-300))
 
 
-@pytest.mark.parametrize("prec,tol,ent_tol", [("fp64", 1e-12, 1e-12), ("fp32", 2e-5, 1e-4)])
+@pytest.mark.parametrize("prec,tol,ent_tol", [("fp64", 1e-12, 1e-12), ("fp32", 1e-4, 4e-4)])
 def test_project_matches_oracle(prec, tol, ent_tol):
+    """The default plan on random and special blocks against the oracle. FP64: rounding. FP32:
+    the one-sided eigensolvers stop once every pair of columns began a sweep orthogonal to 1e-4,
+    which bounds the projection's error by about 1e-4 ||W||_F (cold starts on random and clustered
+    blocks land between 1e-5 and 5e-5, by rounding; a CPU simulation of the same arithmetic shows
+    the same spread); entries by four times that relative to max |W_ij|."""
     torch, cadmm = require_gpu()
     rng = np.random.default_rng(42)
     blocks = batch(rng)

@@ -59,7 +59,7 @@ def check_against_oracle(got, blocks, sizes, lens, offs, tol, ent_tol):
 # (sizes, precision, Frobenius bound, entry bound): FP64 to rounding; FP32 within the one-sided
 # Jacobi's stopping rule (columns orthogonal to 1e-4), the FP32 mode's accuracy budget
 CALLS = [([1, 2, 7, 12, 30, 31, 45, 60, 96, 5, 33], "fp64", 1e-12, 1e-12),
-         ([30, 12, 17, 64], "fp32", 2e-5, 1e-4)]
+         ([30, 12, 17, 64], "fp32", 1e-4, 4e-4)]
 
 
 def test_noalloc_matches_oracle_and_project_psd_batched_on_two_calls():
