@@ -68,8 +68,14 @@ typedef struct {
                           iterating, which can move its results by rounding.                   */
     int form;          /* SDP_PRIMAL or SDP_DUAL                                                 */
     int prec;          /* SDP_PROJ_FP64 or SDP_PROJ_FP32                                         */
-    int flags;         /* reserved, must be 0                                                    */
+    int flags;         /* 0 or SDP_FLAG_HOST_KKT                                                 */
 } admm_opts;
+
+/* By default sdp_setup and sdp_setup_conic form A D^-1 A^T, its Cholesky factor and inverse on the
+ * GPU (FP64) when 64 <= m <= 4096 and no column of A on the pattern has more than 4096 nonzeros;
+ * batches and other sizes take the host. SDP_FLAG_HOST_KKT keeps them on the host always (the two
+ * agree to rounding; sdp_set_opts does not change where an existing handle was factored). */
+#define SDP_FLAG_HOST_KKT 1
 
 typedef struct {
     int iters;         /* iterations performed on this handle since the last admm_reset          */

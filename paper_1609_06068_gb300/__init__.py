@@ -47,6 +47,7 @@ EXPORTS = [
     "sdp_status_string", "sdp_last_error",
 ]
 SDP_NOALLOC_MAX_BLOCKS = 32768
+SDP_FLAG_HOST_KKT = 1
 
 
 class SDPError(RuntimeError):
@@ -193,9 +194,10 @@ def _dev_ptr(t, n: int | None = None, name: str = "tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_opts(rho=1.0, tol=1e-4, max_iter=2000, check_every=16, form="primal", prec="fp64") -> admm_opts:
+def make_opts(rho=1.0, tol=1e-4, max_iter=2000, check_every=16, form="primal", prec="fp64",
+              flags=0) -> admm_opts:
     return admm_opts(float(rho), float(tol), int(max_iter), int(check_every),
-                     FORMS.get(form, form), PRECS.get(prec, prec), 0)
+                     FORMS.get(form, form), PRECS.get(prec, prec), int(flags))
 
 
 def _result(r: admm_result) -> dict:

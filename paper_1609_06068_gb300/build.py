@@ -19,7 +19,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libchordal_admm.so")
 OBJDIR = os.path.join(ROOT, "_build")
 
-SOURCES = ["setup.cpp", "chordal.cpp", "project.cu", "kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "chordal.cpp", "project.cu", "kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu", "kkt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
           "-I" + os.path.join(ROOT, "include")]

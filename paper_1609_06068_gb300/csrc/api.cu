@@ -58,7 +58,7 @@ int check_opts(const admm_opts* o) {
     if (o->max_iter < 0 || o->check_every < 0) return set_err(SDP_ERR_ARG, "max_iter and check_every must be >= 0");
     if (o->form != SDP_PRIMAL && o->form != SDP_DUAL) return set_err(SDP_ERR_ARG, "form must be SDP_PRIMAL or SDP_DUAL");
     if (o->prec != SDP_PROJ_FP64 && o->prec != SDP_PROJ_FP32) return set_err(SDP_ERR_ARG, "prec must be SDP_PROJ_FP64 or SDP_PROJ_FP32");
-    if (o->flags != 0) return set_err(SDP_ERR_ARG, "flags must be 0");
+    if ((o->flags & ~SDP_FLAG_HOST_KKT) != 0) return set_err(SDP_ERR_ARG, "flags must be 0 or SDP_FLAG_HOST_KKT");
     return SDP_OK;
 }
 
@@ -654,13 +654,43 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(sell_off, hp.sell_off);
     UP(sell_row, hp.sell_row);
     UP(sell_val, hp.sell_val);
-    P.kkt_tri = hp.kkt_tri ? 1 : 0;
-    if (hp.kkt_tri) {
-        UP(Linv, hp.Linv);
-        UP(LinvT, hp.LinvT);
-        if ((rc = h->dalloc(&P.z1, (size_t)std::max(1, hp.m)))) return rc;
+    if (hp.kkt_on_device) {
+        // the KKT factorization on the device, from the A^T slices and w/D just uploaded
+        cadmm::KktInputs ki;
+        ki.m = hp.m;
+        ki.nslices = (int)hp.sell_len.size();
+        ki.sell_col = P.sell_col;
+        ki.sell_off = P.sell_off;
+        ki.sell_row = P.sell_row;
+        ki.sell_val = P.sell_val;
+        ki.wdinv = P.wdinv;
+        ki.slot_len_h.swap(hp.slot_len);
+        cadmm::KktOutputs ko;
+        const size_t mm = (size_t)hp.m * hp.m;
+        double *L = nullptr, *Li = nullptr, *LiT = nullptr, *Mi = nullptr;
+        if ((rc = h->dalloc(&L, mm)) || (rc = h->dalloc(&Li, mm)) || (rc = h->dalloc(&LiT, mm)) ||
+            (rc = h->dalloc(&Mi, mm)))
+            return rc;
+        ko.L = L;
+        ko.Linv = Li;
+        ko.LinvT = LiT;
+        ko.Minv = Mi;
+        std::string kerr;
+        if ((rc = cadmm::device_kkt(ki, ko, kerr))) return set_err(rc, kerr);
+        P.kkt_tri = ko.kappa1 > cadmm::kKktTriCond ? 1 : 0;
+        P.Minv = Mi;
+        P.Linv = Li;
+        P.LinvT = LiT;
+        if (P.kkt_tri && (rc = h->dalloc(&P.z1, (size_t)std::max(1, hp.m)))) return rc;
     } else {
-        UP(Minv, hp.Minv);
+        P.kkt_tri = hp.kkt_tri ? 1 : 0;
+        if (hp.kkt_tri) {
+            UP(Linv, hp.Linv);
+            UP(LinvT, hp.LinvT);
+            if ((rc = h->dalloc(&P.z1, (size_t)std::max(1, hp.m)))) return rc;
+        } else {
+            UP(Minv, hp.Minv);
+        }
     }
     UP(cone_lo, hp.cone_lo);
     UP(cone_hi, hp.cone_hi);
@@ -723,7 +753,8 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         HostProblem hp;
         std::string err;
         rc = cadmm::build_host_problem(n, m, A_ptr, A_row, A_col, A_val, b, C_nnz, C_row, C_col, C_val,
-                                       pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, nullptr, hp, err);
+                                       pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, nullptr, hp, err,
+                                       (opts->flags & SDP_FLAG_HOST_KKT) == 0);
         if (rc) return set_err(rc, err);
         return create_handle(hp, opts, out);
     } catch (const std::bad_alloc&) {
@@ -744,7 +775,8 @@ int sdp_setup_conic(const sdp_problem* pr, const sdp_cones* cones, const admm_op
         std::string err;
         rc = cadmm::build_host_problem(pr->n, pr->m, pr->A_ptr, pr->A_row, pr->A_col, pr->A_val, pr->b,
                                        pr->C_nnz, pr->C_row, pr->C_col, pr->C_val, pr->pat_nnz, pr->pat_row,
-                                       pr->pat_col, pr->p, pr->clique_ptr, pr->clique_vtx, cones, hp, err);
+                                       pr->pat_col, pr->p, pr->clique_ptr, pr->clique_vtx, cones, hp, err,
+                                       (opts->flags & SDP_FLAG_HOST_KKT) == 0);
         if (rc) return set_err(rc, err);
         return create_handle(hp, opts, out);
     } catch (const std::bad_alloc&) {

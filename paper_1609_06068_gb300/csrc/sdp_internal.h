@@ -60,6 +60,10 @@ struct HostProblem {
     std::vector<double> Linv, LinvT;
     double kkt_cond = 1.0;                      // kappa_1(A D^-1 A^T) (largest over a batch)
     bool kkt_tri = false;                       // affine step by the two triangular factors
+    // The factorization is left to the device (M, L, L^-1, M^-1 and kappa then come from
+    // device_kkt); slot_len[32 s + t] is the length of the column in slot t of A^T slice s.
+    bool kkt_on_device = false;
+    std::vector<int> slot_len;
     // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
     int ninst = 1;
     std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
@@ -91,11 +95,39 @@ int chordal_cliques(int n, long long nnz, const int* row, const int* col, std::v
 int build_host_problem_batch(int count, const sdp_problem* in, HostProblem& hp, std::string& err);
 
 // Builds HostProblem from the ABI inputs. Returns an SDP_* status and fills err on failure.
+// kkt_device: the KKT factorization may be left to device_kkt (if the problem fits its limits).
 int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, const int* A_col,
                        const double* A_val, const double* b, long long C_nnz, const int* C_row,
                        const int* C_col, const double* C_val, long long pat_nnz,
                        const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
-                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err);
+                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err,
+                       bool kkt_device = false);
+
+// ---------------------------------------------------------------- KKT factorization on the device
+// (kkt.cu) for single problems with kKktDeviceMinM <= m <= kKktDeviceMaxM and A^T columns of at
+// most 4096 nonzeros: M = A D^-1 A^T from the sliced ELL of A^T, L, L^-1, M^-1 and kappa_1(M).
+constexpr int kKktDeviceMinM = 64;
+constexpr int kKktDeviceMaxM = 4096;
+bool device_kkt_fits(int m, int max_col_len);
+struct KktInputs {
+    int m = 0, nslices = 0;
+    const int* sell_col = nullptr;
+    const long long* sell_off = nullptr;
+    const unsigned short* sell_row = nullptr;
+    const double* sell_val = nullptr;
+    const double* wdinv = nullptr;
+    std::vector<int> slot_len_h;
+    cudaStream_t stream = nullptr;
+};
+struct KktOutputs {
+    double* L = nullptr;       // m x m: M, then its Cholesky factor in the lower triangle
+    double* Linv = nullptr;    // m x m row-major, lower
+    double* LinvT = nullptr;   // m x m row-major, (L^-1)^T
+    double* Minv = nullptr;    // m x m row-major, symmetric
+    double kappa1 = 0.0;
+};
+// SDP_OK, SDP_ERR_NOT_PD (A numerically rank-deficient) or SDP_ERR_CUDA; synchronizes the stream.
+int device_kkt(const KktInputs& in, KktOutputs& out, std::string& err);
 
 // ---------------------------------------------------------------- kernel launch parameters
 

@@ -163,7 +163,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                        const double* A_val, const double* b, long long C_nnz, const int* C_row,
                        const int* C_col, const double* C_val, long long pat_nnz,
                        const int* pat_row, const int* pat_col, int p, const int* clique_ptr,
-                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err) {
+                       const int* clique_vtx, const sdp_cones* cones, HostProblem& hp, std::string& err,
+                       bool kkt_device) {
     // ---- cone variables (free, nonnegative, second-order), appended after the pattern entries
     long long nc = 0;
     if (cones) {
@@ -501,108 +502,115 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         });
     }
 
-    // ---- M = A D^-1 A^T on the full symmetric vectors: M_ij = sum_e w_e A_ie A_je / D_e, with
-    // w_e = 2 off the diagonal (both (i,j) and (j,i) of the pattern) and 1 on it. Columns are
-    // split into a fixed number of chunks so the sum order does not depend on the machine.
-    const size_t mm = (size_t)m * m;
-    std::vector<double> M(mm, 0.0);
-    {
-        const int chunks = (m <= 2048) ? 16 : 1;
-        std::vector<std::vector<double>> part(chunks);
-        auto work = [&](int ch) {
-            std::vector<double>& Mp = part[ch];
-            Mp.assign(mm, 0.0);
-            const long long e0 = (long long)nEL * ch / chunks, e1 = (long long)nEL * (ch + 1) / chunks;
-            for (long long e = e0; e < e1; ++e) {
-                const double wd = hp.wdinv[e];
-                const int lo = hp.c_colptr[e], hi = hp.c_colptr[e + 1];
-                for (int s1 = lo; s1 < hi; ++s1) {
-                    const double vi = wd * hp.c_val[s1];
-                    double* Mi = Mp.data() + (size_t)hp.c_row[s1] * m;
-                    for (int s2 = lo; s2 <= s1; ++s2) Mi[hp.c_row[s2]] += vi * hp.c_val[s2];
+    // ---- the KKT factorization: on the device (kkt.cu, after the upload) when the caller allows it
+    // and the problem fits its limits; here otherwise. The device needs each A^T slot's length.
+    int max_col = 0;
+    for (int e = 0; e < nEL; ++e) max_col = std::max(max_col, hp.c_colptr[e + 1] - hp.c_colptr[e]);
+    hp.kkt_on_device = kkt_device && m >= kKktDeviceMinM && device_kkt_fits(m, max_col);
+    if (!hp.kkt_on_device) {
+        // ---- M = A D^-1 A^T on the full symmetric vectors: M_ij = sum_e w_e A_ie A_je / D_e, with
+        // w_e = 2 off the diagonal (both (i,j) and (j,i) of the pattern) and 1 on it. Columns are
+        // split into a fixed number of chunks so the sum order does not depend on the machine.
+        const size_t mm = (size_t)m * m;
+        std::vector<double> M(mm, 0.0);
+        {
+            const int chunks = (m <= 2048) ? 16 : 1;
+            std::vector<std::vector<double>> part(chunks);
+            auto work = [&](int ch) {
+                std::vector<double>& Mp = part[ch];
+                Mp.assign(mm, 0.0);
+                const long long e0 = (long long)nEL * ch / chunks, e1 = (long long)nEL * (ch + 1) / chunks;
+                for (long long e = e0; e < e1; ++e) {
+                    const double wd = hp.wdinv[e];
+                    const int lo = hp.c_colptr[e], hi = hp.c_colptr[e + 1];
+                    for (int s1 = lo; s1 < hi; ++s1) {
+                        const double vi = wd * hp.c_val[s1];
+                        double* Mi = Mp.data() + (size_t)hp.c_row[s1] * m;
+                        for (int s2 = lo; s2 <= s1; ++s2) Mi[hp.c_row[s2]] += vi * hp.c_val[s2];
+                    }
                 }
+            };
+            parallel_for(chunks, work);
+            // the chunks add up in a fixed order; rows of M in parallel
+            parallel_for(m, [&](int i) {
+                double* Mi = M.data() + (size_t)i * m;
+                for (int ch = 0; ch < chunks; ++ch) {
+                    const double* Pi = part[ch].data() + (size_t)i * m;
+                    for (int j = 0; j < m; ++j) Mi[j] += Pi[j];
+                }
+            });
+        }
+
+        // ---- Cholesky M = L L^T (row-major lower, in place). A pivot at or below 1e-12 of the
+        // original diagonal means A has (numerically) dependent rows.
+        std::vector<double> L(mm, 0.0);
+        for (int j = 0; j < m; ++j) {
+            const double* Lj = L.data() + (size_t)j * m;
+            double d = M[(size_t)j * m + j];
+            for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
+            if (!(d > 1e-12 * M[(size_t)j * m + j]) || !std::isfinite(d))
+                return fail(err, SDP_ERR_NOT_PD, "A D^-1 A^T is not positive definite (A rank-deficient)");
+            const double ljj = std::sqrt(d);
+            L[(size_t)j * m + j] = ljj;
+            for (int i = j + 1; i < m; ++i) {
+                double* Li = L.data() + (size_t)i * m;
+                double s = M[(size_t)i * m + j];
+                for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+                Li[j] = s / ljj;
             }
-        };
-        parallel_for(chunks, work);
-        // the chunks add up in a fixed order; rows of M in parallel
+        }
+        // ---- L^-1 (lower) by forward substitution on the unit vectors (columns are independent: in
+        // parallel, each with its own work vector), then M^-1 = L^-T L^-1, so that the affine step's
+        // y is one product: M^-1_ij = sum_{k >= max(i, j)} L^-1_ki L^-1_kj, k ascending.
+        std::vector<double> Linv(mm, 0.0);
+        parallel_for(m, [&](int j) {
+            std::vector<double> xcol(m, 0.0);
+            xcol[j] = 1.0 / L[(size_t)j * m + j];
+            for (int i = j + 1; i < m; ++i) {
+                const double* Li = L.data() + (size_t)i * m;
+                double s = 0.0;
+                for (int k = j; k < i; ++k) s += Li[k] * xcol[k];
+                xcol[i] = -s / Li[i];
+            }
+            for (int i = j; i < m; ++i) Linv[(size_t)i * m + j] = xcol[i];
+        });
+        // (L^-1)^T row-major, so that the products below read rows
+        std::vector<double> LinvTr(mm, 0.0);
         parallel_for(m, [&](int i) {
-            double* Mi = M.data() + (size_t)i * m;
-            for (int ch = 0; ch < chunks; ++ch) {
-                const double* Pi = part[ch].data() + (size_t)i * m;
-                for (int j = 0; j < m; ++j) Mi[j] += Pi[j];
+            for (int k = i; k < m; ++k) LinvTr[(size_t)i * m + k] = Linv[(size_t)k * m + i];
+        });
+        hp.Minv.assign(mm, 0.0);
+        parallel_for(m, [&](int i) {
+            const double* Ti = LinvTr.data() + (size_t)i * m;
+            for (int j = 0; j <= i; ++j) {
+                const double* Tj = LinvTr.data() + (size_t)j * m;
+                double s = 0.0;
+                for (int k = i; k < m; ++k) s += Ti[k] * Tj[k];
+                hp.Minv[(size_t)i * m + j] = s;
             }
         });
-    }
-
-    // ---- Cholesky M = L L^T (row-major lower, in place). A pivot at or below 1e-12 of the
-    // original diagonal means A has (numerically) dependent rows.
-    std::vector<double> L(mm, 0.0);
-    for (int j = 0; j < m; ++j) {
-        const double* Lj = L.data() + (size_t)j * m;
-        double d = M[(size_t)j * m + j];
-        for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
-        if (!(d > 1e-12 * M[(size_t)j * m + j]) || !std::isfinite(d))
-            return fail(err, SDP_ERR_NOT_PD, "A D^-1 A^T is not positive definite (A rank-deficient)");
-        const double ljj = std::sqrt(d);
-        L[(size_t)j * m + j] = ljj;
-        for (int i = j + 1; i < m; ++i) {
-            double* Li = L.data() + (size_t)i * m;
-            double s = M[(size_t)i * m + j];
-            for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
-            Li[j] = s / ljj;
-        }
-    }
-    // ---- L^-1 (lower) by forward substitution on the unit vectors (columns are independent: in
-    // parallel, each with its own work vector), then M^-1 = L^-T L^-1, so that the affine step's
-    // y is one product: M^-1_ij = sum_{k >= max(i, j)} L^-1_ki L^-1_kj, k ascending.
-    std::vector<double> Linv(mm, 0.0);
-    parallel_for(m, [&](int j) {
-        std::vector<double> xcol(m, 0.0);
-        xcol[j] = 1.0 / L[(size_t)j * m + j];
-        for (int i = j + 1; i < m; ++i) {
-            const double* Li = L.data() + (size_t)i * m;
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s += Li[k] * xcol[k];
-            xcol[i] = -s / Li[i];
-        }
-        for (int i = j; i < m; ++i) Linv[(size_t)i * m + j] = xcol[i];
-    });
-    // (L^-1)^T row-major, so that the products below read rows
-    std::vector<double> LinvTr(mm, 0.0);
-    parallel_for(m, [&](int i) {
-        for (int k = i; k < m; ++k) LinvTr[(size_t)i * m + k] = Linv[(size_t)k * m + i];
-    });
-    hp.Minv.assign(mm, 0.0);
-    parallel_for(m, [&](int i) {
-        const double* Ti = LinvTr.data() + (size_t)i * m;
-        for (int j = 0; j <= i; ++j) {
-            const double* Tj = LinvTr.data() + (size_t)j * m;
-            double s = 0.0;
-            for (int k = i; k < m; ++k) s += Ti[k] * Tj[k];
-            hp.Minv[(size_t)i * m + j] = s;
-        }
-    });
-    for (int i = 0; i < m; ++i)
-        for (int j = i + 1; j < m; ++j) hp.Minv[(size_t)i * m + j] = hp.Minv[(size_t)j * m + i];
-    // kappa_1(M) = ||M||_1 ||M^-1||_1 (both symmetric: largest absolute row sums). With the
-    // explicit inverse, x = D^-1 (r - A^T y) misses A x = rhs2 by about kappa eps; with the two
-    // triangular factors by about eps, as with substitution. Above kKktTriCond the affine step
-    // takes the factors (one more launch per iteration).
-    {
-        double nm = 0.0, ni = 0.0;
-        for (int i = 0; i < m; ++i) {
-            double a = 0.0, bsum = 0.0;
-            for (int j = 0; j < m; ++j) {
-                a += std::fabs(M[(size_t)i * m + j]);
-                bsum += std::fabs(hp.Minv[(size_t)i * m + j]);
+        for (int i = 0; i < m; ++i)
+            for (int j = i + 1; j < m; ++j) hp.Minv[(size_t)i * m + j] = hp.Minv[(size_t)j * m + i];
+        // kappa_1(M) = ||M||_1 ||M^-1||_1 (both symmetric: largest absolute row sums). With the
+        // explicit inverse, x = D^-1 (r - A^T y) misses A x = rhs2 by about kappa eps; with the two
+        // triangular factors by about eps, as with substitution. Above kKktTriCond the affine step
+        // takes the factors (one more launch per iteration).
+        {
+            double nm = 0.0, ni = 0.0;
+            for (int i = 0; i < m; ++i) {
+                double a = 0.0, bsum = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    a += std::fabs(M[(size_t)i * m + j]);
+                    bsum += std::fabs(hp.Minv[(size_t)i * m + j]);
+                }
+                nm = std::max(nm, a);
+                ni = std::max(ni, bsum);
             }
-            nm = std::max(nm, a);
-            ni = std::max(ni, bsum);
+            hp.kkt_cond = m > 0 ? nm * ni : 1.0;
+            hp.kkt_tri = hp.kkt_cond > kKktTriCond;
         }
-        hp.kkt_cond = m > 0 ? nm * ni : 1.0;
-        hp.kkt_tri = hp.kkt_cond > kKktTriCond;
+        hp.Linv.swap(Linv);
     }
-    hp.Linv.swap(Linv);
 
     // ---- A^T as sliced ELL (32 columns per slice, one lane per column on the device). Within
     // each window of 256 consecutive columns the columns are ordered by length (longest first,
@@ -659,6 +667,13 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         });
         std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
         std::vector<unsigned short>().swap(hp.c_row);
+        if (hp.kkt_on_device) {
+            hp.slot_len.assign(32LL * ns, 0);
+            for (long long q = 0; q < 32LL * ns; ++q) {
+                const int c = slot_col[q];
+                hp.slot_len[q] = c < 0 ? 0 : hp.c_colptr[c + 1] - hp.c_colptr[c];
+            }
+        }
     }
 
     hp.ninst = 1;
@@ -668,7 +683,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     hp.inst_e = {0, nEL};
     hp.inst_pos = {0, hp.SL};
     hp.inst_row = {0, m};
-    hp.mblk_off = {0, (long long)mm};
+    hp.mblk_off = {0, (long long)m * m};
     if (hp.kkt_tri) fill_linv_t(hp);
     return SDP_OK;
 }

@@ -62,7 +62,7 @@ def rel_err(a, b) -> float:
 
 
 def setup_handle(cadmm, arrs, form="primal", prec="fp64", rho=1.0, tol=1e-4, max_iter=2000,
-                 check_every=16):
+                 check_every=16, flags=0):
     opts = cadmm.make_opts(rho=rho, tol=tol, max_iter=max_iter, check_every=check_every, form=form,
-                           prec=prec)
+                           prec=prec, flags=flags)
     return cadmm.ChordalADMM(arrs, opts)
