@@ -577,6 +577,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         s2 = cadmm.ChordalADMM(e2e_arrs, opts)
         e2e_setup_s += time.perf_counter() - t0
+        e2e_stages = cadmm.sdp_setup_times(s2.h)
         if tuned is not None:
             cadmm.sdp_set_proj_table(s2.h, "fp32", {int(n): cadmm.project_variants().index(v)
                                                     for n, v in tuned.items()})
@@ -594,7 +595,7 @@ def run_ours(args):
         e2e_s_max = reduce(world, e2e_s, "max")
         e2e = dict(value=e2e_iters_all / e2e_s_max, unit=unit, h2d_bytes_per_step=h2d,
                    d2h_bytes_per_step=d2h, ms_per_step=1e3 * e2e_s_max / args.e2e_steps,
-                   setup_ms=1e3 * e2e_setup_s / args.e2e_steps,
+                   setup_ms=1e3 * e2e_setup_s / args.e2e_steps, setup_stages_ms_last=e2e_stages,
                    includes="sdp_setup (host maps, upload; A D^-1 A^T, Cholesky and inverse on the "
                             "device from m = 64) + admm_solve + sdp_get_solution")
 
@@ -665,7 +666,7 @@ def run_sweep(args):
         params = dict(sw["fixed"], **{args.sweep: val})
         out = dict(sweep=args.sweep, point=i, value=val, params=params, n=inst.n, m=len(inst.b),
                    p=len(inst.cliques), clique=len(inst.cliques[0]), nnz_A=s.sizes["nnz_A"],
-                   setup_ms=1e3 * setup_s, tol=SWEEP_TOL, rho=rho)
+                   setup_ms=1e3 * setup_s, setup_stages_ms=cadmm.sdp_setup_times(s.h), tol=SWEEP_TOL, rho=rho)
         for prec in ("fp32", "fp64"):
             s.set_opts(prec=prec)
             s.reset()

@@ -359,6 +359,20 @@ int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len);
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
 const char* sdp_phase_name(sdp_handle h, int i);
 
+/* Wall-clock time of the stages of the sdp_setup* call that made h, in milliseconds (the
+ * set-up that Algorithms 1 and 2 do once before iterating: the clique maps, A on the lower
+ * pattern and the cached factor of A D^-1 A^T). Stage i is named by sdp_setup_stage_name(i):
+ * "host_build" (index maps, A in CSR and the A^T slice layout, and the KKT factorization when it
+ * is built on the host), "plan" (kernel preparation and work schedules), "alloc_upload" (device
+ * allocations and host-to-device copies), "device_kkt" (the wait for the A^T slices and the KKT
+ * factorization built on the device, which run while the copies after the CSR proceed; 0 when
+ * they are built on the host) and "finish" (pinned control block, stream, first reset and the
+ * closing device synchronization). Writes min(max_out, count) values and returns count (5), or
+ * SDP_ERR_ARG for a NULL handle or a NULL ms_out with max_out > 0. sdp_setup_stage_name returns
+ * NULL out of range. */
+int sdp_setup_times(sdp_handle h, double* ms_out, int max_out);
+const char* sdp_setup_stage_name(int i);
+
 /* Batched PSD projection that allocates nothing (no counterpart in the paper: it exists for
  * callers, not for the method). Same arguments and results (to rounding: every block goes to the
  * kernel variant that fits the largest one) as project_psd_batched, for

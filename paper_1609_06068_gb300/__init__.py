@@ -41,6 +41,7 @@ EXPORTS = [
     "sdp_setup", "sdp_setup_batch", "sdp_setup_conic", "sdp_batch_layout", "sdp_batch_results", "sdp_set_opts", "admm_reset", "admm_iterate", "admm_solve", "sdp_get_sizes",
     "sdp_get_solution", "sdp_get_state", "sdp_set_state", "sdp_get_maps", "sdp_gather",
     "sdp_scatter", "project_psd_batched", "sdp_time_phases", "sdp_phase_name",
+    "sdp_setup_times", "sdp_setup_stage_name",
     "project_psd_batched_noalloc", "project_variant_count", "project_variant_name",
     "project_variant_fits", "project_psd_batched_variant", "sdp_set_proj_table", "sdp_set_cost",
     "sdp_set_rhs", "sdp_unrolled_forward", "sdp_unrolled_backward", "sdp_chordal_cliques", "sdp_proj_sweeps", "sdp_plan", "sdp_free",
@@ -128,6 +129,8 @@ def load_library(path: str = LIB_PATH):
         "project_psd_batched": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "sdp_time_phases": (_I, [_P, _I, _P, _P, _I]),
         "sdp_phase_name": (ctypes.c_char_p, [_P, _I]),
+        "sdp_setup_times": (_I, [_P, _P, _I]),
+        "sdp_setup_stage_name": (ctypes.c_char_p, [_I]),
         "project_psd_batched_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
         "project_variant_count": (_I, []),
         "project_variant_name": (ctypes.c_char_p, [_I]),
@@ -525,6 +528,16 @@ def sdp_time_phases(h, reps: int = 20, stream=None) -> dict:
     if n < 0:
         _check(n, "sdp_time_phases")
     return {lib.sdp_phase_name(h, i).decode(): float(ms[i]) for i in range(n)}
+
+
+def sdp_setup_times(h) -> dict:
+    """Wall-clock milliseconds of the stages of the setup call that made h, by stage name."""
+    lib = load_library()
+    ms = np.zeros(8)
+    n = lib.sdp_setup_times(h, _ptr(ms), len(ms))
+    if n < 0:
+        _check(n, "sdp_setup_times")
+    return {lib.sdp_setup_stage_name(i).decode(): float(ms[i]) for i in range(n)}
 
 
 def sdp_phase_name(h, i: int) -> str | None:

@@ -68,8 +68,20 @@ namespace cadmm {
 int record_error(int code, const std::string& msg) { return set_err(code, msg); }
 }  // namespace cadmm
 
+// Wall-clock stages of sdp_setup*, in milliseconds (sdp_setup_times).
+enum { kSetupHost = 0, kSetupPlan, kSetupUpload, kSetupKkt, kSetupFinish, kSetupStages };
+const char* const kSetupStageName[kSetupStages] = {"host_build", "plan", "alloc_upload", "device_kkt", "finish"};
+using SetupClock = std::chrono::steady_clock;
+double ms_since(SetupClock::time_point& t) {
+    const SetupClock::time_point now = SetupClock::now();
+    const double ms = std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+    return ms;
+}
+
 struct sdp_ctx {
     int device = 0;
+    double setup_ms[kSetupStages] = {};
     admm_opts opts{};
     int n = 0, m = 0, p = 0, smax = 0, nEL = 0, SL = 0, ninst = 1;
     int n_cone = 0;               // non-PSD cone variables (last n_cone entries and positions)
@@ -128,8 +140,8 @@ struct sdp_ctx {
         *ptr = static_cast<T*>(p_);
         return SDP_OK;
     }
-    template <typename T>
-    int upload(T** ptr, const std::vector<T>& v, size_t capacity = 0) {
+    template <typename T, typename Alloc>
+    int upload(T** ptr, const std::vector<T, Alloc>& v, size_t capacity = 0) {
         int rc = dalloc(ptr, std::max(v.size(), capacity));
         if (rc) return rc;
         if (!v.empty()) {
@@ -523,9 +535,11 @@ int run_project_batched(const double* in, double* out, const int* sizes, const l
     return SDP_OK;
 }
 
-int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
+int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out, double host_ms) {
+    SetupClock::time_point clk = SetupClock::now();
     sdp_ctx* h = new sdp_ctx();
     std::unique_ptr<sdp_ctx> guard(h);
+    h->setup_ms[kSetupHost] = host_ms;
     CK(cudaGetDevice(&h->device));
     h->opts = *opts;
     h->n = hp.n; h->m = hp.m; h->p = hp.p; h->smax = hp.smax;
@@ -566,6 +580,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     }
     const Schedules S = build_schedules(h->src, std::vector<char>(hp.ninst, 1));
     h->planned = hp.ninst;
+    h->setup_ms[kSetupPlan] = ms_since(clk);
     IterPtrs& P = h->P;
     P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
     P.ninst = hp.ninst;
@@ -597,6 +612,62 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(inst_row, hp.inst_row);
     UP(mblk_off, hp.mblk_off);
     UP(blk_inst, blk_inst);
+    // A^T slices, w/D and the CSR of A first: from them the device builds the slices' contents and
+    // the KKT factorization (on a stream of its own) while the rest is uploaded
+    UP(wdinv, hp.wdinv);
+    UP(sell_col, hp.sell_col);
+    UP(sell_len, hp.sell_len);
+    UP(sell_off, hp.sell_off);
+    UP(a_rowptr, hp.a_rowptr);
+    UP(a_col, hp.a_col);
+    UP(a_val, hp.a_val);
+    const long long ell_size = hp.sell_off.empty() ? 0 : hp.sell_off.back();
+    unsigned short* ell_row = nullptr;
+    double* ell_val = nullptr;
+    if (hp.kkt_on_device) {     // filled on the device from the CSR
+        if ((rc = h->dalloc(&ell_row, (size_t)ell_size)) || (rc = h->dalloc(&ell_val, (size_t)ell_size))) return rc;
+        P.sell_row = ell_row;
+        P.sell_val = ell_val;
+    } else {
+        UP(sell_row, hp.sell_row);
+        UP(sell_val, hp.sell_val);
+    }
+    cadmm::KktRun kkt_run;      // declared after guard: waits for its stream before h is freed
+    cadmm::KktOutputs ko;
+    if (hp.kkt_on_device) {
+        cadmm::KktInputs ki;
+        int* col_slot = nullptr;
+        if ((rc = h->upload(&col_slot, hp.col_slot))) return rc;
+        ki.m = hp.m;
+        ki.nslices = (int)hp.sell_len.size();
+        ki.sell_col = P.sell_col;
+        ki.sell_len = P.sell_len;
+        ki.sell_off = P.sell_off;
+        ki.sell_row = P.sell_row;
+        ki.sell_val = P.sell_val;
+        ki.wdinv = P.wdinv;
+        ki.slot_len_h.swap(hp.slot_len);
+        ki.a_rowptr = P.a_rowptr;
+        ki.a_col = P.a_col;
+        ki.a_val = P.a_val;
+        ki.nnz = hp.nnz;
+        ki.nEL = hp.nEL;
+        ki.col_slot = col_slot;
+        ki.ell_row = ell_row;
+        ki.ell_val = ell_val;
+        ki.ell_size = ell_size;
+        const size_t mm = (size_t)hp.m * hp.m;
+        double *L = nullptr, *Li = nullptr, *LiT = nullptr, *Mi = nullptr;
+        if ((rc = h->dalloc(&L, mm)) || (rc = h->dalloc(&Li, mm)) || (rc = h->dalloc(&LiT, mm)) ||
+            (rc = h->dalloc(&Mi, mm)))
+            return rc;
+        ko.L = L;
+        ko.Linv = Li;
+        ko.LinvT = LiT;
+        ko.Minv = Mi;
+        std::string kerr;
+        if ((rc = cadmm::device_kkt_launch(ki, ko, kkt_run, kerr))) return set_err(rc, kerr);
+    }
     // Re-planning a batch for fewer problems splits their work more finely, so the schedules and
     // partial sums are sized for the finest split any subset can get (chunks of at least 1024
     // nonzeros per row, one slice per A^T chunk, 256 positions per update CTA).
@@ -642,45 +713,18 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
     UP(heavy, hp.heavy);
     UP(D, hp.D);
     UP(dinv, hp.dinv);
-    UP(wdinv, hp.wdinv);
     UP(c, hp.c);
     UP(b, hp.b);
     UP(ew, hp.ew);
-    UP(a_rowptr, hp.a_rowptr);
-    UP(a_col, hp.a_col);
-    UP(a_val, hp.a_val);
-    UP(sell_col, hp.sell_col);
-    UP(sell_len, hp.sell_len);
-    UP(sell_off, hp.sell_off);
-    UP(sell_row, hp.sell_row);
-    UP(sell_val, hp.sell_val);
     if (hp.kkt_on_device) {
-        // the KKT factorization on the device, from the A^T slices and w/D just uploaded
-        cadmm::KktInputs ki;
-        ki.m = hp.m;
-        ki.nslices = (int)hp.sell_len.size();
-        ki.sell_col = P.sell_col;
-        ki.sell_off = P.sell_off;
-        ki.sell_row = P.sell_row;
-        ki.sell_val = P.sell_val;
-        ki.wdinv = P.wdinv;
-        ki.slot_len_h.swap(hp.slot_len);
-        cadmm::KktOutputs ko;
-        const size_t mm = (size_t)hp.m * hp.m;
-        double *L = nullptr, *Li = nullptr, *LiT = nullptr, *Mi = nullptr;
-        if ((rc = h->dalloc(&L, mm)) || (rc = h->dalloc(&Li, mm)) || (rc = h->dalloc(&LiT, mm)) ||
-            (rc = h->dalloc(&Mi, mm)))
-            return rc;
-        ko.L = L;
-        ko.Linv = Li;
-        ko.LinvT = LiT;
-        ko.Minv = Mi;
         std::string kerr;
-        if ((rc = cadmm::device_kkt(ki, ko, kerr))) return set_err(rc, kerr);
+        h->setup_ms[kSetupUpload] += ms_since(clk);
+        if ((rc = cadmm::device_kkt_wait(kkt_run, ko, kerr))) return set_err(rc, kerr);
+        h->setup_ms[kSetupKkt] = ms_since(clk);
         P.kkt_tri = ko.kappa1 > cadmm::kKktTriCond ? 1 : 0;
-        P.Minv = Mi;
-        P.Linv = Li;
-        P.LinvT = LiT;
+        P.Minv = ko.Minv;
+        P.Linv = ko.Linv;
+        P.LinvT = ko.LinvT;
         if (P.kkt_tri && (rc = h->dalloc(&P.z1, (size_t)std::max(1, hp.m)))) return rc;
     } else {
         P.kkt_tri = hp.kkt_tri ? 1 : 0;
@@ -720,6 +764,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
         P.vstore = vs;
         h->vstore_elems = hp.voff[hp.p];
     }
+    h->setup_ms[kSetupUpload] += ms_since(clk);
     CK(cudaMallocHost(&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
@@ -733,6 +778,7 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out) {
         return rc;
     }
     CK(cudaDeviceSynchronize());
+    h->setup_ms[kSetupFinish] = ms_since(clk);
     return SDP_OK;
 }
 
@@ -750,13 +796,14 @@ int sdp_setup(int n, int m, const long long* A_ptr, const int* A_row, const int*
         *out = nullptr;
         int rc = check_opts(opts);
         if (rc) return rc;
+        SetupClock::time_point clk = SetupClock::now();
         HostProblem hp;
         std::string err;
         rc = cadmm::build_host_problem(n, m, A_ptr, A_row, A_col, A_val, b, C_nnz, C_row, C_col, C_val,
                                        pat_nnz, pat_row, pat_col, p, clique_ptr, clique_vtx, nullptr, hp, err,
                                        (opts->flags & SDP_FLAG_HOST_KKT) == 0);
         if (rc) return set_err(rc, err);
-        return create_handle(hp, opts, out);
+        return create_handle(hp, opts, out, ms_since(clk));
     } catch (const std::bad_alloc&) {
         return set_err(SDP_ERR_ARG, "host out of memory");
     } catch (...) {
@@ -771,6 +818,7 @@ int sdp_setup_conic(const sdp_problem* pr, const sdp_cones* cones, const admm_op
         if (!pr) return set_err(SDP_ERR_ARG, "problem is NULL");
         int rc = check_opts(opts);
         if (rc) return rc;
+        SetupClock::time_point clk = SetupClock::now();
         HostProblem hp;
         std::string err;
         rc = cadmm::build_host_problem(pr->n, pr->m, pr->A_ptr, pr->A_row, pr->A_col, pr->A_val, pr->b,
@@ -778,7 +826,7 @@ int sdp_setup_conic(const sdp_problem* pr, const sdp_cones* cones, const admm_op
                                        pr->pat_col, pr->p, pr->clique_ptr, pr->clique_vtx, cones, hp, err,
                                        (opts->flags & SDP_FLAG_HOST_KKT) == 0);
         if (rc) return set_err(rc, err);
-        return create_handle(hp, opts, out);
+        return create_handle(hp, opts, out, ms_since(clk));
     } catch (const std::bad_alloc&) {
         return set_err(SDP_ERR_ARG, "host out of memory");
     } catch (...) {
@@ -820,11 +868,12 @@ int sdp_setup_batch(int count, const sdp_problem* problems, const admm_opts* opt
         if (count < 1 || !problems) return set_err(SDP_ERR_ARG, "count must be >= 1 and problems non-NULL");
         int rc = check_opts(opts);
         if (rc) return rc;
+        SetupClock::time_point clk = SetupClock::now();
         HostProblem hp;
         std::string err;
         rc = cadmm::build_host_problem_batch(count, problems, hp, err);
         if (rc) return set_err(rc, err);
-        return create_handle(hp, opts, out);
+        return create_handle(hp, opts, out, ms_since(clk));
     } catch (const std::bad_alloc&) {
         return set_err(SDP_ERR_ARG, "host out of memory");
     } catch (...) {
@@ -1305,6 +1354,16 @@ const char* sdp_phase_name(sdp_handle h, int i) {
     if (!h) return nullptr;
     return cadmm::phase_name(h->opts.form, h->ninst > 1, h->P.ncs > 0, h->P.kkt_tri != 0, i);
 }
+
+int sdp_setup_times(sdp_handle h, double* ms_out, int max_out) {
+    if (!h) return set_err(SDP_ERR_ARG, "handle is NULL");
+    if (max_out < 0 || (max_out > 0 && !ms_out)) return set_err(SDP_ERR_ARG, "ms_out is NULL");
+    const int k = std::min<int>(max_out, kSetupStages);
+    for (int i = 0; i < k; ++i) ms_out[i] = h->setup_ms[i];
+    return kSetupStages;
+}
+
+const char* sdp_setup_stage_name(int i) { return (i >= 0 && i < kSetupStages) ? kSetupStageName[i] : nullptr; }
 
 void sdp_free(sdp_handle h) { delete h; }
 

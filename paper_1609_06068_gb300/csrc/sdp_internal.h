@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/chordal_admm.h"
@@ -24,6 +26,26 @@ struct Ctrl {
 };
 
 // Host-side result of setup: everything the device needs, in upload order.
+// A vector whose resize leaves new elements uninitialized, for large arrays that are filled in
+// parallel right after (the first write, not a serial zero fill, then touches each page).
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = DefaultInitAlloc<U>;
+    };
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) {}
+    template <class U, class... Args>
+    void construct(U* p, Args&&... args) {
+        if constexpr (sizeof...(Args) == 0) ::new ((void*)p) U;
+        else ::new ((void*)p) U(std::forward<Args>(args)...);
+    }
+};
+template <class T>
+using uvector = std::vector<T, DefaultInitAlloc<T>>;
+
 struct HostProblem {
     int n = 0, m = 0, p = 0, smax = 0;
     int nEL = 0;        // |E_L|
@@ -41,8 +63,9 @@ struct HostProblem {
     std::vector<int> heavy;                     // E_L entries covered by more than kHeavyCount cliques
     std::vector<double> D, dinv, wdinv, c, b;   // D, 1/D, w/D, c on E_L; b
     std::vector<unsigned char> ew;              // [nEL] weight 1 (diagonal) or 2
-    std::vector<int> a_rowptr, a_col;           // CSR of A (rows = constraints)
-    std::vector<double> a_val;
+    std::vector<int> a_rowptr;                  // CSR of A (rows = constraints)
+    uvector<int> a_col;
+    uvector<double> a_val;
     std::vector<int> c_colptr;                  // CSC of A (columns = E_L entries); host only
     std::vector<unsigned short> c_row;
     std::vector<double> c_val;
@@ -61,9 +84,11 @@ struct HostProblem {
     double kkt_cond = 1.0;                      // kappa_1(A D^-1 A^T) (largest over a batch)
     bool kkt_tri = false;                       // affine step by the two triangular factors
     // The factorization is left to the device (M, L, L^-1, M^-1 and kappa then come from
-    // device_kkt); slot_len[32 s + t] is the length of the column in slot t of A^T slice s.
+    // device_kkt_launch), and so is the fill of the A^T slices: sell_row and sell_val stay empty
+    // here, slot_len[32 s + t] is the length of the column in slot t of slice s and col_slot[e]
+    // the slot (32 s + t) of column e.
     bool kkt_on_device = false;
-    std::vector<int> slot_len;
+    std::vector<int> slot_len, col_slot;
     // Batches: instances are concatenated (block-diagonal problem); ranges are [q] .. [q+1].
     int ninst = 1;
     std::vector<int> inst_vtx, inst_cl, inst_e, inst_pos, inst_row, inst_sl;   // vertices, cliques,
@@ -104,20 +129,31 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                        bool kkt_device = false);
 
 // ---------------------------------------------------------------- KKT factorization on the device
-// (kkt.cu) for single problems with kKktDeviceMinM <= m <= kKktDeviceMaxM and A^T columns of at
-// most 4096 nonzeros: M = A D^-1 A^T from the sliced ELL of A^T, L, L^-1, M^-1 and kappa_1(M).
+// (kkt.cu) for single problems with kKktDeviceMinM <= m <= kKktDeviceMaxM: the A^T slices from
+// the CSR of A, M = A D^-1 A^T from them, L, L^-1, M^-1 and kappa_1(M).
 constexpr int kKktDeviceMinM = 64;
 constexpr int kKktDeviceMaxM = 4096;
 bool device_kkt_fits(int m, int max_col_len);
 struct KktInputs {
     int m = 0, nslices = 0;
     const int* sell_col = nullptr;
+    const int* sell_len = nullptr;
     const long long* sell_off = nullptr;
     const unsigned short* sell_row = nullptr;
     const double* sell_val = nullptr;
     const double* wdinv = nullptr;
     std::vector<int> slot_len_h;
-    cudaStream_t stream = nullptr;
+    // When ell_row is set, the slices are first filled here from the CSR of A (rows ascending
+    // within every column, padding 0) into ell_row / ell_val, which sell_row / sell_val name.
+    const int* a_rowptr = nullptr;
+    const int* a_col = nullptr;
+    const double* a_val = nullptr;
+    long long nnz = 0;
+    int nEL = 0;
+    const int* col_slot = nullptr;    // [nEL] slot 32 s + t of column e
+    unsigned short* ell_row = nullptr;
+    double* ell_val = nullptr;
+    long long ell_size = 0;           // sell_off[nslices]
 };
 struct KktOutputs {
     double* L = nullptr;       // m x m: M, then its Cholesky factor in the lower triangle
@@ -126,8 +162,22 @@ struct KktOutputs {
     double* Minv = nullptr;    // m x m row-major, symmetric
     double kappa1 = 0.0;
 };
-// SDP_OK, SDP_ERR_NOT_PD (A numerically rank-deficient) or SDP_ERR_CUDA; synchronizes the stream.
-int device_kkt(const KktInputs& in, KktOutputs& out, std::string& err);
+// The factorization runs on a stream of its own, so that the caller can go on uploading while it
+// runs: device_kkt_launch enqueues it (SDP_OK or SDP_ERR_CUDA), device_kkt_wait waits for it and
+// fills kappa1 (SDP_OK, SDP_ERR_NOT_PD when A is numerically rank-deficient, or SDP_ERR_CUDA).
+// The outputs must outlive the run; KktRun's destructor waits for the stream before it frees the
+// scratch, so a caller that gives up between the two calls leaves no work in flight.
+struct KktRun {
+    cudaStream_t st = nullptr;
+    int m = 0;
+    double* d_rows = nullptr;   // largest absolute row sums of M and M^-1
+    int* d_notpd = nullptr;     // set by a pivot at or below 1e-12 of its diagonal entry
+    std::vector<void*> bufs;
+    void release();
+    ~KktRun() { release(); }
+};
+int device_kkt_launch(const KktInputs& in, const KktOutputs& out, KktRun& run, std::string& err);
+int device_kkt_wait(KktRun& run, KktOutputs& out, std::string& err);
 
 // ---------------------------------------------------------------- kernel launch parameters
 

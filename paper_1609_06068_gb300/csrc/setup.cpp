@@ -46,6 +46,21 @@ struct EntryIndex {
         if (it == hi || *it != r) return -1;
         return (long long)(it - rows.data());
     }
+    // The same, for a row r of column c known to come after position `after` (an entry of the
+    // same column with a smaller row): galloping forward from there, so that a run of lookups in
+    // E_L order costs about the gaps between them.
+    long long find_after(long long r, long long c, long long after) const {
+        const int* base = rows.data();
+        const long long end = col_start[c + 1];
+        long long lo = after + 1, step = 1;
+        while (lo + step - 1 < end && base[lo + step - 1] < r) {
+            lo += step;
+            step <<= 1;
+        }
+        const int* it = std::lower_bound(base + lo, base + std::min(end, lo + step), (int)r);
+        if (it == base + end || *it != r) return -1;
+        return (long long)(it - base);
+    }
 };
 
 // Set on the worker threads of a batch build: each problem is then built on one thread.
@@ -292,8 +307,21 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
                 }
         }
     }
-    std::vector<long long> keys(pos_key);
-    std::sort(keys.begin(), keys.end());
+    // keys in increasing order by two counting passes (row, then column: a stable LSD radix
+    // sort in base n), then duplicates dropped
+    std::vector<long long> keys(pos_key.size());
+    {
+        std::vector<long long> tmp(pos_key.size());
+        std::vector<long long> cnt((size_t)n + 1);
+        auto pass = [&](const std::vector<long long>& in, std::vector<long long>& out, bool by_col) {
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (long long k : in) cnt[(by_col ? k / n : k % n) + 1]++;
+            for (int d = 0; d < n; ++d) cnt[d + 1] += cnt[d];
+            for (long long k : in) out[cnt[by_col ? k / n : k % n]++] = k;
+        };
+        pass(pos_key, tmp, false);
+        pass(tmp, keys, true);
+    }
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
     if ((long long)keys.size() + nc >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
     const int nEL_mat = (int)keys.size();
@@ -400,70 +428,129 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     hp.b.assign(b, b + m);
 
     // ---- A on E_L: CSR by constraint (duplicates merged), then CSC by entry. Constraints are
-    // converted in parallel; the first failing constraint (lowest index) decides the error.
-    std::vector<std::vector<std::pair<int, double>>> rows(m);
-    std::vector<int> row_err(m, SDP_OK);
-    std::vector<std::string> row_msg(m);
-    parallel_for(m, [&](int i) {
-        std::vector<std::pair<int, double>>& row = rows[i];
-        row.reserve((size_t)(A_ptr[i + 1] - A_ptr[i]));
-        for (long long t = A_ptr[i]; t < A_ptr[i + 1]; ++t) {
-            const long long r = A_row[t], cc = A_col[t];
-            if (r < 0 || r >= n || cc < 0 || cc >= n) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A index out of range"; return; }
-            if (r < cc) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A must be given as lower coordinates (row >= col)"; return; }
-            const long long e = index.find(r, cc);
-            if (e < 0) {
-                if (A_val[t] == 0.0) continue;
-                row_err[i] = SDP_ERR_CLIQUE;
-                row_msg[i] = "a nonzero of A is not covered by the cliques";
-                return;
-            }
-            row.emplace_back((int)e, A_val[t]);
-        }
-        if (nc > 0)
-            for (long long t = cones->A_ptr[i]; t < cones->A_ptr[i + 1]; ++t)
-                row.emplace_back(nEL_mat + cones->A_var[t], cones->A_val[t]);
-        auto by_entry = [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; };
-        if (!std::is_sorted(row.begin(), row.end(), by_entry)) std::sort(row.begin(), row.end(), by_entry);
-        size_t w = 0;
-        for (size_t t = 0; t < row.size(); ++t) {
-            if (w > 0 && row[w - 1].first == row[t].first) row[w - 1].second += row[t].second;
-            else row[w++] = row[t];
-        }
-        size_t k = 0;
-        for (size_t t = 0; t < w; ++t)
-            if (row[t].second != 0.0) row[k++] = row[t];
-        row.resize(k);
-    });
-    for (int i = 0; i < m; ++i)
-        if (row_err[i] != SDP_OK) return fail(err, row_err[i], row_msg[i]);
-    hp.a_rowptr.assign(m + 1, 0);
+    // converted in parallel tasks over contiguous ranges of constraints, each written straight
+    // into the CSR arrays at its input offset (an upper bound: merging and dropping zeros only
+    // shorten a constraint), then the constraints that shrank are moved down. Entries that come
+    // in increasing E_L order (the usual case) are written as they are found; otherwise the
+    // constraint is put in order by a stable LSD radix sort on 11-bit digits (std::stable_sort
+    // for short ones), so duplicates add up in input order. The first failing constraint (lowest
+    // index) decides the error.
     {
-        long long total = 0;
-        for (int i = 0; i < m; ++i) total += (long long)rows[i].size();
-        if (total >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "nnz(A) >= 2^31");
-        hp.a_col.resize(total);
-        hp.a_val.resize(total);
-        for (int i = 0; i < m; ++i) hp.a_rowptr[i + 1] = hp.a_rowptr[i] + (int)rows[i].size();
-        parallel_for(m, [&](int i) {
-            size_t q = hp.a_rowptr[i];
-            for (const auto& pr : rows[i]) {
-                hp.a_col[q] = pr.first;
-                hp.a_val[q] = pr.second;
-                ++q;
+        std::vector<long long> in_off(m + 1, 0);
+        for (int i = 0; i < m; ++i)
+            in_off[i + 1] = in_off[i] + (A_ptr[i + 1] - A_ptr[i]) + (nc > 0 ? cones->A_ptr[i + 1] - cones->A_ptr[i] : 0);
+        if (in_off[m] >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "nnz(A) >= 2^31");
+        hp.a_col.resize(in_off[m]);
+        hp.a_val.resize(in_off[m]);
+        const int ntask = std::max(1, std::min(m, 4 * worker_count()));
+        std::vector<int> row_len(m, 0), row_err(m, SDP_OK);
+        std::vector<std::string> row_msg(m);
+        int ebits = 1;
+        while (ebits < 31 && (1LL << ebits) < (long long)nEL) ++ebits;
+        parallel_for(ntask, [&](int tk) {
+            const int i0 = (int)((long long)m * tk / ntask), i1 = (int)((long long)m * (tk + 1) / ntask);
+            std::vector<std::pair<int, double>> kp, kp2;       // an out-of-order constraint's entries
+            std::vector<int> hist(2048);
+            auto by_entry = [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; };
+            for (int i = i0; i < i1; ++i) {
+                int* oc = hp.a_col.data() + in_off[i];
+                double* ov = hp.a_val.data() + in_off[i];
+                int w = 0;                                     // entries written
+                bool ordered = true;                           // so far strictly increasing
+                int last = -1;
+                kp.clear();
+                auto put = [&](int e, double v) {
+                    if (ordered && e > last) {
+                        last = e;
+                        if (v != 0.0) {
+                            oc[w] = e;
+                            ov[w++] = v;
+                        }
+                        return;
+                    }
+                    if (ordered) {                             // first entry out of order: switch
+                        ordered = false;
+                        for (int q = 0; q < w; ++q) kp.emplace_back(oc[q], ov[q]);
+                    }
+                    kp.emplace_back(e, v);
+                };
+                long long prev_r = -1, prev_c = -1, prev_e = -1;     // last entry found
+                for (long long t = A_ptr[i]; t < A_ptr[i + 1]; ++t) {
+                    const long long r = A_row[t], cc = A_col[t];
+                    if (r < 0 || r >= n || cc < 0 || cc >= n) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A index out of range"; return; }
+                    if (r < cc) { row_err[i] = SDP_ERR_ARG; row_msg[i] = "A must be given as lower coordinates (row >= col)"; return; }
+                    const long long e = (cc == prev_c && r > prev_r) ? index.find_after(r, cc, prev_e) : index.find(r, cc);
+                    if (e < 0) {
+                        if (A_val[t] == 0.0) continue;
+                        row_err[i] = SDP_ERR_CLIQUE;
+                        row_msg[i] = "a nonzero of A is not covered by the cliques";
+                        return;
+                    }
+                    prev_r = r;
+                    prev_c = cc;
+                    prev_e = e;
+                    put((int)e, A_val[t]);
+                }
+                if (nc > 0)
+                    for (long long t = cones->A_ptr[i]; t < cones->A_ptr[i + 1]; ++t)
+                        put(nEL_mat + cones->A_var[t], cones->A_val[t]);
+                if (!ordered) {
+                    const size_t cnt = kp.size();
+                    if (cnt <= 512) {
+                        std::stable_sort(kp.begin(), kp.end(), by_entry);
+                    } else {
+                        kp2.resize(cnt);
+                        for (int shift = 0; shift < ebits; shift += 11) {
+                            std::fill(hist.begin(), hist.end(), 0);
+                            for (size_t q = 0; q < cnt; ++q) hist[(kp[q].first >> shift) & 2047]++;
+                            int sum = 0;
+                            for (int d = 0; d < 2048; ++d) {
+                                const int c = hist[d];
+                                hist[d] = sum;
+                                sum += c;
+                            }
+                            for (size_t q = 0; q < cnt; ++q) kp2[hist[(kp[q].first >> shift) & 2047]++] = kp[q];
+                            kp.swap(kp2);
+                        }
+                    }
+                    // merge duplicates, drop zeros
+                    w = 0;
+                    for (size_t t = 0; t < cnt;) {
+                        const int e = kp[t].first;
+                        double v = kp[t].second;
+                        for (++t; t < cnt && kp[t].first == e; ++t) v += kp[t].second;
+                        if (v != 0.0) {
+                            oc[w] = e;
+                            ov[w++] = v;
+                        }
+                    }
+                }
+                row_len[i] = w;
             }
-            std::vector<std::pair<int, double>>().swap(rows[i]);
         });
+        for (int i = 0; i < m; ++i)
+            if (row_err[i] != SDP_OK) return fail(err, row_err[i], row_msg[i]);
+        hp.a_rowptr.assign(m + 1, 0);
+        for (int i = 0; i < m; ++i) hp.a_rowptr[i + 1] = hp.a_rowptr[i] + row_len[i];
+        if (hp.a_rowptr[m] != in_off[m]) {
+            for (int i = 0; i < m; ++i)                        // move down, in order (never upward)
+                if (hp.a_rowptr[i] != in_off[i]) {
+                    std::memmove(hp.a_col.data() + hp.a_rowptr[i], hp.a_col.data() + in_off[i], sizeof(int) * row_len[i]);
+                    std::memmove(hp.a_val.data() + hp.a_rowptr[i], hp.a_val.data() + in_off[i], sizeof(double) * row_len[i]);
+                }
+            hp.a_col.resize(hp.a_rowptr[m]);
+            hp.a_val.resize(hp.a_rowptr[m]);
+        }
     }
     hp.nnz = (long long)hp.a_col.size();
     // CSC by a parallel transpose over column ranges: every row of the CSR lists its columns in
     // increasing order, so the entries of row i in columns [e0, e1) are one contiguous run found
     // by binary search. Each worker owns a range of columns and walks the rows in order, so every
     // column lists its rows in increasing order (as a serial transpose would) and each worker
-    // writes only its own part of the output.
+    // writes only its own part of the output. When the device builds the KKT factorization it
+    // also fills the A^T slices from the CSR (device_kkt_launch), and the host only counts the
+    // columns.
     hp.c_colptr.assign(nEL + 1, 0);
-    hp.c_row.resize(hp.nnz);
-    hp.c_val.resize(hp.nnz);
     {
         const int nt = std::max(1, std::min(4 * worker_count(), nEL / 256 + 1));
         auto cols_of = [&](int t, int& e0, int& e1) {
@@ -486,7 +573,14 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             }
         });
         for (int e = 0; e < nEL; ++e) hp.c_colptr[e + 1] += hp.c_colptr[e];
-        parallel_for(nt, [&](int t) {
+        int max_col = 0;
+        for (int e = 0; e < nEL; ++e) max_col = std::max(max_col, hp.c_colptr[e + 1] - hp.c_colptr[e]);
+        hp.kkt_on_device = kkt_device && m >= kKktDeviceMinM && device_kkt_fits(m, max_col);
+        if (!hp.kkt_on_device) {
+            hp.c_row.resize(hp.nnz);
+            hp.c_val.resize(hp.nnz);
+        }
+        if (!hp.kkt_on_device) parallel_for(nt, [&](int t) {
             int e0, e1;
             cols_of(t, e0, e1);
             std::vector<int> fillp(hp.c_colptr.begin() + e0, hp.c_colptr.begin() + e1);
@@ -503,10 +597,8 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     }
 
     // ---- the KKT factorization: on the device (kkt.cu, after the upload) when the caller allows it
-    // and the problem fits its limits; here otherwise. The device needs each A^T slot's length.
-    int max_col = 0;
-    for (int e = 0; e < nEL; ++e) max_col = std::max(max_col, hp.c_colptr[e + 1] - hp.c_colptr[e]);
-    hp.kkt_on_device = kkt_device && m >= kKktDeviceMinM && device_kkt_fits(m, max_col);
+    // and the problem fits its limits (decided above); here otherwise. The device needs each A^T
+    // slot's length.
     if (!hp.kkt_on_device) {
         // ---- M = A D^-1 A^T on the full symmetric vectors: M_ij = sum_e w_e A_ie A_je / D_e, with
         // w_e = 2 off the diagonal (both (i,j) and (j,i) of the pattern) and 1 on it. Columns are
@@ -645,33 +737,39 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
         }
         hp.sell_off[ns] = off;
         if (off >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "padded nnz(A) >= 2^31");
-        hp.sell_val.assign(off, 0.0);
-        hp.sell_row.assign(off, 0);
-        parallel_for(ns, [&](int sl) {
-            // in storage order (element k of the 32 slots, then k + 1, ...): the writes are
-            // contiguous and the reads are 32 forward streams
-            int beg[32], len[32];
-            for (int t = 0; t < 32; ++t) {
-                const int c = slot_col[32LL * sl + t];
-                beg[t] = c < 0 ? 0 : hp.c_colptr[c];
-                len[t] = c < 0 ? 0 : hp.c_colptr[c + 1] - hp.c_colptr[c];
-            }
-            const long long base = hp.sell_off[sl];
-            for (int k = 0; k < hp.sell_len[sl]; ++k)
-                for (int t = 0; t < 32; ++t)
-                    if (k < len[t]) {
-                        const long long q = base + 32LL * k + t;
-                        hp.sell_val[q] = hp.c_val[beg[t] + k];
-                        hp.sell_row[q] = hp.c_row[beg[t] + k];
-                    }
-        });
-        std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
-        std::vector<unsigned short>().swap(hp.c_row);
-        if (hp.kkt_on_device) {
+        if (!hp.kkt_on_device) {
+            hp.sell_val.assign(off, 0.0);
+            hp.sell_row.assign(off, 0);
+            parallel_for(ns, [&](int sl) {
+                // in storage order (element k of the 32 slots, then k + 1, ...): the writes are
+                // contiguous and the reads are 32 forward streams
+                int beg[32], len[32];
+                for (int t = 0; t < 32; ++t) {
+                    const int c = slot_col[32LL * sl + t];
+                    beg[t] = c < 0 ? 0 : hp.c_colptr[c];
+                    len[t] = c < 0 ? 0 : hp.c_colptr[c + 1] - hp.c_colptr[c];
+                }
+                const long long base = hp.sell_off[sl];
+                for (int k = 0; k < hp.sell_len[sl]; ++k)
+                    for (int t = 0; t < 32; ++t)
+                        if (k < len[t]) {
+                            const long long q = base + 32LL * k + t;
+                            hp.sell_val[q] = hp.c_val[beg[t] + k];
+                            hp.sell_row[q] = hp.c_row[beg[t] + k];
+                        }
+            });
+            std::vector<double>().swap(hp.c_val);       // the device reads the sliced form only
+            std::vector<unsigned short>().swap(hp.c_row);
+        } else {
+            // the device fills the slices from the CSR: it needs each slot's length and each
+            // column's slot
             hp.slot_len.assign(32LL * ns, 0);
+            hp.col_slot.assign(nEL, 0);
             for (long long q = 0; q < 32LL * ns; ++q) {
                 const int c = slot_col[q];
-                hp.slot_len[q] = c < 0 ? 0 : hp.c_colptr[c + 1] - hp.c_colptr[c];
+                if (c < 0) continue;
+                hp.slot_len[q] = hp.c_colptr[c + 1] - hp.c_colptr[c];
+                hp.col_slot[c] = (int)q;
             }
         }
     }

@@ -329,3 +329,34 @@ def near_dependent_block_arrow(l=4, d=3, h=2, m=8, delta=1e-4, seed=17) -> dict:
     C = Z + sum(y * A for y, A in zip(y0, As))
     C[P & (C == 0)] = 1e-3
     return problem_from_dense(C, As, b, block_arrow_cliques(l, d, h))
+
+
+def messy_constraints(arrs: dict, seed=3, split=0.3) -> dict:
+    """The same problem with A given the untidy way a caller may give it: every constraint's
+    entries shuffled, a share of them split into two halves (duplicates that add back exactly),
+    explicit zeros added on the diagonal, and a pair +x, -x added on a diagonal position the
+    constraint does not use (a duplicate that cancels). The merged CSR is then bit for bit that
+    of the tidy problem."""
+    rng = np.random.default_rng(seed)
+    ptr, rows, cols, vals = (np.asarray(arrs[k]) for k in ("A_ptr", "A_row", "A_col", "A_val"))
+    verts = np.unique(np.concatenate([np.asarray(c) for c in arrs["cliques"]]))
+    out_r, out_c, out_v, out_p = [], [], [], [0]
+    for i in range(len(ptr) - 1):
+        r, c, v = rows[ptr[i]:ptr[i + 1]], cols[ptr[i]:ptr[i + 1]], vals[ptr[i]:ptr[i + 1]]
+        halves = rng.random(len(v)) < split
+        rr = np.concatenate([r, r[halves]])
+        cc = np.concatenate([c, c[halves]])
+        vv = np.concatenate([np.where(halves, v / 2, v), v[halves] / 2])
+        used = set(zip(r.tolist(), c.tolist()))
+        free = [int(d) for d in verts if (int(d), int(d)) not in used]
+        zeros = rng.choice(verts, size=min(3, len(verts)), replace=False)
+        rr = np.concatenate([rr, zeros]); cc = np.concatenate([cc, zeros]); vv = np.concatenate([vv, np.zeros(len(zeros))])
+        if free:
+            d = free[int(rng.integers(len(free)))]
+            x = float(rng.standard_normal())
+            rr = np.concatenate([rr, [d, d]]); cc = np.concatenate([cc, [d, d]]); vv = np.concatenate([vv, [x, -x]])
+        perm = rng.permutation(len(vv))
+        out_r.append(rr[perm]); out_c.append(cc[perm]); out_v.append(vv[perm])
+        out_p.append(out_p[-1] + len(vv))
+    return dict(arrs, A_ptr=np.asarray(out_p, np.int64), A_row=np.concatenate(out_r).astype(np.int32),
+                A_col=np.concatenate(out_c).astype(np.int32), A_val=np.concatenate(out_v).astype(np.float64))

@@ -322,3 +322,18 @@ def test_plan_reports_host_errors(lib):
     with pytest.raises(cadmm.SDPError) as exc:
         cadmm.sdp_plan(dict(arrs, cliques=[np.array([1, 0], np.int32)]))
     assert exc.value.code == cadmm.SDP_ERR_CLIQUE
+
+
+@pytest.mark.parametrize("case", ["short", "long"])
+def test_plan_merges_untidy_constraints(lib, case):
+    """Shuffled entries, split duplicates, explicit zeros and a cancelling pair leave the host
+    build's count of stored nonzeros of A unchanged. "long" has constraints of more than 512
+    entries, which take the radix-sort path; "short" the comparison sort."""
+    if case == "short":
+        arrs = sdp_cases.random_block_arrow(l=4, d=3, h=2, m=6, seed=2)
+    else:
+        arrs = sdp_cases.random_block_arrow(l=30, d=5, h=4, m=8, seed=4, density=0.6)
+        assert np.min(np.diff(arrs["A_ptr"])) > 512
+    tidy = cadmm.sdp_plan(arrs)
+    messy = cadmm.sdp_plan(sdp_cases.messy_constraints(arrs))
+    assert messy == tidy

@@ -118,3 +118,21 @@ def test_device_kkt_ill_conditioned_takes_factors(form):
         x = sdp.from_lower(rows, cols, dev.state()["x"])
         rhs = sdp.b if form == "primal" else -sdp.b / 1.0
         assert np.max(np.abs(sdp.A @ x - rhs)) <= 1e-10 * max(1.0, np.max(np.abs(rhs)))
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_untidy_constraints_give_identical_iterates(flags):
+    """Shuffled entries, split duplicates, explicit zeros and a cancelling pair in A: after the
+    host build merges them (and, without SDP_FLAG_HOST_KKT, the device builds the A^T slices
+    and the factorization from that CSR), the iterates are bit for bit those of the tidy input."""
+    torch, cadmm = require_gpu()
+    arrs = sdp_cases.random_block_arrow(l=30, d=5, h=4, m=70, seed=9, density=0.6)
+    messy = sdp_cases.messy_constraints(arrs, seed=5)
+    fl = flags * cadmm.SDP_FLAG_HOST_KKT
+    with setup_handle(cadmm, arrs, form="dual", rho=0.5, tol=0.0, flags=fl) as a, \
+            setup_handle(cadmm, messy, form="dual", rho=0.5, tol=0.0, flags=fl) as b:
+        a.iterate(15)
+        b.iterate(15)
+        sa, sb = a.state(), b.state()
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), key
