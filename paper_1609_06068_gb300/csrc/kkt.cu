@@ -163,11 +163,9 @@ __global__ void __launch_bounds__(kMThreads) k_kkt_partial(const int* s_lo, int 
 // The same sums with whole slices staged: slice s's 32 interleaved columns are copied to shared
 // memory with cp.async (values 8 bytes and row pairs 4 bytes at a time, each element row k padded
 // to 33 values and 34 rows so that a lane per k reads distinct banks) while the previous slice is
-// summed, two buffers deep. The CTA takes one column at a time, its products (k1, k2), k2 <= k1,
-// numbered row by row (f = k1 (k1 + 1) / 2 + k2) and dealt to the threads in turn, so every FP64
-// instruction has all its lanes busy; the products of a column go to distinct entries, and one
-// barrier per column keeps columns apart. The column's values times w/D are formed one column
-// ahead.
+// summed, two buffers deep. M row r belongs to warp r % 8: a warp takes, column by column, the
+// entries k1 whose row it owns (found 32 at a time with a ballot), its lanes the k2 <= k1, so the
+// warps never write the same entry and need no barrier between columns.
 constexpr int kValPitch = 33, kRowPitch = 34;      // per element row k of a staged slice
 struct SliceBuf {
     double* val;            // [Lcap][kValPitch]
@@ -223,15 +221,6 @@ __device__ __forceinline__ void stage_slice(const SliceBuf& b, int s, int len_s,
     }
 }
 
-// (k1, k2) of product number f of a column's triangle
-__device__ __forceinline__ void tri_pair(int f, int& k1, int& k2) {
-    int r = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
-    while (r > 0 && r * (r + 1) / 2 > f) --r;
-    while ((r + 1) * (r + 2) / 2 <= f) ++r;
-    k1 = r;
-    k2 = f - r * (r + 1) / 2;
-}
-
 template <bool kShared>
 __global__ void __launch_bounds__(kMThreads) k_kkt_partial_slices(const int* s_lo, int G, const int* band_lo,
                                                                   const int* slot_len, const double* slot_wd,
@@ -244,17 +233,16 @@ __global__ void __launch_bounds__(kMThreads) k_kkt_partial_slices(const int* s_l
     const int g = kShared ? blockIdx.x : blockIdx.x % G;
     const int band = kShared ? 0 : blockIdx.x / G;
     double* Ms = reinterpret_cast<double*>(smraw);
-    double* wcol = reinterpret_cast<double*>(smraw + (kShared ? (size_t)P * sizeof(double) : 0));   // [2][Lcap]
-    unsigned char* bufs = reinterpret_cast<unsigned char*>(wcol + 2 * (size_t)Lcap);
+    unsigned char* bufs = smraw + (kShared ? (size_t)P * sizeof(double) : 0);
     const size_t bb = slice_buf_bytes(Lcap);
     double* Mp = kShared ? Ms : part + (size_t)g * P;
     if (kShared)
         for (long long q = threadIdx.x; q < P; q += blockDim.x) Ms[q] = 0.0;
     const int r0 = kShared ? 0 : band_lo[band], r1 = kShared ? m : band_lo[band + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sA = s_lo[g], sB = s_lo[g + 1];
     if (sA < sB) stage_slice(slice_buf_at(bufs, Lcap), sA, sell_len[sA], sell_off[sA], slot_len, slot_wd, sell_row, sell_val);
     cp_async_commit();
-    int wsel = 0;                                        // wcol buffer of the next column
     for (int s = sA; s < sB; ++s) {
         if (s + 1 < sB)
             stage_slice(slice_buf_at(bufs + ((s + 1 - sA) & 1) * bb, Lcap), s + 1, sell_len[s + 1], sell_off[s + 1],
@@ -263,23 +251,12 @@ __global__ void __launch_bounds__(kMThreads) k_kkt_partial_slices(const int* s_l
         cp_async_wait<1>();                          // slice s has landed (s + 1 may be in flight)
         __syncthreads();
         const SliceBuf b = slice_buf_at(bufs + ((s - sA) & 1) * bb, Lcap);
-        // w/D times the values of the slice's first non-empty column
-        int t = 0;
-        while (t < 32 && b.len[t] == 0) ++t;
-        if (t < 32)
-            for (int k = threadIdx.x; k < b.len[t]; k += blockDim.x) wcol[wsel * Lcap + k] = b.wd[t] * b.val[k * kValPitch + t];
-        while (t < 32) {
+        for (int t = 0; t < 32; ++t) {
             const int len = b.len[t];
+            if (len == 0) continue;
+            const double wd = b.wd[t];
             const unsigned short* rw = b.row + t;        // element k at rw[k * kRowPitch]
             const double* vl = b.val + t;                // element k at vl[k * kValPitch]
-            const double* wv = wcol + wsel * Lcap;
-            int tn = t + 1;                              // the next non-empty column of the slice
-            while (tn < 32 && b.len[tn] == 0) ++tn;
-            __syncthreads();                             // wcol of column t is complete; the previous column is done
-            wsel ^= 1;
-            if (tn < 32)
-                for (int k = threadIdx.x; k < b.len[tn]; k += blockDim.x)
-                    wcol[wsel * Lcap + k] = b.wd[tn] * b.val[k * kValPitch + tn];
             int p0 = 0, p1 = len;
             if (!kShared) {
                 int lo = 0, hi = len;                    // first k with row >= r0
@@ -289,31 +266,28 @@ __global__ void __launch_bounds__(kMThreads) k_kkt_partial_slices(const int* s_l
                 while (lo < hi) { const int mid = (lo + hi) >> 1; if ((int)rw[mid * kRowPitch] < r1) lo = mid + 1; else hi = mid; }
                 p1 = lo;
             }
-            // products f in [F(p0), F(p1)): k1 in [p0, p1), k2 <= k1; four at a time per thread,
-            // whose entries differ, so that their read-modify-writes can all be in flight
-            const int f0 = p0 * (p0 + 1) / 2, f1 = p1 * (p1 + 1) / 2;
-            for (int fb = f0 + 4 * (int)threadIdx.x; fb < f1; fb += 4 * (int)blockDim.x) {
-                double* at[4];
-                double pa[4], pb[4], cur[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    at[u] = nullptr;
-                    pa[u] = pb[u] = 0.0;
-                    if (fb + u < f1) {
-                        int k1, k2;
-                        tri_pair(fb + u, k1, k2);
-                        at[u] = Mp + tri_off(rw[k1 * kRowPitch]) + rw[k2 * kRowPitch];
-                        pa[u] = wv[k1];
-                        pb[u] = vl[k2 * kValPitch];
+            for (int kb = p0; kb < p1; kb += 32) {
+                const int kl = kb + lane;
+                const bool own = kl < p1 && (rw[kl * kRowPitch] & (kWarps - 1)) == warp;
+                unsigned mask = __ballot_sync(0xffffffffu, own);
+                while (mask) {
+                    const int k1 = kb + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const double v1 = wd * vl[k1 * kValPitch];
+                    double* rowp = Mp + tri_off(rw[k1 * kRowPitch]);
+                    int k2 = lane;
+                    for (; k2 + 32 <= k1; k2 += 64) {
+                        const int c0 = rw[k2 * kRowPitch], c1 = rw[(k2 + 32) * kRowPitch];
+                        const double a0 = rowp[c0], a1 = rowp[c1];
+                        rowp[c0] = fma(v1, vl[k2 * kValPitch], a0);
+                        rowp[c1] = fma(v1, vl[(k2 + 32) * kValPitch], a1);
+                    }
+                    if (k2 <= k1) {
+                        const int c0 = rw[k2 * kRowPitch];
+                        rowp[c0] = fma(v1, vl[k2 * kValPitch], rowp[c0]);
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) cur[u] = at[u] ? *at[u] : 0.0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (at[u]) *at[u] = fma(pa[u], pb[u], cur[u]);
             }
-            t = tn;
         }
         __syncthreads();                             // buffer (s - sA) & 1 is refilled next
     }
@@ -634,7 +608,7 @@ int device_kkt_launch(const KktInputs& in, const KktOutputs& out, KktRun& run, s
     const long long P = (long long)m * (m + 1) / 2;
     int Lcap = 1;
     for (int v : in.slot_len_h) Lcap = std::max(Lcap, v);
-    const size_t slices_bytes = 2 * slice_buf_bytes(Lcap) + 2 * sizeof(double) * Lcap;
+    const size_t slices_bytes = 2 * slice_buf_bytes(Lcap);
     const size_t stage_bytes = (size_t)m * (sizeof(double) + sizeof(int));
     const size_t tri_bytes = (size_t)P * sizeof(double);
     const bool use_shared = tri_bytes + stage_bytes <= (size_t)smem_optin;
