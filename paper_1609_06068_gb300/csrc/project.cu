@@ -186,9 +186,10 @@ __device__ __forceinline__ void rotation(double app, double aqq, double apq, dou
 template <int MODE>
 __device__ __forceinline__ double load_w(const ProjArgs& a, long long off, int pos, double rinv) {
     if (MODE == PROJ_PLAIN) return a.in[off + pos];
-    if (MODE == PROJ_PRIMAL)
-        return __dsub_rn(a.x[a.gather_idx[off + pos]], __dmul_rn(rinv, a.lam[off + pos]));
-    return __dsub_rn(a.v[off + pos], __dmul_rn(rinv, a.lam[off + pos]));
+    // one FP64 instruction (an FP64 instruction issues at one warp instruction per 64 clocks per
+    // SM partition on GB300), and one rounding instead of two
+    if (MODE == PROJ_PRIMAL) return fma(-rinv, a.lam[off + pos], a.x[a.gather_idx[off + pos]]);
+    return fma(-rinv, a.lam[off + pos], a.v[off + pos]);
 }
 
 // Scaling of a block by an exact power of two, 2^-e2 before the eigensolve and 2^e2 after, with
@@ -202,6 +203,36 @@ __device__ __forceinline__ int block_exponent(double wmax) {
 }
 __device__ __forceinline__ double pow2_exact(int k) {       // 2^k for |k| <= 1000, from its exponent bits
     return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// x 2^-e2 rounded to FP32 (to nearest, ties to even), from the bits, with no FP64 instruction:
+// the scaling only moves the exponent, and the rounding takes the top 24 of the 53 significand
+// bits. Values that land below FP32's normal range (under 2^-126 after scaling, while the block's
+// largest entry lands in [1, 2)) become zero; an infinity or a NaN passes through unscaled.
+__device__ __forceinline__ float scaled_to_float(double x, int e2) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0x7ff) return (float)x;
+    const int fe = ex - e2 - 896;                        // FP32 biased exponent after scaling
+    if (ex == 0 || fe <= 0) return __uint_as_float(sign);
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    unsigned bits = sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29);
+    const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ++bits;
+    return __uint_as_float(bits);
+}
+// (double)f 2^e2, exactly, from the bits (zero, subnormal, infinite and NaN inputs, and results
+// outside the normal FP64 range, take the arithmetic).
+__device__ __forceinline__ double float_scaled_to_double(float f, int e2) {
+    const unsigned u = __float_as_uint(f);
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
+    const int fe = (int)((u >> 23) & 0xff);
+    const int de = fe - 127 + 1023 + e2;
+    if (fe == 0 || fe == 0xff || de <= 0 || de >= 0x7ff) return (double)f * pow2_exact(e2);
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)de << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
 }
 
 // Batches: true when clique blk belongs to a problem that has stopped, so the CTA must return.
@@ -854,10 +885,12 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 // ---------------------------------------------------------------------------------------------
 // FP32, padded order N <= 32, one CTA of four warps per clique, for launches with few cliques
 // (fewer than the GPU holds warps), where a projection's time is the length of its dependent
-// chain rather than its operation count. The whole CTA loads W, forms G = B V_prev and rebuilds
-// the projection; the Jacobi sweeps run in warp 0 alone, lane c holding column c of G (rows
-// 0..31) in registers. A round is then 32 shuffles, a Gram entry, the 2x2 rotation and the column
-// update, with no barrier and no shared-memory exchange (k_project_os spends both on every round).
+// chain rather than its operation count. The whole CTA loads W, forms G = B V_prev, runs the
+// Jacobi sweeps and rebuilds the projection. In the sweeps lane c of every warp holds column c of
+// G, warp w its rows 8w .. 8w + 7, in registers: a round is 8 shuffles and 8 multiply-adds of a
+// partial Gram entry per warp, one barrier to add the four partials, the 2x2 rotation and an
+// 8-row column update (with all 32 rows in one warp, the 32 shuffles of a round were most of its
+// time).
 //
 // The method is k_project_ow's (one-sided Jacobi on G = B V, B = W + sigma I, sigma = 2 ||W||_F,
 // V never formed: v_j = g_j / mu_j, lambda_j = mu_j - sigma with mu_j = ||g_j||), with three
@@ -925,7 +958,8 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
     constexpr int LD = kWSLD;
     __shared__ __align__(16) float Ws[32 * LD];   // W (scaled), later Q = V diag(lambda+)^(1/2)
     __shared__ __align__(16) float Vs[32 * LD];   // previous eigenvectors (warm start)
-    __shared__ __align__(16) float Gs[32 * LD];   // G = B V_prev
+    __shared__ float s_gp[2][4 * 32];              // a round's partial Gram entries, by round parity
+    __shared__ float s_cn[4][32];                  // partial column norms
     __shared__ int s_exp[4];
     __shared__ float s_sq[4];
     __shared__ double red_d[33 * 3];
@@ -980,13 +1014,12 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
     // (a block whose entries are all zero or subnormal is scaled by 2^1000; a block holding an
     // infinity or a NaN goes through unscaled and shows as such in the residuals)
     const int e2 = emax == 0 ? -1000 : emax == 0x7ff ? 0 : min(max(emax - 1023, -1000), 1000);
-    const double down = pow2_exact(-e2), up = pow2_exact(e2);
     float sq = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int cb = w + 4 * k, ra = cb + lane;
         if (cb < s && ra < s) {
-            const float wt = (float)(wv[k] * down);
+            const float wt = scaled_to_float(wv[k], e2);
             Ws[ra * LD + cb] = wt;
             Ws[cb * LD + ra] = wt;
             sq = fmaf(ra == cb ? wt : 2.f * wt, wt, sq);
@@ -997,10 +1030,11 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
     __syncthreads();
     const float sigma = 2.f * sqrtf((s_sq[0] + s_sq[1]) + (s_sq[2] + s_sq[3]));
 
-    // ---- G = B V_prev (warm) by all four warps, warp w rows 8w .. 8w + 7, lane j column j
+    // ---- G = B V_prev (warm) by all four warps, warp w rows 8w .. 8w + 7, lane j column j; the
+    // rows stay in the warp's registers for the sweeps
+    const int r0 = 8 * w;
+    float g[8];
     if (warm) {
-        const int r0 = 8 * w;
-        float g[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) g[k] = sigma * Vs[(r0 + k) * LD + lane];
 #pragma unroll 2
@@ -1017,34 +1051,34 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) Gs[(r0 + k) * LD + lane] = lane < N ? g[k] : 0.f;
-        __syncthreads();
+        for (int k = 0; k < 8; ++k) g[k] = lane < N ? g[k] : 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = lane < N ? Ws[(r0 + k) * LD + lane] + ((r0 + k == lane) ? sigma : 0.f) : 0.f;
     }
 
-    // ---- sweeps: warp 0, lane c = column c. The column is kept as kap * gh: a rotation scales
-    // both columns of its pair by c, which goes into kap, so the rows take one FMA each
-    // (gh' = gh -+ t (kap_partner / kap) gh_partner); every sweep starts from kap = 1.
+    // ---- sweeps by all four warps, lane c = column c, warp w its rows 8w .. 8w + 7. A round's
+    // Gram entry is the sum of the four warps' partial sums, exchanged through shared memory with
+    // one barrier (double-buffered by round parity) and added in the same order in every warp, so
+    // all warps hold the same alpha, gamma, rotation and kap and take the same branches. The
+    // column is kept as kap * gh: a rotation scales both columns of its pair by c, which goes into
+    // kap, so the rows take one FMA each (gh' = gh -+ t (kap_partner / kap) gh_partner); every
+    // sweep starts from kap = 1.
     int sweeps = 0;
-    if (w == 0) {
-        __syncwarp();
-        const int c = lane;
-        float g[32];
-        if (warm) {
-#pragma unroll
-            for (int r = 0; r < 32; ++r) g[r] = Gs[r * LD + c];
-        } else {
-#pragma unroll
-            for (int r = 0; r < 32; ++r) g[r] = c < N ? Ws[r * LD + c] + ((r == c) ? sigma : 0.f) : 0.f;
-        }
+    const int c = lane;
+    {
         const int n = N - 1;                      // rounds per sweep (odd)
         float kap = 1.f, kinv = 1.f;
         for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
-            float alpha = 0.f;                    // ||g_c||^2 (true scale)
+            float ap = 0.f;
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                g[r] *= kap;
-                alpha = fmaf(g[r], g[r], alpha);
+            for (int k = 0; k < 8; ++k) {
+                g[k] *= kap;
+                ap = fmaf(g[k], g[k], ap);
             }
+            s_cn[w][c] = ap;
+            __syncthreads();
+            float alpha = (s_cn[0][c] + s_cn[1][c]) + (s_cn[2][c] + s_cn[3][c]);   // ||g_c||^2
             kap = 1.f;
             kinv = 1.f;
             bool big = false;                     // some pair started this sweep beyond the stop
@@ -1055,20 +1089,26 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
                 const int p = c >= N ? c : (c == n ? rd : (j == c ? n : j));
                 j += 2;
                 if (j >= n) j -= n;
-                float gp[32];
+                float gp[8];
 #pragma unroll
-                for (int r = 0; r < 32; ++r) gp[r] = __shfl_sync(0xffffffffu, g[r], p);
+                for (int k = 0; k < 8; ++k) gp[k] = __shfl_sync(0xffffffffu, g[k], p);
                 const float beta = __shfl_sync(0xffffffffu, alpha, p);
                 const float kp = __shfl_sync(0xffffffffu, kap, p);
                 const bool first = c < p;
                 const float d = first ? beta - alpha : alpha - beta;   // alpha_j - alpha_i
                 const float two_over_d = __fdividef(2.f, d);           // ready before gamma is
-                float ga[4] = {0.f, 0.f, 0.f, 0.f};
+                float ga0 = 0.f, ga1 = 0.f;
 #pragma unroll
-                for (int r = 0; r < 32; ++r) ga[r & 3] = fmaf(g[r], gp[r], ga[r & 3]);
+                for (int k = 0; k < 8; k += 2) {
+                    ga0 = fmaf(g[k], gp[k], ga0);
+                    ga1 = fmaf(g[k + 1], gp[k + 1], ga1);
+                }
+                float* pr = s_gp[rd & 1];
+                pr[w * 32 + c] = ga0 + ga1;
+                __syncthreads();
                 // both ends form the same product (kap * kp in the same order at both ends)
                 const float kk = first ? kap * kp : kp * kap;
-                const float gam = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * kk;
+                const float gam = ((pr[c] + pr[32 + c]) + (pr[64 + c] + pr[96 + c])) * kk;
                 const float g2 = gam * gam, ab = alpha * beta;
                 const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
                 big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
@@ -1080,7 +1120,7 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
                 // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j), with s = t c
                 const float f = rot ? (first ? -t : t) * (kp * kinv) : 0.f;
 #pragma unroll
-                for (int r = 0; r < 32; ++r) g[r] = fmaf(f, gp[r], g[r]);
+                for (int k = 0; k < 8; ++k) g[k] = fmaf(f, gp[k], g[k]);
                 if (rot) {
                     kap *= q.c;
                     kinv *= q.ic;
@@ -1090,23 +1130,29 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
             ++sweeps;
             if (!__any_sync(0xffffffffu, big)) break;
         }
-#pragma unroll
-        for (int r = 0; r < 32; ++r) g[r] *= kap;
         // lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into Ws
-        float mu2 = 0.f;
+        float mp = 0.f;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) mu2 = fmaf(g[r], g[r], mu2);
+        for (int k = 0; k < 8; ++k) {
+            g[k] *= kap;
+            mp = fmaf(g[k], g[k], mp);
+        }
+        s_cn[w][c] = mp;              // the last read of s_cn was before this sweep's barriers
+        __syncthreads();
+        const float mu2 = (s_cn[0][c] + s_cn[1][c]) + (s_cn[2][c] + s_cn[3][c]);
         const float mu = sqrtf(mu2);
         const float inv = mu > 0.f ? 1.f / mu : 0.f;
         const float lam = mu - sigma;
         const float qs = (c < N && lam > 0.f) ? sqrtf(lam) * inv : 0.f;
         if (vglob != nullptr && c < N) {
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-                if (r < N) vglob[r * N + c] = mu > 0.f ? g[r] * inv : (r == c ? 1.f : 0.f);
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                if (r < N) vglob[r * N + c] = mu > 0.f ? g[k] * inv : (r == c ? 1.f : 0.f);
+            }
         }
 #pragma unroll
-        for (int r = 0; r < 32; ++r) Ws[r * LD + c] = g[r] * qs;
+        for (int k = 0; k < 8; ++k) Ws[(r0 + k) * LD + c] = g[k] * qs;
     }
     __syncthreads();
 
@@ -1129,7 +1175,7 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
             acc[2] = fmaf(qa.z, qb.z, acc[2]);
             acc[3] = fmaf(qa.w, qb.w, acc[3]);
         }
-        const double xv = ((double)((acc[0] + acc[1]) + (acc[2] + acc[3]))) * up;
+        const double xv = float_scaled_to_double((acc[0] + acc[1]) + (acc[2] + acc[3]), e2);
         const int pos = packed_pos(ra, cb, s);
         if (MODE == PROJ_PRIMAL) {
             const double u = a.x[a.gather_idx[off + pos]];

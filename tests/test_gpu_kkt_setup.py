@@ -44,7 +44,10 @@ def test_device_kkt_matches_host_and_oracle(form, m):
             a, b = dev.state(), host.state()
             ref = oracle_state_to_abi(sdp, st)
             for key in ref:
-                assert rel_err(a[key], b[key]) <= 1e-11, (it, key, rel_err(a[key], b[key]))
+                # the first iteration from zero is one affine step through M^-1: it carries the
+                # difference of the two builds of M^-1 alone
+                bound = 1e-12 if it == 0 else 1e-11
+                assert rel_err(a[key], b[key]) <= bound, (it, key, rel_err(a[key], b[key]))
                 assert rel_err(a[key], ref[key]) <= 1e-10, (it, key, rel_err(a[key], ref[key]))
 
 
