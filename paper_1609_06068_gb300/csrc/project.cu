@@ -911,8 +911,8 @@ __global__ void __launch_bounds__(32 * 4 * CPL, CPL == 1 ? 4 : 2) k_project_os(P
 //   - small rotations (|zeta| <= 2^-7, the usual case once a warm start is close) take the series
 //     of jacobi_rot, with 2 / (alpha_j - alpha_i) formed while the Gram entry is still being
 //     summed; a round whose rotations are all small has no square root or division on its chain.
-// The sweeps stop after one in which every pair started within kOneSidedStop of orthogonal, as in
-// the other one-sided kernels.
+// The sweeps stop once every pair, in the last N - 1 rounds, started within kOneSidedStop of
+// orthogonal (the other one-sided kernels ask this of a whole sweep).
 // The rotation that makes two columns of G orthogonal, for the one-sided kernels: from
 // d = alpha_j - alpha_i, gamma and zeta = 2 gamma / d, the tangent t = zeta / (1 + sqrt(1 +
 // zeta^2)) (= sign(d) 2 gamma / (|d| + sqrt(d^2 + 4 gamma^2)), Golub & Van Loan's smaller root),
@@ -1069,7 +1069,12 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
     {
         const int n = N - 1;                      // rounds per sweep (odd)
         float kap = 1.f, kinv = 1.f;
-        for (int sweep = 0; sweep < kOneSidedMaxSweeps; ++sweep) {
+        // The sweeps stop once n consecutive rounds (every pair met once, possibly across two
+        // sweeps) found no pair beyond kOneSidedStop: the test of the other one-sided kernels
+        // (a whole sweep without one), taken at any round rather than at sweep ends.
+        int clean = 0;
+        bool stop = false;
+        for (int sweep = 0; sweep < kOneSidedMaxSweeps && !stop; ++sweep) {
             float ap = 0.f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -1081,7 +1086,6 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
             float alpha = (s_cn[0][c] + s_cn[1][c]) + (s_cn[2][c] + s_cn[3][c]);   // ||g_c||^2
             kap = 1.f;
             kinv = 1.f;
-            bool big = false;                     // some pair started this sweep beyond the stop
             // round-robin partner: player n meets player rd; player i < n meets (2 rd - i) mod n,
             // or player n when that is i itself. j tracks (2 rd - c) mod n.
             int j = (c == 0 || c >= n) ? 0 : n - c;
@@ -1111,10 +1115,17 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
                 const float gam = ((pr[c] + pr[32 + c]) + (pr[64 + c] + pr[96 + c])) * kk;
                 const float g2 = gam * gam, ab = alpha * beta;
                 const bool rot = p != c && g2 > (kWSSkip * kWSSkip) * ab;
-                big |= p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
+                const bool big = p != c && g2 > (kOneSidedStop * kOneSidedStop) * ab;
                 const float z = gam * two_over_d;                      // zeta
                 const bool series = fabsf(z) <= kSmallAngle;
-                if (!__any_sync(0xffffffffu, rot)) continue;
+                if (!__any_sync(0xffffffffu, rot)) {
+                    if (++clean >= n) {
+                        stop = true;
+                        break;
+                    }
+                    continue;
+                }
+                clean = __any_sync(0xffffffffu, big) ? 0 : clean + 1;
                 const JRot q = jacobi_rot(gam, d, z, series, __any_sync(0xffffffffu, rot && !series));
                 const float t = q.t;
                 // g_i' = c g_i - s g_j (i), g_j' = s g_i + c g_j (j), with s = t c
@@ -1126,9 +1137,12 @@ __global__ void __launch_bounds__(128) k_project_ws(ProjArgs a, double rinv) {
                     kinv *= q.ic;
                     alpha = first ? alpha - t * gam : alpha + t * gam;
                 }
+                if (clean >= n) {
+                    stop = true;
+                    break;
+                }
             }
             ++sweeps;
-            if (!__any_sync(0xffffffffu, big)) break;
         }
         // lambda_j = mu_j - sigma, v_j = g_j / mu_j; Q = V diag(max(lambda, 0))^(1/2) into Ws
         float mp = 0.f;
