@@ -1290,23 +1290,27 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 
     // ---- W scaled by 2^-e2 (exact) into the segment's tile, both triangles, zero padding. Up to
     // 16 rows the lane reads its column once, all loads in flight, and keeps it until the scale is
-    // known; 32 doubles per lane would spill, so NR = 32 reads the column twice.
+    // known; 32 doubles per lane would spill, so NR = 32 forms W twice, its packed entries dealt
+    // to the lanes in turn (entries c, c + 32, ...) so that the lanes share the triangle evenly.
+    // The block's exponent comes from the bits, and the scaling and rounding to FP32 take no FP64
+    // instruction (FP64 instructions issue at one warp instruction per 64 clocks here).
     constexpr int KW = NR <= 16 ? NR : 1;
     double wc[KW];
-    double wmax = 0.0;
+    int emax = 0;
+    const int len = s * (s + 1) / 2;
     if constexpr (NR <= 16) {
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             wc[r] = (r >= c && r < s) ? load_w<MODE>(a, off, packed_pos(r, c, s), rinv) : 0.0;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) wmax = fmax(wmax, fabs(wc[r]));
+        for (int r = 0; r < NR; ++r) emax = max(emax, (__double2hiint(wc[r]) >> 20) & 0x7ff);
     } else {
-        if (c < s)
-            for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
+        for (int q = c; q < len; q += NR) emax = max(emax, (__double2hiint(load_w<MODE>(a, off, q, rinv)) >> 20) & 0x7ff);
     }
-    wmax = seg_maxd<NR>(wmax);
-    const int e2 = block_exponent(wmax);
-    const double down = pow2_exact(-e2), up = pow2_exact(e2);
+#pragma unroll
+    for (int o = NR / 2; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    // ilogb of max |W_ij| from the biased exponent, clamped to [-1000, 1000] as in block_exponent
+    const int e2 = emax == 0 ? -1000 : emax == 0x7ff ? 0 : min(max(emax - 1023, -1000), 1000);
 #pragma unroll
     for (int r = 0; r < NR; ++r) Ws[r * LD + c] = 0.f;
     __syncwarp();
@@ -1314,17 +1318,22 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (r >= c && r < s) {
-                const float wt = (float)((wc[r]) * down);
+                const float wt = scaled_to_float(wc[r], e2);
                 Ws[r * LD + c] = wt;
                 Ws[c * LD + r] = wt;
             }
     } else {
-        if (c < s)
-            for (int r = c; r < s; ++r) {
-                const float wt = (float)((load_w<MODE>(a, off, packed_pos(r, c, s), rinv)) * down);
-                Ws[r * LD + c] = wt;
-                Ws[c * LD + r] = wt;
+        int col = 0, cend = s;                        // entry q lies in column col, which ends at cend
+        for (int q = c; q < len; q += NR) {
+            while (q >= cend) {
+                ++col;
+                cend += s - col;
             }
+            const int r = col + (q - (cend - (s - col)));
+            const float wt = scaled_to_float(load_w<MODE>(a, off, q, rinv), e2);
+            Ws[r * LD + col] = wt;
+            Ws[col * LD + r] = wt;
+        }
     }
     __syncwarp();
 
@@ -1440,15 +1449,22 @@ __global__ void __launch_bounds__(128, NR == 32 ? 4 : 0) k_project_ow(ProjArgs a
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL && act) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
-    for (int cb = 0; cb < s; ++cb) {
-        const float* Qb = Ws + cb * LD;
-        for (int ra = cb + c; ra < s; ra += NR) {
+    // the packed entries dealt to the segment's lanes in turn, as for W
+    int col = 0, cend = s;
+    for (int q = c; q < len; q += NR) {
+        while (q >= cend) {
+            ++col;
+            cend += s - col;
+        }
+        const int cb = col, ra = col + (q - (cend - (s - col)));
+        {
             const float* Qa = Ws + ra * LD;
+            const float* Qb = Ws + cb * LD;
             float acc = 0.f;
 #pragma unroll 8
             for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = ((double)acc) * up;
-            const int pos = packed_pos(ra, cb, s);
+            const double xv = float_scaled_to_double(acc, e2);
+            const int pos = q;
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
                 const double l = a.lam[off + pos];
@@ -1512,28 +1528,41 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
     const bool warm = a.vstore != nullptr && a.ctrl != nullptr;
     float* vglob = a.vstore != nullptr ? reinterpret_cast<float*>(a.vstore) + a.voff[blk] : nullptr;
 
-    // ---- W scaled by 2^-e2 (exact) into the tile, both triangles, zero padding
-    double wmax = 0.0;
-    if (c < s)
-        for (int r = c; r < s; ++r) wmax = fmax(wmax, fabs(load_w<MODE>(a, off, packed_pos(r, c, s), rinv)));
-    red[c] = (float)0;
-    double wm = wmax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-    double* redd = reinterpret_cast<double*>(Vs);     // Vs is free until the warm start fills it
-    if ((c & 31) == 0) redd[c >> 5] = wm;
+    // ---- W scaled by 2^-e2 (exact) into the tile, both triangles, zero padding. The packed
+    // entries are dealt to the 64 lanes in turn (lane c takes entries c, c + 64, ...), so the lanes
+    // share the triangle evenly; W is formed once (one FMA) into FP64 scratch (the V tile, free
+    // until the warm start fills it), the block's exponent comes from the bits, and the scaling
+    // and rounding to FP32 take no FP64 instruction.
+    const int len = s * (s + 1) / 2;
+    double* wsc = reinterpret_cast<double*>(Vs);      // 64 x LD floats hold the 2080 doubles of s = 64
+    int emax = 0;
+    for (int q = c; q < len; q += 64) {
+        const double wv = load_w<MODE>(a, off, q, rinv);
+        wsc[q] = wv;
+        emax = max(emax, (__double2hiint(wv) >> 20) & 0x7ff);
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    int* redi = reinterpret_cast<int*>(red);
+    if ((c & 31) == 0) redi[c >> 5] = emax;
     for (int r = 0; r < 64; ++r) Ts[r * LD + c] = 0.f;
     pair_sync(pair);
-    wmax = fmax(redd[0], redd[1]);
-    const int e2 = block_exponent(wmax);
-    const double down = pow2_exact(-e2), up = pow2_exact(e2);
-    pair_sync(pair);
-    if (c < s)
-        for (int r = c; r < s; ++r) {
-            const float wt = (float)((load_w<MODE>(a, off, packed_pos(r, c, s), rinv)) * down);
-            Ts[r * LD + c] = wt;
-            Ts[c * LD + r] = wt;
+    emax = max(redi[0], redi[1]);
+    // ilogb of max |W_ij| from the biased exponent, clamped to [-1000, 1000] as in block_exponent
+    const int e2 = emax == 0 ? -1000 : emax == 0x7ff ? 0 : min(max(emax - 1023, -1000), 1000);
+    {
+        int col = 0, cend = s;                        // entry q lies in column col, which ends at cend
+        for (int q = c; q < len; q += 64) {
+            while (q >= cend) {
+                ++col;
+                cend += s - col;
+            }
+            const int r = col + (q - (cend - (s - col)));
+            const float wt = scaled_to_float(wsc[q], e2);
+            Ts[r * LD + col] = wt;
+            Ts[col * LD + r] = wt;
         }
+    }
+    pair_sync(pair);                                  // the scratch is read before V overwrites it
     if (warm)
         for (int r = 0; r < 64; ++r) Vs[r * LD + c] = (r < N && c < N) ? vglob[r * N + c] : (r == c ? 1.f : 0.f);
     pair_sync(pair);
@@ -1660,14 +1689,28 @@ __global__ void __launch_bounds__(128) k_project_ow64(ProjArgs a, double rinv) {
     double pv[3] = {0.0, 0.0, 0.0};
     double* xk_new = nullptr;
     if (MODE == PROJ_PRIMAL) xk_new = (a.ctrl->iter & 1) ? a.xk[0] : a.xk[1];
-    for (int cb = 0; cb < s; ++cb) {
-        const float* Qb = Ts + cb * LD;
-        for (int ra = cb + c; ra < s; ra += 64) {
-            const float* Qa = Ts + ra * LD;
-            float acc = 0.f;
-            for (int i = 0; i < N; ++i) acc = fmaf(Qa[i], Qb[i], acc);
-            const double xv = ((double)acc) * up;
-            const int pos = packed_pos(ra, cb, s);
+    // the packed entries dealt to the lanes in turn, as for W; rows of Q read four at a time
+    const int N4 = (N + 3) & ~3;
+    int col = 0, cend = s;
+    for (int q = c; q < len; q += 64) {
+        while (q >= cend) {
+            ++col;
+            cend += s - col;
+        }
+        const int cb = col, ra = col + (q - (cend - (s - col)));
+        {
+            const float4* Qa = reinterpret_cast<const float4*>(Ts + ra * LD);
+            const float4* Qb = reinterpret_cast<const float4*>(Ts + cb * LD);
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int i = 0; i < N4 / 4; ++i) {
+                const float4 x = Qa[i], y = Qb[i];
+                acc0 = fmaf(x.x, y.x, acc0);
+                acc1 = fmaf(x.y, y.y, acc1);
+                acc0 = fmaf(x.z, y.z, acc0);
+                acc1 = fmaf(x.w, y.w, acc1);
+            }
+            const double xv = float_scaled_to_double(acc0 + acc1, e2);
+            const int pos = q;
             if (MODE == PROJ_PRIMAL) {
                 const double u = a.x[a.gather_idx[off + pos]];
                 const double l = a.lam[off + pos];
