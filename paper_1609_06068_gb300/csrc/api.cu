@@ -130,14 +130,32 @@ struct sdp_ctx {
     Ctrl* h_ctrl = nullptr;    // pinned, two slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
+    // Device arrays live as long as the handle, so small ones are carved (256-byte aligned) from
+    // chunks of kChunkBytes and large ones get an allocation each: a setup makes a few dozen
+    // cudaMalloc calls fewer, and sdp_free as many cudaFree calls fewer.
+    static constexpr size_t kChunkBytes = size_t(4) << 20;
+    char* chunk_next = nullptr;
+    size_t chunk_left = 0;
     template <typename T>
     int dalloc(T** ptr, size_t count) {
-        void* p_ = nullptr;
-        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-        const cudaError_t e = cudaMalloc(&p_, bytes);
-        if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        allocs.push_back(p_);
-        *ptr = static_cast<T*>(p_);
+        const size_t bytes = (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~size_t(255);
+        if (bytes > chunk_left) {
+            const bool own = bytes * 4 > kChunkBytes;     // a large array: an allocation of its own
+            const size_t sz = own ? bytes : kChunkBytes;
+            void* p_ = nullptr;
+            const cudaError_t e = cudaMalloc(&p_, sz);
+            if (e != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            allocs.push_back(p_);
+            if (own) {
+                *ptr = static_cast<T*>(p_);
+                return SDP_OK;
+            }
+            chunk_next = static_cast<char*>(p_);
+            chunk_left = sz;
+        }
+        *ptr = reinterpret_cast<T*>(chunk_next);
+        chunk_next += bytes;
+        chunk_left -= bytes;
         return SDP_OK;
     }
     template <typename T, typename Alloc>
