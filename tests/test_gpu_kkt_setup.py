@@ -139,3 +139,54 @@ def test_untidy_constraints_give_identical_iterates(flags):
         sa, sb = a.state(), b.state()
         for key in sa:
             assert np.array_equal(sa[key], sb[key]), key
+
+
+@pytest.mark.parametrize("m,density", [(300, 0.4), (450, 0.9)])
+def test_device_kkt_global_partials_match_host(m, density):
+    """From m = 240 the partial sums of A D^-1 A^T no longer fit in shared memory and go to global
+    memory in row bands: m = 300 with short columns stages whole slices, m = 450 with columns of
+    about 400 entries stages one column at a time. The first iteration (one affine step through
+    M^-1) agrees with the host build to 1e-12, later iterates to 1e-11, and with the oracle to
+    1e-10."""
+    torch, cadmm = require_gpu()
+    arrs = sdp_cases.random_block_arrow(l=30, d=6, h=4, m=m, seed=41 + m, density=density)
+    sdp = make_oracle(arrs)
+    assert np.linalg.cond(sdp.M) < 1e4
+    st = orc.admm_init(sdp, "dual")
+    with setup_handle(cadmm, arrs, form="dual", rho=0.3, tol=0.0) as dev, \
+            setup_handle(cadmm, arrs, form="dual", rho=0.3, tol=0.0, flags=cadmm.SDP_FLAG_HOST_KKT) as host:
+        for it in range(6):
+            st = orc.dual_iteration(sdp, st, 0.3)
+            dev.iterate(1)
+            host.iterate(1)
+            a, b = dev.state(), host.state()
+            ref = oracle_state_to_abi(sdp, st)
+            for key in ref:
+                bound = 1e-12 if it == 0 else 1e-11
+                assert rel_err(a[key], b[key]) <= bound, (it, key, rel_err(a[key], b[key]))
+                assert rel_err(a[key], ref[key]) <= 1e-10, (it, key, rel_err(a[key], ref[key]))
+
+
+def test_setup_times_report_the_stages():
+    """sdp_setup_times: five named stages, none negative, adding up to no more than the setup
+    call's wall time; the device stage is zero when the host builds the factorization."""
+    import time
+    torch, cadmm = require_gpu()
+    arrs = sdp_cases.random_block_arrow(l=12, d=5, h=4, m=80, seed=3, density=0.4)
+    for flags in (0, cadmm.SDP_FLAG_HOST_KKT):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = setup_handle(cadmm, arrs, form="dual", flags=flags)
+        wall_ms = 1e3 * (time.perf_counter() - t0)
+        try:
+            st = cadmm.sdp_setup_times(s.h)
+        finally:
+            s.close()
+        assert list(st) == ["host_build", "plan", "alloc_upload", "device_kkt", "finish"]
+        assert all(v >= 0.0 for v in st.values())
+        assert sum(st.values()) <= wall_ms + 0.5, (st, wall_ms)
+        if flags:
+            assert st["device_kkt"] == 0.0
+        else:
+            assert st["device_kkt"] > 0.0
+    assert cadmm.load_library().sdp_setup_stage_name(5) is None
