@@ -1145,7 +1145,7 @@ int project_variant_count(void) { return cadmm::PV_COUNT; }
 
 const char* project_variant_name(int v) {
     static const char* names[cadmm::PV_COUNT] = {"os32", "os64", "ts16", "ts32", "ts64", "ts96",
-                                                 "ow8", "ow16", "ow32", "ow64", "ws32"};
+                                                 "ow8", "ow16", "ow32", "ow64", "ws32", "ws64"};
     return (v >= 0 && v < cadmm::PV_COUNT) ? names[v] : nullptr;
 }
 

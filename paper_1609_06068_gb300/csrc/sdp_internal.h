@@ -224,7 +224,7 @@ struct Sched {
 // Projection launches: the cliques in processing order (largest first) split into runs that use
 // the same kernel variant. A run [start, start + count) of `order` goes to one launch.
 enum ProjVariant { PV_OS1 = 0, PV_OS2, PV_TS16, PV_TS32, PV_TS64, PV_TS96, PV_OW8, PV_OW16, PV_OW32, PV_OW64,
-                   PV_WS32, PV_COUNT };
+                   PV_WS32, PV_WS64, PV_COUNT };
 constexpr int kMaxProjRuns = 64;
 struct ProjPlan {
     int runs;
