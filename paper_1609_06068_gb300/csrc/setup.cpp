@@ -47,19 +47,15 @@ struct EntryIndex {
         return (long long)(it - rows.data());
     }
     // The same, for a row r of column c known to come after position `after` (an entry of the
-    // same column with a smaller row): galloping forward from there, so that a run of lookups in
-    // E_L order costs about the gaps between them.
+    // same column with a smaller row): a few steps forward from there, then a binary search, so
+    // that a run of lookups in E_L order costs about the gaps between them.
     long long find_after(long long r, long long c, long long after) const {
         const int* base = rows.data();
         const long long end = col_start[c + 1];
-        long long lo = after + 1, step = 1;
-        while (lo + step - 1 < end && base[lo + step - 1] < r) {
-            lo += step;
-            step <<= 1;
-        }
-        const int* it = std::lower_bound(base + lo, base + std::min(end, lo + step), (int)r);
-        if (it == base + end || *it != r) return -1;
-        return (long long)(it - base);
+        long long q = after + 1;
+        for (int k = 0; k < 8 && q < end && base[q] < r; ++k) ++q;
+        if (q < end && base[q] < r) q = std::lower_bound(base + q, base + end, (int)r) - base;
+        return (q < end && base[q] == r) ? q : -1;
     }
 };
 
