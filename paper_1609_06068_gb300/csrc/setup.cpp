@@ -18,7 +18,6 @@ namespace cadmm {
 
 namespace {
 
-inline long long key_of(long long row, long long col, long long n) { return col * n + row; }
 
 int fail(std::string& err, int code, const std::string& msg) {
     err = msg;
@@ -30,13 +29,11 @@ int fail(std::string& err, int code, const std::string& msg) {
 struct EntryIndex {
     std::vector<long long> col_start;   // [n+1]
     std::vector<int> rows;              // [|E_L|]
-    void build(const std::vector<long long>& keys, long long n) {
+    // From the entries' rows and columns, sorted by column, then row.
+    void build(const std::vector<int>& el_row, const std::vector<int>& el_col, long long n) {
         col_start.assign(n + 1, 0);
-        rows.resize(keys.size());
-        for (size_t e = 0; e < keys.size(); ++e) {
-            rows[e] = (int)(keys[e] % n);
-            col_start[keys[e] / n + 1]++;
-        }
+        rows = el_row;
+        for (int c : el_col) col_start[c + 1]++;
         for (long long c = 0; c < n; ++c) col_start[c + 1] += col_start[c];
     }
     long long find(long long r, long long c) const {
@@ -287,9 +284,9 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     std::stable_sort(hp.order.begin(), hp.order.end(),
                      [&](int x, int y) { return hp.blk_size[x] > hp.blk_size[y]; });
 
-    // ---- lower pattern E_L = union of lower clique pairs, column-major (key = col*n + row).
+    // ---- lower pattern E_L = union of lower clique pairs, column-major (by column, then row).
     // Packed positions are enumerated in storage order: clique, column b, rows a >= b.
-    std::vector<long long> pos_key(SL_mat);
+    std::vector<int> pos_row(SL_mat), pos_col(SL_mat);
     hp.pos_w.assign(SL, 1);
     {
         long long q = 0;
@@ -298,41 +295,50 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
             const int s = hp.blk_size[k];
             for (int bb = 0; bb < s; ++bb)
                 for (int a = bb; a < s; ++a, ++q) {
-                    pos_key[q] = key_of(v[a], v[bb], n);
+                    pos_row[q] = v[a];
+                    pos_col[q] = v[bb];
                     hp.pos_w[q] = (a == bb) ? 1 : 2;
                 }
         }
     }
-    // keys in increasing order by two counting passes (row, then column: a stable LSD radix
-    // sort in base n), then duplicates dropped
-    std::vector<long long> keys(pos_key.size());
+    // the positions ordered by column, then row (two stable counting passes, by row and then by
+    // column), and repeated pairs dropped
+    std::vector<int> el_row, el_col;
     {
-        std::vector<long long> tmp(pos_key.size());
-        std::vector<long long> cnt((size_t)n + 1);
-        auto pass = [&](const std::vector<long long>& in, std::vector<long long>& out, bool by_col) {
-            std::fill(cnt.begin(), cnt.end(), 0);
-            for (long long k : in) cnt[(by_col ? k / n : k % n) + 1]++;
-            for (int d = 0; d < n; ++d) cnt[d + 1] += cnt[d];
-            for (long long k : in) out[cnt[by_col ? k / n : k % n]++] = k;
-        };
-        pass(pos_key, tmp, false);
-        pass(tmp, keys, true);
+        const int L = (int)SL_mat;
+        std::vector<int> ord1(L), ord2(L);
+        std::vector<int> cnt((size_t)n + 1, 0);
+        for (int q = 0; q < L; ++q) cnt[pos_row[q] + 1]++;
+        for (int d = 0; d < n; ++d) cnt[d + 1] += cnt[d];
+        for (int q = 0; q < L; ++q) ord1[cnt[pos_row[q]]++] = q;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int q = 0; q < L; ++q) cnt[pos_col[q] + 1]++;
+        for (int d = 0; d < n; ++d) cnt[d + 1] += cnt[d];
+        for (int i = 0; i < L; ++i) ord2[cnt[pos_col[ord1[i]]]++] = ord1[i];
+        el_row.reserve(L);
+        el_col.reserve(L);
+        for (int i = 0; i < L; ++i) {
+            const int q = ord2[i];
+            if (el_row.empty() || pos_row[q] != el_row.back() || pos_col[q] != el_col.back()) {
+                el_row.push_back(pos_row[q]);
+                el_col.push_back(pos_col[q]);
+            }
+        }
     }
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    if ((long long)keys.size() + nc >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
-    const int nEL_mat = (int)keys.size();
+    if ((long long)el_row.size() + nc >= (1LL << 31)) return fail(err, SDP_ERR_UNSUPPORTED, "|E_L| >= 2^31");
+    const int nEL_mat = (int)el_row.size();
     const int nEL = nEL_mat + (int)nc;    // cone variable j is entry nEL_mat + j
     hp.nEL = nEL;
     hp.n_cone = (int)nc;
     EntryIndex index;
-    index.build(keys, std::max(n, 1));
+    index.build(el_row, el_col, std::max(n, 1));
     hp.pat_row.resize(nEL);
     hp.pat_col.resize(nEL);
     hp.ew.assign(nEL, 1);
     for (int e = 0; e < nEL_mat; ++e) {
-        hp.pat_row[e] = (int)(keys[e] % n);
-        hp.pat_col[e] = (int)(keys[e] / n);
-        hp.ew[e] = hp.pat_row[e] == hp.pat_col[e] ? 1 : 2;
+        hp.pat_row[e] = el_row[e];
+        hp.pat_col[e] = el_col[e];
+        hp.ew[e] = el_row[e] == el_col[e] ? 1 : 2;
     }
     for (int j = 0; j < (int)nc; ++j) hp.pat_row[nEL_mat + j] = hp.pat_col[nEL_mat + j] = n + j;
 
@@ -342,7 +348,7 @@ int build_host_problem(int n, int m, const long long* A_ptr, const int* A_row, c
     std::vector<int> cnt(nEL + 1, 0);
     parallel_for(p, [&](int k) {
         for (long long q = hp.blk_off[k]; q < hp.blk_off[k] + (long long)hp.blk_size[k] * (hp.blk_size[k] + 1) / 2; ++q)
-            hp.gather_idx[q] = (int)index.find(pos_key[q] % n, pos_key[q] / n);
+            hp.gather_idx[q] = (int)index.find(pos_row[q], pos_col[q]);
     });
     for (long long j = 0; j < nc; ++j) hp.gather_idx[SL_mat + j] = nEL_mat + (int)j;
     if (nc > 0) {
