@@ -205,33 +205,37 @@ __device__ __forceinline__ double pow2_exact(int k) {       // 2^k for |k| <= 10
     return __longlong_as_double((long long)(1023 + k) << 52);
 }
 
-// x 2^-e2 rounded to FP32 (to nearest, ties to even), from the bits, with no FP64 instruction:
+// x 2^-e2 rounded to FP32 (to nearest, ties to even), from the bits, with no FP64 instruction
+// (on GB300 an FP64 instruction, conversions included, takes a warp 64 clocks per SM partition):
 // the scaling only moves the exponent, and the rounding takes the top 24 of the 53 significand
 // bits. Values that land below FP32's normal range (under 2^-126 after scaling, while the block's
-// largest entry lands in [1, 2)) become zero; an infinity or a NaN passes through unscaled.
+// largest entry lands in [1, 2)) become zero; an infinity or a NaN stays one (unscaled).
 __device__ __forceinline__ float scaled_to_float(double x, int e2) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0x7ff) return (float)x;
-    const int fe = ex - e2 - 896;                        // FP32 biased exponent after scaling
-    if (ex == 0 || fe <= 0) return __uint_as_float(sign);
     const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    unsigned bits = sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29);
+    const int fe = ex - e2 - 896;                        // FP32 biased exponent after scaling
+    unsigned bits = sign | ((unsigned)min(max(fe, 0), 255) << 23) | (unsigned)(mant >> 29);
     const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
-    if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ++bits;
+    bits += (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+    const unsigned special = sign | 0x7F800000u | (mant != 0ull ? 0x00400000u : 0u);   // inf, NaN
+    bits = ex == 0x7ff ? special : (ex == 0 || fe <= 0) ? sign : bits;
     return __uint_as_float(bits);
 }
-// (double)f 2^e2, exactly, from the bits (zero, subnormal, infinite and NaN inputs, and results
-// outside the normal FP64 range, take the arithmetic).
+// (double)f 2^e2 from the bits, with no FP64 instruction: exact for normal results; a zero or
+// FP32-subnormal f (under 2^-126 of the block's scale) gives zero, an infinity or a NaN stays one,
+// and a result outside the normal FP64 range becomes zero or an infinity.
 __device__ __forceinline__ double float_scaled_to_double(float f, int e2) {
     const unsigned u = __float_as_uint(f);
-    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
     const int fe = (int)((u >> 23) & 0xff);
+    const unsigned long long mant = (unsigned long long)(u & 0x7FFFFFu) << 29;
     const int de = fe - 127 + 1023 + e2;
-    if (fe == 0 || fe == 0xff || de <= 0 || de >= 0x7ff) return (double)f * pow2_exact(e2);
-    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)de << 52) |
-                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    unsigned long long bits = sign | ((unsigned long long)min(max(de, 0), 0x7ff) << 52) | mant;
+    bits = (fe == 0 || de <= 0) ? sign
+         : (fe == 0xff) ? (sign | 0x7FF0000000000000ull | mant)
+         : (de >= 0x7ff) ? (sign | 0x7FF0000000000000ull) : bits;
     return __longlong_as_double((long long)bits);
 }
 
