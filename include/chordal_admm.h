@@ -349,13 +349,15 @@ int project_psd_batched_variant(const double* in, double* out, const int* sizes,
  * rebuilt at the next admm_iterate; iterates are unchanged. */
 int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len);
 
-/* Profiling: run `reps` iterations kernel by kernel (no graph) on cuda_stream with CUDA events
- * between the phases, and write the average device milliseconds of each phase of one iteration
- * to ms_out[0 .. count-1] in launch order (count = 6 primal, 7 dual, one more for the per-problem
- * stop test of a batch; the projection phase covers all of its launches). Returns count, or < 0
- * on error; max_out is the capacity of ms_out. The iterations really run and advance the state,
- * with the stop test disabled. sdp_phase_name(h, i) names phase i for the handle's current form
- * (NULL when out of range). */
+/* Profiling: run one untimed iteration and then `reps` timed iterations kernel by kernel (no
+ * graph) on cuda_stream, with CUDA events between the phases, all queued before the host waits
+ * (so an event pair brackets the device's work, not the host's submission), and write the
+ * average device milliseconds of each phase of one iteration to ms_out[0 .. count-1] in launch
+ * order (count = 5 primal, 6 dual, one more each for cones, for the per-problem stop test of a
+ * batch and for the triangular KKT solve, whose two solves are two phases; the projection phase
+ * covers all of its launches). Returns count, or < 0 on error; max_out is the capacity of ms_out.
+ * The reps + 1 iterations really run and advance the state, with the stop test disabled.
+ * sdp_phase_name(h, i) names phase i for the handle's current form (NULL when out of range). */
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
 const char* sdp_phase_name(sdp_handle h, int i);
 

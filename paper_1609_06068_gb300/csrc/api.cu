@@ -602,6 +602,11 @@ int create_handle(HostProblem& hp, const admm_opts* opts, sdp_handle* out, doubl
     IterPtrs& P = h->P;
     P.n = hp.n; P.m = hp.m; P.p = hp.p; P.nEL = hp.nEL; P.SL = hp.SL; P.smax = hp.smax;
     P.ninst = hp.ninst;
+    // Programmatic dependent launch hides part of each kernel's launch latency. On GB300 it paid
+    // where the kernels are short (1.5e6 nonzeros of A, cliques of 30: 17.2 k -> 17.9 k FP32
+    // iterations/s) and not where a pass over A takes half a millisecond (2e8 nonzeros: a batch
+    // 0.8 % faster, a single problem 2 % slower).
+    P.pdl = hp.nnz <= (1LL << 24) ? 1 : 0;
     P.mmax = 0;
     for (int q = 0; q < hp.ninst; ++q) P.mmax = std::max(P.mmax, hp.inst_row[q + 1] - hp.inst_row[q]);
     P.row_chunks = (int)S.row.size();
@@ -1348,21 +1353,29 @@ int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, i
     if (max_out < count) return set_err(SDP_ERR_ARG, "ms_out too small");
     CK(cudaSetDevice(h->device));
     cudaStream_t st = as_stream(cuda_stream);
-    std::vector<cudaEvent_t> ev(count + 1);
-    for (auto& e : ev) CK(cudaEventCreate(&e));
+    // Every repetition is queued before the device reaches it: one untimed iteration first, then
+    // the timed ones with no host synchronization between them, so that an event pair brackets
+    // the device's work and not the host's time to submit the launch after an idle stream.
+    const size_t per = (size_t)count + 1;
+    std::vector<cudaEvent_t> ev(per * (size_t)reps, nullptr);
+    cudaError_t ce = cudaSuccess;
+    for (size_t i = 0; i < ev.size() && ce == cudaSuccess; ++i) ce = cudaEventCreate(&ev[i]);
     std::vector<double> acc(count, 0.0);
-    cudaError_t ce = cadmm::launch_ctrl_arm(h->P.ctrl, reps, 0.0, st);
-    for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
+    if (ce == cudaSuccess) ce = cadmm::launch_ctrl_arm(h->P.ctrl, reps + 1, 0.0, st);
+    if (ce == cudaSuccess)
+        ce = cadmm::launch_iteration(h->P, h->plan[h->opts.prec], h->opts.form, h->opts.prec, h->opts.rho, st);
+    for (int r = 0; r < reps && ce == cudaSuccess; ++r)
         ce = cadmm::launch_iteration(h->P, h->plan[h->opts.prec], h->opts.form, h->opts.prec, h->opts.rho, st,
-                                     ev.data());
-        if (ce == cudaSuccess) ce = cudaEventSynchronize(ev[count]);
+                                     ev.data() + per * (size_t)r);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    for (int r = 0; r < reps && ce == cudaSuccess; ++r)
         for (int i = 0; i < count && ce == cudaSuccess; ++i) {
             float ms = 0.f;
-            ce = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            ce = cudaEventElapsedTime(&ms, ev[per * r + i], ev[per * r + i + 1]);
             acc[i] += ms;
         }
-    }
-    for (auto& e : ev) cudaEventDestroy(e);
+    for (auto& e : ev)
+        if (e != nullptr) cudaEventDestroy(e);
     if (ce != cudaSuccess) return set_err(SDP_ERR_CUDA, std::string("sdp_time_phases: ") + cudaGetErrorString(ce));
     for (int i = 0; i < count; ++i) ms_out[i] = acc[i] / reps;
     return count;

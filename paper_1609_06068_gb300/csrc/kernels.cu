@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(256) k_finalize_batch(IterPtrs P, int form, do
     __shared__ double red[33 * 4];
     __shared__ int red_i[33 * 2];
     __shared__ bool s_last;
+    pdl_wait();
     Ctrl* C = P.ctrl;
     if (C->done) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -765,6 +766,7 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 ProjArgs proj_args_for(const IterPtrs& P, double rho) {
     ProjArgs a{};
+    a.pdl = P.pdl;
     a.order = P.order;
     a.size = P.blk_size;
     a.off = P.blk_off64;
@@ -898,8 +900,8 @@ __global__ void __launch_bounds__(kConeThreads) k_project_cones(IterPtrs P, doub
 cudaError_t launch_project_cones(const IterPtrs& P, int mode, double rho, cudaStream_t st) {
     if (P.ncs <= 0) return cudaSuccess;
     if (mode == PROJ_PRIMAL)
-        return launch_pdl(k_project_cones<PROJ_PRIMAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
-    return launch_pdl(k_project_cones<PROJ_DUAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
+        return launch_pdl(P.pdl != 0, k_project_cones<PROJ_PRIMAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
+    return launch_pdl(P.pdl != 0, k_project_cones<PROJ_DUAL>, dim3(P.ncs), dim3(kConeThreads), 0, st, P, rho, 1.0 / rho);
 }
 
 // All runs of the projection plan, largest cliques first.
@@ -940,27 +942,27 @@ cudaError_t launch_affine(const IterPtrs& P, int form, double rho, double rinv, 
     cudaError_t e;
     mk.mark();
     const int warps = kRowThreads / 32;
-    if ((e = launch_pdl(k_spmv_rows, dim3(cdiv(P.row_chunks, warps)), dim3(kRowThreads), 0, st, P)) != cudaSuccess)
+    if ((e = launch_pdl(P.pdl != 0, k_spmv_rows, dim3(cdiv(P.row_chunks, warps)), dim3(kRowThreads), 0, st, P)) != cudaSuccess)
         return e;
     const size_t mbytes = (size_t)P.mmax * sizeof(double);   // the largest problem's y, staged
     mk.mark();
     if (P.kkt_tri) {
-        if ((e = launch_pdl(k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess)
+        if ((e = launch_pdl(P.pdl != 0, k_tri_lower, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess)
             return e;
         mk.mark();
-        if ((e = launch_pdl(k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
-    } else if ((e = launch_pdl(k_solve_y, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) {
+        if ((e = launch_pdl(P.pdl != 0, k_tri_upper, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P)) != cudaSuccess) return e;
+    } else if ((e = launch_pdl(P.pdl != 0, k_solve_y, dim3(P.tri_ctas), dim3(kTriThreads), mbytes, st, P, rinv, form)) != cudaSuccess) {
         return e;
     }
     mk.mark();
     if (P.col_split)
-        e = launch_pdl(k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
+        e = launch_pdl(P.pdl != 0, k_spmv_cols_split, dim3(P.col_chunks), dim3(kColThreads), 0, st, P);
     else
-        e = launch_pdl(k_spmv_cols, dim3(P.col_chunks), dim3(kColThreads), mbytes, st, P);
+        e = launch_pdl(P.pdl != 0, k_spmv_cols, dim3(P.col_chunks), dim3(kColThreads), mbytes, st, P);
     if (e != cudaSuccess) return e;
     if (form == SDP_DUAL) {
         mk.mark();
-        return launch_pdl(k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);
+        return launch_pdl(P.pdl != 0, k_update_dual, dim3(P.pos_ctas), dim3(kEntThreads), 0, st, P, rho, rinv);
     }
     return cudaSuccess;
 }
@@ -999,7 +1001,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         if (P.ncs > 0) mk.mark();
         if ((e = launch_project_cones(P, PROJ_PRIMAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
-        if ((e = launch_pdl(k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
+        if ((e = launch_pdl(P.pdl != 0, k_scatter_primal, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P, rinv,
                             rho, 0)) != cudaSuccess)
             return e;
     } else {
@@ -1009,7 +1011,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
         if (P.ncs > 0) mk.mark();
         if ((e = launch_project_cones(P, PROJ_DUAL, rho, st)) != cudaSuccess) return e;
         mk.mark();
-        if ((e = launch_pdl(k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
+        if ((e = launch_pdl(P.pdl != 0, k_scatter_dual, dim3(P.ent_ctas + P.heavy_ctas), dim3(kEntThreads), 0, st, P,
                             rinv)) != cudaSuccess)
             return e;
         if ((e = launch_affine(P, form, rho, rinv, st, mk)) != cudaSuccess) return e;
@@ -1017,7 +1019,7 @@ cudaError_t launch_iteration(const IterPtrs& P, const ProjPlan& plan, int form, 
     if (P.ninst > 1) {
         mk.mark();
         const int ctas = (P.ninst + 7) / 8;
-        if ((e = launch_pdl(k_finalize_batch, dim3(ctas), dim3(256), 0, st, P, form, rho)) != cudaSuccess) return e;
+        if ((e = launch_pdl(P.pdl != 0, k_finalize_batch, dim3(ctas), dim3(256), 0, st, P, form, rho)) != cudaSuccess) return e;
     }
     mk.mark();
     return cudaGetLastError();

@@ -2090,36 +2090,50 @@ cudaError_t prepare_mode() {
 
 template <typename T, int MODE>
 cudaError_t launch_mode(const ProjArgs& a, int variant, int smax, cudaStream_t st) {
+    // programmatic launch inside an iteration's chain of kernels when the iteration asks for it,
+    // for the FP32 kernels only (FP64 blocks measured slower with it); stand-alone projections
+    // launch after their predecessor completes
+    const bool pdl = sizeof(T) == 4 && MODE != PROJ_PLAIN && a.pdl != 0;
     const size_t smem = project_smem_bytes(smax, sizeof(T) == 4 ? SDP_PROJ_FP32 : SDP_PROJ_FP64, MODE);
     const double rinv = 1.0 / a.rho;
     switch (variant) {
         case PV_OS1:
-            return launch_pdl(k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_os<MODE, 1>, dim3(a.count), dim3(128), OSLayout<1>::kBytes, st,
+                              a, rinv);
         case PV_OS2:
-            return launch_pdl(k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_os<MODE, 2>, dim3(a.count), dim3(256), OSLayout<2>::kBytes, st,
+                              a, rinv);
         case PV_WS32:
-            return launch_pdl(k_project_ws<MODE>, dim3(a.count), dim3(128), 0, st, a, rinv);
+            return launch_pdl(pdl, k_project_ws<MODE>, dim3(a.count), dim3(128), 0, st, a, rinv);
         case PV_WS64:
-            return launch_pdl(k_project_ws64<MODE>, dim3(a.count), dim3(128), 0, st, a, rinv);
+            return launch_pdl(pdl, k_project_ws64<MODE>, dim3(a.count), dim3(128), 0, st, a, rinv);
         case PV_OW8:
-            return launch_pdl(k_project_ow<MODE, 8>, dim3((a.count + OWLayout<8>::BPC - 1) / OWLayout<8>::BPC),
-                              dim3(128), OWLayout<8>::kBytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_ow<MODE, 8>,
+                              dim3((a.count + OWLayout<8>::BPC - 1) / OWLayout<8>::BPC), dim3(128),
+                              OWLayout<8>::kBytes, st, a, rinv);
         case PV_OW16:
-            return launch_pdl(k_project_ow<MODE, 16>, dim3((a.count + OWLayout<16>::BPC - 1) / OWLayout<16>::BPC),
-                              dim3(128), OWLayout<16>::kBytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_ow<MODE, 16>,
+                              dim3((a.count + OWLayout<16>::BPC - 1) / OWLayout<16>::BPC), dim3(128),
+                              OWLayout<16>::kBytes, st, a, rinv);
         case PV_OW64:
-            return launch_pdl(k_project_ow64<MODE>, dim3((a.count + 1) / 2), dim3(128), kOW64Bytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_ow64<MODE>, dim3((a.count + 1) / 2), dim3(128), kOW64Bytes, st,
+                              a, rinv);
         case PV_OW32:
-            return launch_pdl(k_project_ow<MODE, 32>, dim3((a.count + OWLayout<32>::BPC - 1) / OWLayout<32>::BPC),
-                              dim3(128), OWLayout<32>::kBytes, st, a, rinv);
+            return launch_pdl(pdl, k_project_ow<MODE, 32>,
+                              dim3((a.count + OWLayout<32>::BPC - 1) / OWLayout<32>::BPC), dim3(128),
+                              OWLayout<32>::kBytes, st, a, rinv);
         case PV_TS16:
-            return launch_pdl(k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st, a, rinv);
+            return launch_pdl(pdl, k_project<T, MODE, ShapeS16>, dim3(a.count), dim3(ShapeS16::NT), smem, st,
+                              a, rinv);
         case PV_TS32:
-            return launch_pdl(k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st, a, rinv);
+            return launch_pdl(pdl, k_project<T, MODE, ShapeS32>, dim3(a.count), dim3(ShapeS32::NT), smem, st,
+                              a, rinv);
         case PV_TS64:
-            return launch_pdl(k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st, a, rinv);
+            return launch_pdl(pdl, k_project<T, MODE, ShapeS64>, dim3(a.count), dim3(ShapeS64::NT), smem, st,
+                              a, rinv);
         default:
-            return launch_pdl(k_project<T, MODE, ShapeS96>, dim3(a.count), dim3(ShapeS96::NT), smem, st, a, rinv);
+            return launch_pdl(pdl, k_project<T, MODE, ShapeS96>, dim3(a.count), dim3(ShapeS96::NT), smem, st,
+                              a, rinv);
     }
 }
 

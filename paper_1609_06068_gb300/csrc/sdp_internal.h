@@ -208,6 +208,7 @@ struct ProjArgs {
     // them whatever the parity of later iterations. NULL for a single problem.
     const int* blk_inst;
     const int* inst_conv;
+    int pdl;                // programmatic dependent launch inside an iteration (0 standalone)
 };
 
 // Entries covered by more cliques than this are scattered by a whole warp (in ascending clique
@@ -237,6 +238,7 @@ struct ProjPlan {
 struct IterPtrs {
     // problem (a batch is the block-diagonal union of its problems)
     int n, m, p, nEL, SL, smax;
+    int pdl;                        // launch the iteration's kernels with programmatic dependent launch
     int ninst;                      // problems in the batch (1 after sdp_setup)
     int mmax;                       // largest number of constraints of one problem
     const int* inst_cl;             // [ninst+1] first clique of each problem
@@ -286,15 +288,12 @@ struct IterPtrs {
     Ctrl* ctrl;
 };
 
-// Programmatic dependent launch (a kernel scheduled while its predecessor finishes, waiting for it
-// in pdl_wait()) is wired through every iteration kernel but switched off: on GB300 it made the
-// captured iteration slower (FP32 projection 9.8k -> 9.0k iter/s, FP64 1.8k -> 0.9k iter/s on the
-// n = 1020 block-arrow workload). With the attribute off, pdl_wait()/pdl_trigger() are no-ops.
-constexpr bool kUsePDL = false;
-
+// Launch with programmatic dependent launch when pdl is set (the kernel is scheduled while its
+// predecessor finishes and waits for it in pdl_wait()); without it pdl_wait()/pdl_trigger() in
+// the kernel are no-ops and it starts once its predecessor has completed.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args... args) {
+inline cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -304,7 +303,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = kUsePDL ? 1 : 0;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
