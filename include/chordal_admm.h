@@ -356,8 +356,10 @@ int sdp_set_proj_table(sdp_handle h, int prec, const int* table, int len);
  * order (count = 5 primal, 6 dual, one more each for cones, for the per-problem stop test of a
  * batch and for the triangular KKT solve, whose two solves are two phases; the projection phase
  * covers all of its launches). Returns count, or < 0 on error; max_out is the capacity of ms_out.
- * The reps + 1 iterations really run and advance the state, with the stop test disabled.
- * sdp_phase_name(h, i) names phase i for the handle's current form (NULL when out of range). */
+ * The reps + 1 iterations really run and advance the state, with the stop test disabled; the
+ * call creates reps x (count + 1) CUDA events, destroyed before it returns (an event that cannot
+ * be created gives SDP_ERR_CUDA). sdp_phase_name(h, i) names phase i for the handle's current
+ * form (NULL when out of range). */
 int sdp_time_phases(sdp_handle h, int reps, void* cuda_stream, double* ms_out, int max_out);
 const char* sdp_phase_name(sdp_handle h, int i);
 
